@@ -1,0 +1,185 @@
+/*
+ * cffyn.h -- C-ABI of the GB300 (sm_103a) implementation of the Chebyshev /
+ * double-Fourier pseudospectral method with the spin-weighted (Yn) tensor
+ * filter on one spherical shell (Bruegmann, arXiv:1104.3408).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Field arrays.  FP64, contiguous, device memory owned by the caller, at least
+ * 16-byte aligned (256 recommended), laid out as the paper's linear 4-d index
+ * (Sec. 2.4) with the single theta cover stored (Sec. 2.1):
+ *     u[((mu * n_phi + j) * n_theta + i) * n_r + k]
+ * k: radius (Chebyshev extrema, increasing r, eq. rk), i: theta (pole
+ * staggered, eq. thetai), j: phi (eq. phij), mu: field.  The library never
+ * frees or retains caller pointers.
+ *
+ * Fields (n_fields = 50, 54 or 58; App. A.1 eqs. gdot, Phidot, Pidot): the
+ * symmetric pairs (tt,tx,ty,tz,xx,xy,xz,yy,yz,zz) of g_ab (fields 0..9),
+ * Pi_ab (10..19), Phi_xab (20..29), Phi_yab (30..39), Phi_zab (40..49); then
+ * H_a (50..53) and dH_a/dt (54..57) where present.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls enqueue work and return; results are ready when the stream
+ * is.  Exceptions: cffyn_create_*, cffyn_destroy and cffyn_constraint_norms
+ * synchronise, cffyn_get_* copy to host synchronously.
+ *
+ * Errors.  Every call returns an int status (0 = CFFYN_OK, negative =
+ * error) and never aborts, traps or throws.  cffyn_last_error() returns a
+ * thread-local message for the last failing call on the calling thread.
+ * CFFYN_ENONFINITE is reported by cffyn_rk4_step when its fused finiteness
+ * check saw a NaN/Inf in a stage right-hand side (the state is then
+ * meaningless but the context stays usable).
+ *
+ * Threading.  A shell handle is not thread-safe: serialise calls on one
+ * handle.  Distinct handles are independent.
+ */
+#ifndef CFFYN_H
+#define CFFYN_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define CFFYN_API __attribute__((visibility("default")))
+#else
+#define CFFYN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CFFYN_OK 0
+#define CFFYN_EINVAL (-1)    /* bad argument (sizes, null pointer, mode) */
+#define CFFYN_ENOMEM (-2)    /* device allocation failed */
+#define CFFYN_ECUDA (-3)     /* a CUDA runtime call failed */
+#define CFFYN_ENONFINITE (-4)/* non-finite value seen by the step's check */
+#define CFFYN_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define CFFYN_ENOTIMPL (-6)  /* option not implemented */
+
+/* Arithmetic of the operator applications and of the pointwise RHS. */
+#define CFFYN_FP64 0   /* FP64 CUDA-core arithmetic throughout */
+#define CFFYN_MIXED 1  /* split-precision BF16 tensor-core products with exact
+                          FP32 partial sums, recombined in 64-bit integers;
+                          double-float (FP32 pair) pointwise arithmetic; FP64
+                          state accumulation */
+
+/* Where the Yn filter is applied (Sec. 2.5). */
+#define CFFYN_FILTER_SUBSTEP 0 /* every stage right-hand side after the BC */
+#define CFFYN_FILTER_STEP 1    /* the state after each full RK4 step (paper) */
+
+typedef struct cffyn_shell cffyn_shell;
+
+typedef struct cffyn_shell_desc {
+  int n_r;          /* radial points, >= 3 (eq. rk) */
+  int n_theta;      /* theta points N, >= 2 (eq. thetai) */
+  int n_phi;        /* phi points, must equal 2 * n_theta (Sec. 2.1) */
+  double r_in;      /* inner radius, > 0 */
+  double r_out;     /* outer radius, > r_in */
+  int L;            /* retained spherical-harmonic degree, 0 <= L <= n_theta-1;
+                       the filter keeps l <= L (n_f = n_theta-1-L, Sec. 3.5) */
+  int n_fields;     /* 50, 54 or 58 (App. A.1) */
+  int precision;    /* CFFYN_FP64 or CFFYN_MIXED */
+  int filter_mode;  /* CFFYN_FILTER_SUBSTEP or CFFYN_FILTER_STEP */
+  double courant;   /* lambda of dt = lambda * min dx (Sec. 4.1); <= 0 -> 0.25 */
+} cffyn_shell_desc;
+
+/* Builds a shell: collocation grid (Sec. 2.1), differentiation matrices
+ * (Sec. 2.3), real DFT matrices (Sec. 3.1), spin-weighted synthesis matrices by
+ * the recursion of eqs. Yninc/Yncoeffs/Ynnegative and the filter matrices
+ * F^n_m = P^n_m f (P^n_m)^+ of eq. FasPfQ for n in [-3,3], m in [0,L], all in
+ * FP64 on the current CUDA device, plus the library's workspace.
+ * Defaults of cffyn_create_shell: 50 fields, CFFYN_MIXED, CFFYN_FILTER_SUBSTEP,
+ * courant 0.25.  Synchronous.  Returns CFFYN_EINVAL for sizes outside the
+ * ranges above (or n_theta > 96, n_r > 96), CFFYN_ENOMEM / CFFYN_ECUDA on
+ * device failures; *out is NULL on error. */
+CFFYN_API int cffyn_create_shell(int n_r, int n_theta, int n_phi, double r_in, double r_out, int L,
+                       cffyn_shell** out);
+CFFYN_API int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out);
+
+/* Frees the handle and its device memory (synchronises the device first).
+ * NULL is allowed. */
+CFFYN_API int cffyn_destroy(cffyn_shell* sh);
+
+/* Bytes of device memory the handle owns (matrices + workspace). */
+CFFYN_API size_t cffyn_device_bytes(const cffyn_shell* sh);
+
+/* dt = courant * min(r_1 - r_0, 2 r_0 sin(theta_0) sin(dphi/2)) (Sec. 4.1). */
+CFFYN_API double cffyn_default_dt(const cffyn_shell* sh);
+
+/* Static gauge source H_a (eq. gauge), H[4][n_phi][n_theta][n_r] device FP64.
+ * The library stores H and its Cartesian derivatives d_i H_a computed with the
+ * shell's spectral operators.  Used when n_fields == 50. */
+CFFYN_API int cffyn_set_gauge(cffyn_shell* sh, const double* H, void* stream);
+
+/* H_a = -Gamma_a(u) (eq. gauge and eq. Gamma from undifferentiated fields),
+ * pointwise.  n_fields == 50: stored as the static gauge (like
+ * cffyn_set_gauge).  n_fields 54/58: written into fields 50..53 of u (u is
+ * then read-write) and dH/dt (54..57) set to zero. */
+CFFYN_API int cffyn_init_gauge_from_state(cffyn_shell* sh, double* u, void* stream);
+
+/* Cartesian derivatives of every field (Secs. 2.3-2.4, chain rule eq. dvdx):
+ * dxyz[d][mu][n_phi][n_theta][n_r], d = x, y, z (3 * n_fields arrays).
+ * The theta derivative uses the double cover of Sec. 2.1. */
+CFFYN_API int cffyn_derivs(cffyn_shell* sh, const double* u, double* dxyz, void* stream);
+
+/* Right-hand side d_t u = S - A^k d_k u of eqs. gdot, Phidot, Pidot with the
+ * freeze-incoming outer boundary condition of App. A.2 applied on the
+ * outermost sphere; no filter.  Requires the gauge for 50 fields. */
+CFFYN_API int cffyn_rhs(cffyn_shell* sh, const double* u, double* dudt, void* stream);
+
+/* Yn tensor filter of Secs. 3.4-3.5: per tensor group, triad decomposition
+ * (eq. tensorexpansion), phi DFT (eq. forwardF), projection with F^n_m per spin
+ * n and azimuthal m (eq. FasPfQ), inverse DFT, recombination.  out may alias u. */
+CFFYN_API int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream);
+
+/* n_steps classical RK4 steps of the method of lines (Sec. 2.5) in place on u
+ * with the shell's filter mode; dt <= 0 selects cffyn_default_dt.  In
+ * CFFYN_FILTER_SUBSTEP mode every stage right-hand side is filtered after the
+ * boundary condition; the caller filters the initial data once.  The first
+ * call captures one step in a CUDA graph (so it must not itself be made during
+ * a stream capture); later calls with the same u and dt replay it.  The call
+ * synchronises `stream` at its end to read the fused finiteness flag and
+ * returns CFFYN_ENONFINITE if a stage right-hand side was not finite. */
+CFFYN_API int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream);
+
+/* RMS over all points of C_iab = d_i g_ab - Phi_iab (30 components, numerical
+ * derivative) and of C_a = H_a + Gamma_a (4 components) (App. A.1), reduced
+ * in FP64 on the device; out[0] = C_iab RMS, out[1] = C_a RMS (host memory).
+ * Synchronous. */
+CFFYN_API int cffyn_constraint_norms(cffyn_shell* sh, const double* u, double out[2], void* stream);
+
+/* Copies the shell's FP64 filter matrix F^n_m (n in [-3,3], m in [0,L];
+ * N x N row-major, N = n_theta) to host memory.  Synchronous.  For checks of
+ * the on-device construction. */
+CFFYN_API int cffyn_get_filter_matrix(const cffyn_shell* sh, int n, int m, double* host_out);
+
+/* Copies one FP64 operator to host: which = 0: D_r (n_r x n_r),
+ * 1: theta derivative of the double cover restricted to the single cover
+ * (N x 2N: columns 0..N-1 act on theta_0..theta_{N-1} at phi_j, column N+q on
+ * theta_{N-1-q} at phi_j + pi), 2: D_phi (n_phi x n_phi).  Row-major. */
+CFFYN_API int cffyn_get_operator(const cffyn_shell* sh, int which, double* host_out);
+
+/* Phase timing of one RK4 step (for benchmarks and tracing): runs one step
+ * on u eagerly (no graph, same kernels as cffyn_rk4_step) with CUDA events
+ * around every kernel group on `stream`, synchronising after each group, and
+ * returns per group the device time in milliseconds summed over the step
+ * (ms_out) and the number of kernel launches (launches_out).  Groups, in
+ * order: d_r, d_theta, d_phi, right-hand side + BC, spin decomposition, phi
+ * analysis, projection, phi synthesis, reconstruction + RK4 update.  u is
+ * advanced by one step.  Both output arrays hold CFFYN_PROFILE_PHASES entries
+ * (host memory). */
+#define CFFYN_PROFILE_PHASES 9
+CFFYN_API int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out,
+                                 int* launches_out, void* stream);
+
+/* Message of the last failing call on this thread (never NULL). */
+CFFYN_API const char* cffyn_last_error(void);
+
+/* Library version string. */
+CFFYN_API const char* cffyn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFFYN_H */

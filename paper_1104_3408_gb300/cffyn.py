@@ -1,0 +1,222 @@
+"""Thin ctypes binding of libcffyn.so (include/cffyn.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device memory and streams come from PyTorch: arrays are contiguous
+float64 CUDA tensors in the layout u[mu, n_phi, n_theta, n_r]; the stream is
+torch's current stream unless one is passed.  If the library is missing the
+calls raise -- there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcffyn.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
+FP64, MIXED = 0, 1
+FILTER_SUBSTEP, FILTER_STEP = 0, 1
+
+EXPORTED = [
+    "cffyn_create_shell", "cffyn_create_shell_ex", "cffyn_destroy", "cffyn_device_bytes",
+    "cffyn_default_dt", "cffyn_set_gauge", "cffyn_init_gauge_from_state", "cffyn_derivs",
+    "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_constraint_norms",
+    "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
+    "cffyn_profile_step",
+]
+PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs", "decompose", "dft_fwd", "project", "dft_inv",
+                  "reconstruct"]
+
+
+class ShellDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
+        ("r_in", ctypes.c_double), ("r_out", ctypes.c_double), ("L", ctypes.c_int),
+        ("n_fields", ctypes.c_int), ("precision", ctypes.c_int), ("filter_mode", ctypes.c_int),
+        ("courant", ctypes.c_double),
+    ]
+
+
+class CffynError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cffyn error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libcffyn.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with __graft_entry__.build() "
+                           "(paper_1104_3408_gb300._build.build())")
+    lib = ctypes.CDLL(path)
+    vp, dp, i, d = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "cffyn_create_shell": ([i, i, i, d, d, i, ctypes.POINTER(vp)], i),
+        "cffyn_create_shell_ex": ([ctypes.POINTER(ShellDesc), ctypes.POINTER(vp)], i),
+        "cffyn_destroy": ([vp], i),
+        "cffyn_device_bytes": ([vp], ctypes.c_size_t),
+        "cffyn_default_dt": ([vp], d),
+        "cffyn_set_gauge": ([vp, dp, vp], i),
+        "cffyn_init_gauge_from_state": ([vp, dp, vp], i),
+        "cffyn_derivs": ([vp, dp, dp, vp], i),
+        "cffyn_rhs": ([vp, dp, dp, vp], i),
+        "cffyn_filter": ([vp, dp, dp, vp], i),
+        "cffyn_rk4_step": ([vp, dp, d, i, vp], i),
+        "cffyn_constraint_norms": ([vp, dp, ctypes.POINTER(ctypes.c_double), vp], i),
+        "cffyn_get_filter_matrix": ([vp, i, i, ctypes.POINTER(ctypes.c_double)], i),
+        "cffyn_get_operator": ([vp, i, ctypes.POINTER(ctypes.c_double)], i),
+        "cffyn_profile_step": ([vp, dp, d, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int), vp], i),
+        "cffyn_last_error": ([], ctypes.c_char_p),
+        "cffyn_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise CffynError(rc, load().cffyn_last_error().decode())
+    return rc
+
+
+def _ptr(t, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{what} must be a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Shell:
+    """One spherical shell (a cffyn_shell handle)."""
+
+    def __init__(self, n_r, n_theta, n_phi, r_in, r_out, L, n_fields=50, precision=MIXED,
+                 filter_mode=FILTER_SUBSTEP, courant=0.25):
+        lib = load()
+        desc = ShellDesc(n_r, n_theta, n_phi, r_in, r_out, L, n_fields, precision, filter_mode,
+                         courant)
+        h = ctypes.c_void_p()
+        _check(lib.cffyn_create_shell_ex(ctypes.byref(desc), ctypes.byref(h)))
+        self.h = h
+        self.n_r, self.n_theta, self.n_phi = n_r, n_theta, n_phi
+        self.r_in, self.r_out, self.L = r_in, r_out, L
+        self.n_fields, self.precision, self.filter_mode = n_fields, precision, filter_mode
+
+    @property
+    def shape(self):
+        return (self.n_fields, self.n_phi, self.n_theta, self.n_r)
+
+    def destroy(self):
+        if self.h:
+            load().cffyn_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def device_bytes(self):
+        return load().cffyn_device_bytes(self.h)
+
+    def default_dt(self):
+        return load().cffyn_default_dt(self.h)
+
+    def set_gauge(self, H, stream=None):
+        _check(load().cffyn_set_gauge(self.h, _ptr(H, "H"), _stream(stream)))
+
+    def init_gauge_from_state(self, u, stream=None):
+        _check(load().cffyn_init_gauge_from_state(self.h, _ptr(u, "u"), _stream(stream)))
+
+    def derivs(self, u, out, stream=None):
+        _check(load().cffyn_derivs(self.h, _ptr(u, "u"), _ptr(out, "dxyz"), _stream(stream)))
+        return out
+
+    def rhs(self, u, out, stream=None):
+        _check(load().cffyn_rhs(self.h, _ptr(u, "u"), _ptr(out, "dudt"), _stream(stream)))
+        return out
+
+    def filter(self, u, out, stream=None):
+        _check(load().cffyn_filter(self.h, _ptr(u, "u"), _ptr(out, "out"), _stream(stream)))
+        return out
+
+    def rk4_step(self, u, dt=0.0, n_steps=1, stream=None):
+        _check(load().cffyn_rk4_step(self.h, _ptr(u, "u"), float(dt), int(n_steps), _stream(stream)))
+        return u
+
+    def profile_step(self, u, dt=0.0, stream=None):
+        """Per-phase device ms and launch counts of one eager RK4 step."""
+        n = len(PROFILE_PHASES)
+        ms = (ctypes.c_double * n)()
+        la = (ctypes.c_int * n)()
+        _check(load().cffyn_profile_step(self.h, _ptr(u, "u"), float(dt), ms, la, _stream(stream)))
+        return {k: (float(ms[i]), int(la[i])) for i, k in enumerate(PROFILE_PHASES)}
+
+    def constraint_norms(self, u, stream=None):
+        out = (ctypes.c_double * 2)()
+        _check(load().cffyn_constraint_norms(self.h, _ptr(u, "u"), out, _stream(stream)))
+        return float(out[0]), float(out[1])
+
+    def get_filter_matrix(self, n, m):
+        import numpy as np
+        a = np.zeros((self.n_theta, self.n_theta))
+        _check(load().cffyn_get_filter_matrix(self.h, n, m,
+                                              a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return a
+
+    def get_operator(self, which):
+        import numpy as np
+        shapes = {0: (self.n_r, self.n_r), 1: (self.n_theta, 2 * self.n_theta),
+                  2: (self.n_phi, self.n_phi)}
+        a = np.zeros(shapes[which])
+        _check(load().cffyn_get_operator(self.h, which,
+                                         a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return a
+
+
+# C-ABI names, one to one (module-level functions taking a Shell)
+def create_shell(n_r, n_theta, n_phi, r_in, r_out, L, **kw):
+    return Shell(n_r, n_theta, n_phi, r_in, r_out, L, **kw)
+
+
+def rhs(sh, u, out, stream=None):
+    return sh.rhs(u, out, stream)
+
+
+def filter(sh, u, out, stream=None):  # noqa: A001 - the C-ABI name
+    return sh.filter(u, out, stream)
+
+
+def rk4_step(sh, u, dt=0.0, n_steps=1, stream=None):
+    return sh.rk4_step(u, dt, n_steps, stream)
+
+
+def derivs(sh, u, out, stream=None):
+    return sh.derivs(u, out, stream)
+
+
+def destroy(sh):
+    sh.destroy()
+
+
+def version():
+    return load().cffyn_version().decode()

@@ -1,0 +1,519 @@
+// C-ABI entry points of include/cffyn.h: argument checks, workspace, and the
+// orchestration of one right-hand side / filter / RK4 step (paper Sec. 2.5)
+// out of the operator kernels (ops.cu) and the pointwise kernels
+// (pointwise.cu).  One RK4 step is captured once into a CUDA graph and
+// replayed.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace cffyn {
+
+static thread_local char g_err[512] = "no error";
+static thread_local long long g_launches = 0;
+
+void count_launch() { ++g_launches; }
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+// ops.cu
+int set_op_smem_limits();
+int op_deriv_r(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int op_deriv_theta(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int op_deriv_phi(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int op_dft_fwd(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int op_project(const cffyn_shell*, const double*, double*, const int*, int, const int* const[3],
+               const int[3], cudaStream_t);
+// setup.cu
+int build_operators(cffyn_shell*);
+void free_sliced(SlicedOp&);
+// pointwise.cu
+int pw_rhs(const cffyn_shell*, const double*, const double*, double*, cudaStream_t);
+int pw_decompose(const cffyn_shell*, const double*, double*, cudaStream_t);
+int pw_reconstruct(const cffyn_shell*, const double*, double*, int, double*, double*, double*, double,
+                   int*, cudaStream_t);
+int pw_cart(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int pw_gauge(const cffyn_shell*, const double*, double*, long long, cudaStream_t);
+int pw_constraints(const cffyn_shell*, const double*, const double*, const double*, long long, double*,
+                   cudaStream_t);
+
+}  // namespace cffyn
+
+using namespace cffyn;
+
+namespace {
+
+constexpr int kNR0 = 16;
+constexpr int kNC[3] = {11, 5, 1};
+const int* slots_r0(const cffyn_shell* sh) { return sh->slots; }
+const int* slots_c(const cffyn_shell* sh, int s) {
+  return sh->slots + 16 + (s == 0 ? 0 : (s == 1 ? 11 : 16));
+}
+
+int check_ptr(const void* p, const char* what) {
+  if (!p) {
+    set_error("%s is NULL", what);
+    return CFFYN_EINVAL;
+  }
+  if (((uintptr_t)p) & 15) {
+    set_error("%s is not 16-byte aligned", what);
+    return CFFYN_EINVAL;
+  }
+  return CFFYN_OK;
+}
+
+int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, cudaStream_t st) {
+  const size_t P = sh->P;
+  int rc;
+  if ((rc = op_deriv_r(sh, u, D, nf, st))) return rc;
+  if ((rc = op_deriv_theta(sh, u, D + (size_t)nf * P, nf, st))) return rc;
+  if ((rc = op_deriv_phi(sh, u, D + (size_t)2 * nf * P, nf, st))) return rc;
+  return CFFYN_OK;
+}
+
+// spin slots in `spin` (nv x P) -> filtered spin slots back in `spin`;
+// scratch: D (3 nv P)
+int filter_spin_slots(cffyn_shell* sh, double* spin, cudaStream_t st) {
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  int rc;
+  double* C = sh->D;
+  double* C2 = sh->D + nvP;
+  if ((rc = op_dft_fwd(sh, spin, C, sh->nv, st))) return rc;
+  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  if ((rc = op_project(sh, C, C2, slots_r0(sh), kNR0, cl, kNC, st))) return rc;
+  if ((rc = op_dft_inv(sh, C2, spin, sh->nv, st))) return rc;
+  return CFFYN_OK;
+}
+
+void free_shell(cffyn_shell* sh) {
+  if (!sh) return;
+  cudaDeviceSynchronize();
+  double** ptrs[] = {&sh->r,     &sh->sth,    &sh->cth,    &sh->sph, &sh->cph,  &sh->Dr,   &sh->Dth2,
+                     &sh->Dph,   &sh->Fan,    &sh->Fsy,    &sh->Fraw, &sh->Fproj0, &sh->FprojC,
+                     &sh->H,     &sh->dH,     &sh->U,      &sh->kacc, &sh->D,    &sh->S,
+                     &sh->red};
+  for (double** p : ptrs)
+    if (*p) cudaFree(*p);
+  SlicedOp* so[] = {&sh->sDr, &sh->sDth2, &sh->sDph, &sh->sFan, &sh->sFsy, &sh->sF0,
+                    &sh->sFC[0], &sh->sFC[1], &sh->sFC[2]};
+  for (SlicedOp* s : so) free_sliced(*s);
+  if (sh->slots) cudaFree(sh->slots);
+  if (sh->cap_stream) cudaStreamDestroy(sh->cap_stream);
+  if (sh->flag_host) cudaFreeHost(sh->flag_host);
+  if (sh->flag) cudaFree(sh->flag);
+  if (sh->graph) cudaGraphExecDestroy(sh->graph);
+  delete sh;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cffyn_last_error(void) { return g_err; }
+const char* cffyn_version(void) { return "cffyn 0.1 (sm_103a)"; }
+
+int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return CFFYN_EINVAL;
+  }
+  *out = nullptr;
+  if (!desc) {
+    set_error("desc is NULL");
+    return CFFYN_EINVAL;
+  }
+  const cffyn_shell_desc& d = *desc;
+  if (d.n_r < 3 || d.n_r > kMaxNr || d.n_theta < 2 || d.n_theta > kMaxN ||
+      d.n_phi != 2 * d.n_theta || !(d.r_in > 0) || !(d.r_out > d.r_in) || d.L < 0 ||
+      d.L > d.n_theta - 1) {
+    set_error("invalid shell sizes (n_r %d, n_theta %d, n_phi %d, r %g..%g, L %d)", d.n_r, d.n_theta,
+              d.n_phi, d.r_in, d.r_out, d.L);
+    return CFFYN_EINVAL;
+  }
+  if (d.n_fields != 50 && d.n_fields != 54 && d.n_fields != 58) {
+    set_error("n_fields must be 50, 54 or 58");
+    return CFFYN_EINVAL;
+  }
+  if (d.n_fields != 50) {
+    set_error("n_fields %d: gauge-field groups are not implemented", d.n_fields);
+    return CFFYN_ENOTIMPL;
+  }
+  if (d.precision != CFFYN_FP64 && d.precision != CFFYN_MIXED) {
+    set_error("precision must be CFFYN_FP64 or CFFYN_MIXED");
+    return CFFYN_EINVAL;
+  }
+  if (d.filter_mode != CFFYN_FILTER_SUBSTEP && d.filter_mode != CFFYN_FILTER_STEP) {
+    set_error("filter_mode must be CFFYN_FILTER_SUBSTEP or CFFYN_FILTER_STEP");
+    return CFFYN_EINVAL;
+  }
+  cffyn_shell* sh = new (std::nothrow) cffyn_shell();
+  if (!sh) {
+    set_error("host allocation failed");
+    return CFFYN_ENOMEM;
+  }
+  sh->d = d;
+  sh->n_r = d.n_r;
+  sh->N = d.n_theta;
+  sh->J = d.n_phi;
+  sh->L = d.L;
+  sh->R = 2 * d.L + 1;
+  sh->nv = d.n_fields;
+  sh->P = (size_t)d.n_r * d.n_theta * d.n_phi;
+  cudaGetDevice(&sh->device);
+  {
+    const double pi = 3.14159265358979323846;
+    double r0 = 0.5 * (d.r_out + d.r_in) - 0.5 * (d.r_out - d.r_in);
+    double r1 = 0.5 * (d.r_out + d.r_in) - 0.5 * (d.r_out - d.r_in) * cos(pi / (d.n_r - 1));
+    double th0 = pi * 0.5 / d.n_theta;
+    double dphi = 2.0 * pi / d.n_phi;
+    double dx = r1 - r0;
+    double ch = 2.0 * r0 * sin(th0) * sin(0.5 * dphi);
+    if (ch < dx) dx = ch;
+    sh->dt_default = (d.courant > 0 ? d.courant : 0.25) * dx;
+  }
+  int rc;
+  auto fail = [&](int code) {
+    free_shell(sh);
+    return code;
+  };
+  if (set_op_smem_limits() != CFFYN_OK) return fail(CFFYN_ECUDA);
+  if ((rc = build_operators(sh))) return fail(rc);
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  auto alloc = [&](double** p, size_t n) -> int {
+    if (cudaMalloc(p, n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of %zu bytes failed", n * sizeof(double));
+      return CFFYN_ENOMEM;
+    }
+    sh->bytes += n * sizeof(double);
+    return CFFYN_OK;
+  };
+  if ((rc = alloc(&sh->U, nvP)) || (rc = alloc(&sh->kacc, nvP)) || (rc = alloc(&sh->D, 3 * nvP)) ||
+      (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, 12 * sh->P)) ||
+      (rc = alloc(&sh->red, 2)))
+    return fail(rc);
+  {
+    int host[33];
+    for (int i = 0; i < 16; ++i) host[i] = i;
+    for (int q = 0; q < 11; ++q) host[16 + q] = 16 + 2 * q;
+    for (int q = 0; q < 5; ++q) host[27 + q] = 38 + 2 * q;
+    host[32] = 48;
+    if (cudaMalloc(&sh->slots, sizeof(host)) != cudaSuccess) return fail(CFFYN_ENOMEM);
+    if (cudaMemcpy(sh->slots, host, sizeof(host), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(CFFYN_ECUDA);
+  }
+  if (cudaMalloc(&sh->flag, 64) != cudaSuccess) return fail(CFFYN_ENOMEM);
+  if (cudaMemset(sh->flag, 0, 64) != cudaSuccess) return fail(CFFYN_ECUDA);
+  if (cudaStreamCreateWithFlags(&sh->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(CFFYN_ECUDA);
+  if (cudaMallocHost(&sh->flag_host, sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("shell construction failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return fail(CFFYN_ECUDA);
+  }
+  *out = sh;
+  return CFFYN_OK;
+}
+
+int cffyn_create_shell(int n_r, int n_theta, int n_phi, double r_in, double r_out, int L,
+                       cffyn_shell** out) {
+  cffyn_shell_desc d;
+  d.n_r = n_r;
+  d.n_theta = n_theta;
+  d.n_phi = n_phi;
+  d.r_in = r_in;
+  d.r_out = r_out;
+  d.L = L;
+  d.n_fields = 50;
+  d.precision = CFFYN_MIXED;
+  d.filter_mode = CFFYN_FILTER_SUBSTEP;
+  d.courant = 0.25;
+  return cffyn_create_shell_ex(&d, out);
+}
+
+int cffyn_destroy(cffyn_shell* sh) {
+  free_shell(sh);
+  return CFFYN_OK;
+}
+
+size_t cffyn_device_bytes(const cffyn_shell* sh) { return sh ? sh->bytes : 0; }
+
+double cffyn_default_dt(const cffyn_shell* sh) { return sh ? sh->dt_default : 0.0; }
+
+static int gauge_derivs(cffyn_shell* sh, cudaStream_t st) {
+  // d_i H_a with the shell's operators: spherical derivatives into D, chain rule into dH
+  int rc;
+  if ((rc = derivs_spherical(sh, sh->H, sh->D, 4, st))) return rc;
+  if ((rc = pw_cart(sh, sh->D, sh->dH, 4, st))) return rc;
+  sh->gauge_set = true;
+  return CFFYN_OK;
+}
+
+int cffyn_set_gauge(cffyn_shell* sh, const double* H, void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(H, "H"))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  CF_CUDA(cudaMemcpyAsync(sh->H, H, 4 * sh->P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return gauge_derivs(sh, st);
+}
+
+int cffyn_init_gauge_from_state(cffyn_shell* sh, double* u, void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u"))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = pw_gauge(sh, u, sh->H, (long long)sh->P, st))) return rc;
+  return gauge_derivs(sh, st);
+}
+
+int cffyn_derivs(cffyn_shell* sh, const double* u, double* dxyz, void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u")) || (rc = check_ptr(dxyz, "dxyz"))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, st))) return rc;
+  return pw_cart(sh, sh->D, dxyz, sh->nv, st);
+}
+
+int cffyn_rhs(cffyn_shell* sh, const double* u, double* dudt, void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u")) || (rc = check_ptr(dudt, "dudt"))) return rc;
+  if (sh->nv == 50 && !sh->gauge_set) {
+    set_error("gauge source not set (cffyn_set_gauge / cffyn_init_gauge_from_state)");
+    return CFFYN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, st))) return rc;
+  return pw_rhs(sh, u, sh->D, dudt, st);
+}
+
+int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u")) || (rc = check_ptr(out, "out"))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = pw_decompose(sh, u, sh->S, st))) return rc;
+  if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
+  return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+}
+
+// One RK4 step on u (enqueued on st); see cffyn_rk4_step.
+static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) {
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
+  int rc;
+  for (int s = 0; s < 4; ++s) {
+    const double* X = s == 0 ? u : sh->U;
+    if ((rc = derivs_spherical(sh, X, sh->D, sh->nv, st))) return rc;
+    if ((rc = pw_rhs(sh, X, sh->D, sh->S, st))) return rc;
+    if (per_sub) {
+      double* spin = sh->D;  // derivatives are dead after the rhs
+      if ((rc = pw_decompose(sh, sh->S, spin + 2 * nvP, st))) return rc;
+      // filter_spin_slots uses D[0..2nvP) as coefficient scratch
+      if ((rc = filter_spin_slots(sh, spin + 2 * nvP, st))) return rc;
+      if ((rc = pw_reconstruct(sh, spin + 2 * nvP, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st)))
+        return rc;
+    } else {
+      if ((rc = pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st))) return rc;
+    }
+  }
+  if (!per_sub) {
+    if ((rc = pw_decompose(sh, u, sh->S, st))) return rc;
+    if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
+    if ((rc = pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st))) return rc;
+  }
+  return CFFYN_OK;
+}
+
+int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u"))) return rc;
+  if (n_steps < 0) { set_error("n_steps < 0"); return CFFYN_EINVAL; }
+  if (sh->nv == 50 && !sh->gauge_set) {
+    set_error("gauge source not set (cffyn_set_gauge / cffyn_init_gauge_from_state)");
+    return CFFYN_EINVAL;
+  }
+  if (n_steps == 0) return CFFYN_OK;
+  if (!(dt > 0)) dt = sh->dt_default;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!sh->graph || sh->graph_u != u || sh->graph_dt != dt) {
+    if (sh->graph) {
+      cudaGraphExecDestroy(sh->graph);
+      sh->graph = nullptr;
+    }
+    cudaGraph_t g;
+    CF_CUDA(cudaStreamBeginCapture(sh->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int erc = enqueue_step(sh, u, dt, sh->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(sh->cap_stream, &g);
+    if (erc) return erc;
+    if (ce != cudaSuccess) {
+      set_error("graph capture failed: %s", cudaGetErrorString(ce));
+      return CFFYN_ECUDA;
+    }
+    ce = cudaGraphInstantiate(&sh->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) {
+      sh->graph = nullptr;
+      set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
+      return CFFYN_ECUDA;
+    }
+    sh->graph_u = u;
+    sh->graph_dt = dt;
+  }
+  CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
+  for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
+  CF_CUDA(cudaMemcpyAsync(sh->flag_host, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(cudaStreamSynchronize(st));
+  if (*sh->flag_host) {
+    set_error("non-finite value in a stage right-hand side");
+    return CFFYN_ENONFINITE;
+  }
+  return CFFYN_OK;
+}
+
+int cffyn_constraint_norms(cffyn_shell* sh, const double* u, double out[2], void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u"))) return rc;
+  if (!out) { set_error("out is NULL"); return CFFYN_EINVAL; }
+  if (sh->nv == 50 && !sh->gauge_set) {
+    set_error("gauge source not set");
+    return CFFYN_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // derivatives of g_ab only (fields 0..9)
+  if ((rc = derivs_spherical(sh, u, sh->D, 10, st))) return rc;
+  double* dcart = sh->S;  // [3][10][P]
+  if ((rc = pw_cart(sh, sh->D, dcart, 10, st))) return rc;
+  double* red = sh->red;
+  CF_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
+  if ((rc = pw_constraints(sh, u, dcart, sh->H, (long long)sh->P, red, st))) return rc;
+  double h[2];
+  CF_CUDA(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CF_CUDA(cudaStreamSynchronize(st));
+  out[0] = sqrt(h[0] / (30.0 * sh->P));
+  out[1] = sqrt(h[1] / (4.0 * sh->P));
+  return CFFYN_OK;
+}
+
+int cffyn_get_filter_matrix(const cffyn_shell* sh, int n, int m, double* host_out) {
+  if (!sh || !host_out) { set_error("NULL argument"); return CFFYN_EINVAL; }
+  if (n < -3 || n > 3 || m < 0 || m > sh->L) {
+    set_error("n must be in [-3,3] and m in [0,L]");
+    return CFFYN_EINVAL;
+  }
+  const size_t per = (size_t)sh->N * sh->N;
+  CF_CUDA(cudaMemcpy(host_out, sh->Fraw + ((size_t)(n + 3) * (sh->L + 1) + m) * per, per * sizeof(double),
+                     cudaMemcpyDeviceToHost));
+  return CFFYN_OK;
+}
+
+int cffyn_get_operator(const cffyn_shell* sh, int which, double* host_out) {
+  if (!sh || !host_out) { set_error("NULL argument"); return CFFYN_EINVAL; }
+  if (which == 0) {
+    CF_CUDA(cudaMemcpy(host_out, sh->Dr, (size_t)sh->n_r * sh->n_r * sizeof(double), cudaMemcpyDeviceToHost));
+  } else if (which == 1) {
+    // top N rows of the 2N x 2N pair operator
+    CF_CUDA(cudaMemcpy(host_out, sh->Dth2, (size_t)sh->N * 2 * sh->N * sizeof(double), cudaMemcpyDeviceToHost));
+  } else if (which == 2) {
+    CF_CUDA(cudaMemcpy(host_out, sh->Dph, (size_t)sh->J * sh->J * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    set_error("which must be 0, 1 or 2");
+    return CFFYN_EINVAL;
+  }
+  return CFFYN_OK;
+}
+
+int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, int* launches_out,
+                       void* stream) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u"))) return rc;
+  if (!ms_out || !launches_out) { set_error("outputs are NULL"); return CFFYN_EINVAL; }
+  if (sh->nv == 50 && !sh->gauge_set) { set_error("gauge source not set"); return CFFYN_EINVAL; }
+  if (!(dt > 0)) dt = sh->dt_default;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  const size_t P = sh->P;
+  const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
+  cudaEvent_t ev[2];
+  CF_CUDA(cudaEventCreate(&ev[0]));
+  CF_CUDA(cudaEventCreate(&ev[1]));
+  for (int k = 0; k < CFFYN_PROFILE_PHASES; ++k) {
+    ms_out[k] = 0.0;
+    launches_out[k] = 0;
+  }
+  auto phase = [&](int k, auto&& fn) -> int {
+    long long l0 = g_launches;
+    cudaEventRecord(ev[0], st);
+    int r = fn();
+    cudaEventRecord(ev[1], st);
+    if (r) return r;
+    if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
+      set_error("profiling: %s", cudaGetErrorString(cudaGetLastError()));
+      return CFFYN_ECUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ms_out[k] += ms;
+    launches_out[k] += (int)(g_launches - l0);
+    return CFFYN_OK;
+  };
+  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
+  for (int s = 0; s < 4 && !rc; ++s) {
+    const double* X = s == 0 ? u : sh->U;
+    double* spin = sh->D + 2 * nvP;
+    if ((rc = phase(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, st); }))) break;
+    if ((rc = phase(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, st); }))) break;
+    if ((rc = phase(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, st); }))) break;
+    if ((rc = phase(3, [&] { return pw_rhs(sh, X, sh->D, sh->S, st); }))) break;
+    if (per_sub) {
+      if ((rc = phase(4, [&] { return pw_decompose(sh, sh->S, spin, st); }))) break;
+      if ((rc = phase(5, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) break;
+      if ((rc = phase(6, [&] {
+             return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
+           })))
+        break;
+      if ((rc = phase(7, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) break;
+      if ((rc = phase(8, [&] {
+             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+           })))
+        break;
+    } else {
+      if ((rc = phase(8, [&] {
+             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+           })))
+        break;
+    }
+  }
+  if (!rc && !per_sub) {
+    rc = phase(4, [&] { return pw_decompose(sh, u, sh->S, st); });
+    if (!rc) rc = phase(5, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); });
+    if (!rc)
+      rc = phase(6, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); });
+    if (!rc) rc = phase(7, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); });
+    if (!rc)
+      rc = phase(8, [&] {
+        return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+      });
+  }
+  (void)P;
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal definitions of the cffyn library: the shell handle, the operator
+// descriptors shared by the FP64 and the split-precision kernels, and error
+// plumbing.  Not part of the public ABI (see include/cffyn.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cffyn.h"
+
+namespace cffyn {
+
+constexpr int kMaxN = 96;      // n_theta limit (N_phi <= 192)
+constexpr int kMaxNr = 96;     // n_r limit
+constexpr int kNumSpinFns = 50;
+
+// Number of split-precision digits per operand (8-bit balanced digits of a
+// 47-bit fixed-point value) and the highest digit-sum kept (pairs i + j <= D).
+constexpr int kSlices = 6;
+
+// Thread-local error message.
+void set_error(const char* fmt, ...);
+// Kernel launches issued by this thread (for the launch counts reported by
+// the profiling entry point).
+void count_launch();
+#define CF_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      ::cffyn::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                \
+                         cudaGetErrorString(e_));                                  \
+      return CFFYN_ECUDA;                                                          \
+    }                                                                              \
+  } while (0)
+
+// --------------------------------------------------------------------------
+// Spin-function layout of the filter (one real slot per Cartesian field).
+// Slots [0, 16): real functions filtered with F^0_m (spin 0, including the
+// real and imaginary parts of the two complex spin-0 components); then
+// complex functions as (re, im) slot pairs: 11 of spin 1 from slot 16, 5 of
+// spin 2 from slot 38, 1 of spin 3 at slot 48.  Gauge groups of 54/58-field
+// states append: H_t (real), H_r (real), H_m (spin 1) per group, stored after
+// slot 50 as [R0 R0 re im] per group.
+struct SpinLayout {
+  int n_real;         // number of real spin-0 slots
+  int n_cplx[4];      // complex pairs per spin 0..3 (spin 0 pairs are counted as reals)
+  int cplx_base[4];   // first slot of each spin class
+};
+
+// --------------------------------------------------------------------------
+// Split-precision (Ozaki-style) operator: digits of every row in the
+// mma.m16n8k16 A-fragment order, plus per-row binary exponents.
+struct SlicedOp {
+  uint4* frag = nullptr;  // [batch][slice][mtile][kstep][lane] -> 4 x bf16x2
+  int* rowexp = nullptr;  // [batch][P_pad]
+  int P = 0, K = 0, mtiles = 0, ksteps = 0, nbatch = 1;
+  size_t frag_stride = 0, rowexp_stride = 0;  // per batch
+};
+
+struct cffyn_shell_impl;
+
+}  // namespace cffyn
+
+struct cffyn_shell {
+  cffyn_shell_desc d;
+  int n_r, N, J, L, nv, R;      // R = 2L + 1 Fourier rows kept
+  size_t P;                     // points per field
+  double dt_default;
+  size_t bytes = 0;
+  int device = 0;
+
+  // grid (device)
+  double *r = nullptr, *sth = nullptr, *cth = nullptr, *sph = nullptr, *cph = nullptr;
+
+  // FP64 operators (device, row-major)
+  double* Dr = nullptr;     // n_r x n_r
+  double* Dth2 = nullptr;   // 2N x 2N (paired planes j, j + J/2)
+  double* Dph = nullptr;    // J x J
+  double* Fan = nullptr;    // R x J   analysis rows a_0..a_L, b_1..b_L
+  double* Fsy = nullptr;    // J x R   synthesis
+  double* Fraw = nullptr;   // [7][L+1] N x N : F^n_m, n = -3..3
+  double* Fproj0 = nullptr; // [L+1] N x N : F^0_m
+  double* FprojC = nullptr; // [3][L+1] N x 2N : [F_s | F_d] for spin 1..3
+
+  // split-precision operators
+  cffyn::SlicedOp sDr, sDth2, sDph, sFan, sFsy;
+  cffyn::SlicedOp sF0;       // batched over m = 0..L
+  cffyn::SlicedOp sFC[3];    // per spin 1..3, batched over m
+
+  cffyn::SpinLayout spin;
+
+  // gauge
+  double* H = nullptr;    // [4][P]
+  double* dH = nullptr;   // [3][4][P]
+  bool gauge_set = false;
+
+  // workspace
+  double* U = nullptr;     // stage state [nv][P]
+  double* kacc = nullptr;  // RK4 accumulator [nv][P]
+  double* D = nullptr;     // spherical derivatives [3][nv][P] (also DFT coefficients)
+  double* S = nullptr;     // rhs / spin functions [nv][P]
+  double* red = nullptr;   // device reduction words (2 doubles)
+  int* flag = nullptr;     // device non-finite flag
+  int* flag_host = nullptr;  // pinned host copy of the flag
+  int* slots = nullptr;    // device slot lists: R0 (16) | C1 (11) | C2 (5) | C3 (1)
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+
+  // graph of one RK4 step
+  cudaGraphExec_t graph = nullptr;
+  double* graph_u = nullptr;
+  double graph_dt = 0.0;
+  cudaStream_t graph_stream = nullptr;
+};

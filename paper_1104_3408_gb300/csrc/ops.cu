@@ -1,0 +1,544 @@
+// Dense operator applications of the hot path: every derivative (paper Sec.
+// 2.4, eqs. D1, D2, D3, with the theta double cover of Sec. 2.1) and every
+// matrix of the Yn filter (Sec. 3.5: phi DFT of eq. forwardF, projection of
+// eq. FasPfQ, inverse DFT of eq. backwardF) is a product
+//     Out[:, c] = W (P x K) * In[:, c]
+// of a small operator W with many columns c.  Each column has its own gather
+// of K input rows (two segments, the second optionally reversed and signed:
+// the theta double cover and the complex spin projection) and its own scatter
+// of P output rows (two segments).  No transposes are materialised.
+//
+// Two arithmetic cores share the tiling and the gathers:
+//   FP64   plain double FMA on CUDA cores (the reference path);
+//   MIXED  split-precision products on the tensor cores: W and each input
+//          column are written as 47-bit fixed-point integers relative to a
+//          per-row / per-column power of two and cut into six balanced 8-bit
+//          digits held exactly in BF16; digit products i + j = d are summed by
+//          mma.sync m16n8k16 in FP32, where they are exact integers (at most
+//          6 * 96 * 2^14 < 2^24), and folded into a 64-bit integer with weight
+//          256^(5-d); pairs with i + j > 5 are dropped (relative truncation
+//          about 6 * 2^-48 of |W| |x| K).  The result is rebuilt as an FP64
+//          number with integer operations only (this part's FP64 and
+//          conversion pipes are narrow).
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace cffyn {
+
+// ---------------------------------------------------------------------------
+// Column descriptors
+
+struct ColDesc {
+  long long in0, in1, out0, out1;  // base offsets of the two row segments
+  float sign1;                     // sign of the second input segment
+  int valid;
+};
+
+struct OpGeom {
+  int K, K0, P, P0;     // rows of W's columns (K), split of the input gather (K0),
+                        // rows of W (P), split of the output scatter (P0)
+  int in_rs, out_rs;    // row strides of input / output
+  int rev1;             // second input segment reversed (row k -> K-1-k+K0... see load)
+  long long ncols;
+};
+
+// All operators used by the shell, as one tagged descriptor.
+enum OpKind : int { OP_R = 0, OP_ROWS = 1, OP_THETA = 2, OP_PROJ0 = 3, OP_PROJC = 4 };
+
+struct OpArgs {
+  OpKind kind;
+  OpGeom g;
+  const double* in;
+  double* out;
+  // OP_ROWS
+  int Q;
+  long long in_bs, out_bs;
+  // OP_THETA / projections
+  int n_r, N, J, R, L;
+  int m;                 // projection: azimuthal number (set per block from blockIdx)
+  const int* slots;      // projection: list of slots (R0: functions; C: re-slots of pairs)
+  int nslots;
+  int batched_m;         // projection launched for all m = 0..L at once
+  long long w_stride;    // FP64 operator stride between consecutive m
+};
+
+__device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
+  ColDesc d;
+  d.valid = c < a.g.ncols;
+  d.sign1 = 1.0f;
+  if (!d.valid) c = 0;
+  switch (a.kind) {
+    case OP_R: {
+      d.in0 = c * a.n_r;
+      d.out0 = d.in0;
+      d.in1 = d.out1 = 0;
+      break;
+    }
+    case OP_ROWS: {
+      long long b = c / a.Q, q = c - b * a.Q;
+      d.in0 = b * a.in_bs + q;
+      d.out0 = b * a.out_bs + q;
+      d.in1 = d.out1 = 0;
+      break;
+    }
+    case OP_THETA: {
+      long long pb = c / a.n_r;
+      int kr = (int)(c - pb * a.n_r);
+      int half = a.J / 2;
+      long long mu = pb / half;
+      int jp = (int)(pb - mu * half);
+      d.in0 = ((mu * a.J + jp) * a.N) * a.n_r + kr;
+      d.in1 = ((mu * a.J + jp + half) * a.N) * a.n_r + kr;
+      d.out0 = d.in0;
+      d.out1 = d.in1;
+      break;
+    }
+    case OP_PROJ0: {
+      // columns: (slot index, part, kr); parts: a (row m) and b (row L+m, m >= 1)
+      int nparts = a.m == 0 ? 1 : 2;
+      long long per = (long long)nparts * a.n_r;
+      if (c >= per * a.nslots) { d.valid = 0; c = 0; }
+      long long fi = c / per;
+      int rem = (int)(c - fi * per);
+      int part = rem / a.n_r, kr = rem - part * a.n_r;
+      int f = a.slots[fi < a.nslots ? fi : 0];
+      int row = part == 0 ? a.m : a.L + a.m;
+      d.in0 = (((long long)f * a.R + row) * a.N) * a.n_r + kr;
+      d.out0 = d.in0;
+      d.in1 = d.out1 = 0;
+      break;
+    }
+    case OP_PROJC: {
+      // columns: (pair, output part, kr); parts aR, aI, bR, bI (m >= 1) or aR, aI
+      int nparts = a.m == 0 ? 2 : 4;
+      long long per = (long long)nparts * a.n_r;
+      if (c >= per * a.nslots) { d.valid = 0; c = 0; }
+      long long pi = c / per;
+      int rem = (int)(c - pi * per);
+      int part = rem / a.n_r, kr = rem - part * a.n_r;
+      int fre = a.slots[pi < a.nslots ? pi : 0], fim = fre + 1;
+      int ra = a.m, rb = a.L + a.m;
+      auto base = [&](int f, int row) {
+        return (((long long)f * a.R + row) * a.N) * a.n_r + kr;
+      };
+      long long aR = base(fre, ra), aI = base(fim, ra);
+      long long bR = a.m ? base(fre, rb) : aR, bI = a.m ? base(fim, rb) : aI;
+      float s0 = a.m ? 1.0f : 0.0f;
+      switch (part) {
+        case 0: d.in0 = aR; d.in1 = bI; d.sign1 = s0; d.out0 = aR; break;
+        case 1: d.in0 = aI; d.in1 = bR; d.sign1 = -s0; d.out0 = aI; break;
+        case 2: d.in0 = bR; d.in1 = aI; d.sign1 = -s0; d.out0 = bR; break;
+        default: d.in0 = bI; d.in1 = aR; d.sign1 = s0; d.out0 = bI; break;
+      }
+      d.out1 = 0;
+      break;
+    }
+  }
+  return d;
+}
+
+__device__ __forceinline__ double load_elem(const OpArgs& a, const ColDesc& d, int k) {
+  if (!d.valid || k >= a.g.K) return 0.0;
+  if (k < a.g.K0) return __ldg(a.in + d.in0 + (long long)k * a.g.in_rs);
+  int kk = a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0);
+  double v = __ldg(a.in + d.in1 + (long long)kk * a.g.in_rs);
+  return d.sign1 == 1.0f ? v : (d.sign1 == -1.0f ? -v : 0.0);
+}
+
+__device__ __forceinline__ void store_elem(const OpArgs& a, const ColDesc& d, int p, double v) {
+  if (!d.valid || p >= a.g.P) return;
+  if (p < a.g.P0)
+    a.out[d.out0 + (long long)p * a.g.out_rs] = v;
+  else
+    a.out[d.out1 + (long long)(p - a.g.P0) * a.g.out_rs] = v;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 core: CTA tile = PT rows x QT columns, whole K staged in shared memory.
+
+constexpr int F64_QT = 32;
+constexpr int F64_PT = 64;
+
+__global__ void __launch_bounds__(256) k_op_fp64(OpArgs a, const double* __restrict__ W) {
+  extern __shared__ double sm64[];
+  if (a.batched_m) {
+    a.m = blockIdx.z;
+    W += (size_t)a.m * a.w_stride;
+  }
+  const int K = a.g.K, P = a.g.P;
+  const int p0 = blockIdx.y * F64_PT;
+  const int PT = min(F64_PT, P - p0);
+  double* Ws = sm64;                 // PT x K
+  double* Xs = sm64 + F64_PT * K;    // K x QT
+  __shared__ ColDesc cols[F64_QT];
+  const long long c0 = (long long)blockIdx.x * F64_QT;
+  const int tid = threadIdx.x;
+  if (tid < F64_QT) cols[tid] = make_col(a, c0 + tid);
+  for (int e = tid; e < PT * K; e += 256) Ws[e] = W[(size_t)(p0 + e / K) * K + (e % K)];
+  __syncthreads();
+  const bool kfast = a.kind == OP_R;
+  for (int e = tid; e < K * F64_QT; e += 256) {
+    int k, c;
+    if (kfast) { k = e % K; c = e / K; } else { c = e % F64_QT; k = e / F64_QT; }
+    Xs[k * F64_QT + c] = load_elem(a, cols[c], k);
+  }
+  __syncthreads();
+  const int tq = tid % F64_QT, tp = tid / F64_QT;  // 8 row groups
+  double acc[F64_PT / 8];
+#pragma unroll
+  for (int r = 0; r < F64_PT / 8; ++r) acc[r] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    double x = Xs[k * F64_QT + tq];
+#pragma unroll
+    for (int r = 0; r < F64_PT / 8; ++r) {
+      int row = tp + 8 * r;
+      if (row < PT) acc[r] = fma(Ws[row * K + k], x, acc[r]);
+    }
+  }
+  if (kfast) {
+    // transpose through shared memory so that stores run along p
+    __syncthreads();
+    double* Os = Xs;  // reuse: PT x QT
+#pragma unroll
+    for (int r = 0; r < F64_PT / 8; ++r) {
+      int row = tp + 8 * r;
+      if (row < PT) Os[row * F64_QT + tq] = acc[r];
+    }
+    __syncthreads();
+    for (int e = tid; e < PT * F64_QT; e += 256) {
+      int p = e % PT, c = e / PT;
+      store_elem(a, cols[c], p0 + p, Os[p * F64_QT + c]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < F64_PT / 8; ++r) {
+      int row = tp + 8 * r;
+      if (row < PT) store_elem(a, cols[tq], p0 + row, acc[r]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split-precision core.
+
+constexpr int OZ_QT = 32;        // columns per CTA (4 n-tiles of 8)
+constexpr int OZ_NT = OZ_QT / 8;
+constexpr int OZ_MAXK = 192;
+constexpr int OZ_KCHUNK = 6;     // k-steps (of 16) per exact partial sum
+
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+// 47-bit fixed point of x relative to 2^E, cut into six balanced base-256
+// digits (d0 most significant), each returned as BF16 bits.
+__device__ __forceinline__ void digits_bf16(double x, int E, unsigned short out[kSlices]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  long long Z = 0;
+  if (e != 0) {
+    const unsigned long long M = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    const int sh = 1028 + E - e;  // >= 6 because |x| < 2^E
+    if (sh < 54) Z = (long long)((M + (1ull << (sh - 1))) >> sh);
+    if (b >> 63) Z = -Z;
+  }
+#pragma unroll
+  for (int i = kSlices - 1; i >= 1; --i) {
+    int lo = (int)(Z & 255);
+    lo = lo >= 128 ? lo - 256 : lo;
+    Z = (Z - lo) >> 8;
+    float f = __int_as_float(0x4B400000 + lo) - 12582912.0f;  // exact small integer
+    out[i] = (unsigned short)(__float_as_uint(f) >> 16);
+  }
+  float f0 = __int_as_float(0x4B400000 + (int)Z) - 12582912.0f;
+  out[0] = (unsigned short)(__float_as_uint(f0) >> 16);
+}
+
+// FP32 value holding an exact integer |v| < 2^24 -> int, integer ops only.
+__device__ __forceinline__ int f32_int_exact(float v) {
+  const unsigned int u = __float_as_uint(v);
+  const int e = (int)((u >> 23) & 0xff);
+  const int m = (int)((u & 0x7fffff) | 0x800000);
+  const int sh = 150 - e;
+  int r = (sh < 32 && e != 0) ? (m >> sh) : 0;
+  return (u >> 31) ? -r : r;
+}
+
+// T * 2^sc as a double (round to nearest), integer ops only.
+__device__ __forceinline__ double i64_scaled_to_double(long long T, int sc) {
+  if (T == 0) return 0.0;
+  const unsigned long long s = T < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long v = T < 0 ? (unsigned long long)(-T) : (unsigned long long)T;
+  const int nb = 64 - __clzll((long long)v);
+  int ex = nb - 1 + sc;
+  unsigned long long m;
+  if (nb > 53) {
+    const int sh = nb - 53;
+    m = (v + (1ull << (sh - 1))) >> sh;
+    if (m >> 53) {
+      m >>= 1;
+      ex += 1;
+    }
+  } else {
+    m = v << (53 - nb);
+  }
+  if (ex + 1023 <= 0) return 0.0;
+  const unsigned long long bits = s | ((unsigned long long)(ex + 1023) << 52) | (m & 0x000fffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint4& a, unsigned int b0, unsigned int b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// CTA: one warp per m-tile of W (mtiles warps), OZ_QT columns.
+__global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
+  extern __shared__ unsigned short smoz[];
+  if (a.batched_m) {
+    a.m = blockIdx.y;
+    W.frag += (size_t)a.m * W.frag_stride;
+    W.rowexp += (size_t)a.m * W.rowexp_stride;
+  }
+  const int K = a.g.K;
+  const int ksteps = W.ksteps;
+  const int KP = ksteps * 16 + 8;                    // row pitch (halfwords), odd multiple of 8
+  unsigned short* Bs = smoz;                         // [kSlices][OZ_QT][KP]
+  __shared__ ColDesc cols[OZ_QT];
+  __shared__ int colE[OZ_QT];
+  const long long c0 = (long long)blockIdx.x * OZ_QT;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid < OZ_QT) {
+    cols[tid] = make_col(a, c0 + tid);
+    colE[tid] = -100000;
+  }
+  __syncthreads();
+  const bool kfast = a.kind == OP_R;
+  const int Kp = ksteps * 16;
+  // pass 1: column exponents
+  for (int e = tid; e < K * OZ_QT; e += nthr) {
+    int k, c;
+    if (kfast) { k = e % K; c = e / K; } else { c = e % OZ_QT; k = e / OZ_QT; }
+    double v = load_elem(a, cols[c], k);
+    if (v != 0.0) atomicMax(&colE[c], exp_field(v) - 1022);
+  }
+  __syncthreads();
+  // pass 2: digits (re-read: the tile is L1/L2 resident)
+  for (int e = tid; e < Kp * OZ_QT; e += nthr) {
+    int k, c;
+    if (kfast) { k = e % Kp; c = e / Kp; } else { c = e % OZ_QT; k = e / OZ_QT; }
+    double v = k < K ? load_elem(a, cols[c], k) : 0.0;
+    unsigned short dg[kSlices];
+    digits_bf16(v, colE[c], dg);
+#pragma unroll
+    for (int s = 0; s < kSlices; ++s) Bs[((size_t)s * OZ_QT + c) * KP + k] = dg[s];
+  }
+  __syncthreads();
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  const int mt = warp;
+  if (mt >= W.mtiles) return;
+  long long T[OZ_NT][4];
+#pragma unroll
+  for (int n = 0; n < OZ_NT; ++n)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) T[n][q] = 0;
+
+  for (int d = 0; d < kSlices; ++d) {
+    for (int kc = 0; kc < ksteps; kc += OZ_KCHUNK) {
+      const int kend = min(ksteps, kc + OZ_KCHUNK);
+      float acc[OZ_NT][4];
+#pragma unroll
+      for (int n = 0; n < OZ_NT; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
+      for (int i = 0; i <= d; ++i) {
+        const int j = d - i;
+        const uint4* Af = W.frag + ((size_t)(i * W.mtiles + mt) * ksteps) * 32 + lane;
+        const unsigned short* Bj = Bs + (size_t)j * OZ_QT * KP;
+        for (int ks = kc; ks < kend; ++ks) {
+          const uint4 af = __ldg(Af + (size_t)ks * 32);
+#pragma unroll
+          for (int n = 0; n < OZ_NT; ++n) {
+            const unsigned short* col = Bj + (size_t)(n * 8 + g) * KP + ks * 16 + 2 * tg;
+            const unsigned int b0 = *reinterpret_cast<const unsigned int*>(col);
+            const unsigned int b1 = *reinterpret_cast<const unsigned int*>(col + 8);
+            mma_bf16(acc[n], af, b0, b1);
+          }
+        }
+      }
+      const int shift = 8 * (kSlices - 1 - d);
+#pragma unroll
+      for (int n = 0; n < OZ_NT; ++n)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) T[n][q] += ((long long)f32_int_exact(acc[n][q])) << shift;
+    }
+  }
+  // epilogue: rows mt*16 + g (+8), columns n*8 + 2tg (+1)
+  const int rowA = mt * 16 + g, rowB = rowA + 8;
+  const int eA = W.rowexp[rowA], eB = W.rowexp[rowB];
+#pragma unroll
+  for (int n = 0; n < OZ_NT; ++n) {
+    const int cA = n * 8 + 2 * tg, cB = cA + 1;
+    const int sA = colE[cA], sB = colE[cB];
+    const double v0 = i64_scaled_to_double(T[n][0], eA + sA - 54);
+    const double v1 = i64_scaled_to_double(T[n][1], eA + sB - 54);
+    const double v2 = i64_scaled_to_double(T[n][2], eB + sA - 54);
+    const double v3 = i64_scaled_to_double(T[n][3], eB + sB - 54);
+    store_elem(a, cols[cA], rowA, v0);
+    store_elem(a, cols[cB], rowA, v1);
+    store_elem(a, cols[cA], rowB, v2);
+    store_elem(a, cols[cB], rowB, v3);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const SlicedOp* Ws,
+                  dim3 extra, cudaStream_t st) {
+  if (a.g.ncols <= 0) return CFFYN_OK;
+  if (sh->d.precision == CFFYN_FP64 || Ws == nullptr) {
+    unsigned gx = (unsigned)((a.g.ncols + F64_QT - 1) / F64_QT);
+    unsigned gy = (unsigned)((a.g.P + F64_PT - 1) / F64_PT);
+    size_t smem = (size_t)(F64_PT * a.g.K + a.g.K * F64_QT) * sizeof(double);
+    k_op_fp64<<<dim3(gx, gy, extra.y), 256, smem, st>>>(a, W64);
+    count_launch();
+  } else {
+    unsigned gx = (unsigned)((a.g.ncols + OZ_QT - 1) / OZ_QT);
+    int KP = Ws->ksteps * 16 + 8;
+    size_t smem = (size_t)kSlices * OZ_QT * KP * sizeof(unsigned short);
+    int threads = Ws->mtiles * 32;
+    k_op_ozaki<<<dim3(gx, extra.y), threads, smem, st>>>(a, *Ws);
+    count_launch();
+  }
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+int set_op_smem_limits() {
+  CF_CUDA(cudaFuncSetAttribute(k_op_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  return CFFYN_OK;
+}
+
+static OpArgs base_args(const cffyn_shell* sh) {
+  OpArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_r = sh->n_r;
+  a.N = sh->N;
+  a.J = sh->J;
+  a.R = sh->R;
+  a.L = sh->L;
+  return a;
+}
+
+// d_r of nfields fields: in/out [nfields][P]
+int op_deriv_r(const cffyn_shell* sh, const double* in, double* out, int nfields, cudaStream_t st) {
+  OpArgs a = base_args(sh);
+  a.kind = OP_R;
+  a.in = in;
+  a.out = out;
+  a.g.K = a.g.K0 = a.g.P = a.g.P0 = sh->n_r;
+  a.g.in_rs = a.g.out_rs = 1;
+  a.g.ncols = (long long)nfields * sh->J * sh->N;
+  return launch(sh, a, sh->Dr, &sh->sDr, dim3(1, 1), st);
+}
+
+int op_deriv_theta(const cffyn_shell* sh, const double* in, double* out, int nfields,
+                   cudaStream_t st) {
+  OpArgs a = base_args(sh);
+  a.kind = OP_THETA;
+  a.in = in;
+  a.out = out;
+  a.g.K = a.g.P = 2 * sh->N;
+  a.g.K0 = a.g.P0 = sh->N;
+  a.g.rev1 = 1;
+  a.g.in_rs = a.g.out_rs = sh->n_r;
+  a.g.ncols = (long long)nfields * (sh->J / 2) * sh->n_r;
+  return launch(sh, a, sh->Dth2, &sh->sDth2, dim3(1, 1), st);
+}
+
+static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb, int K, int P,
+                   long long in_bs, long long out_bs, const double* W, const SlicedOp* Ws,
+                   cudaStream_t st) {
+  OpArgs a = base_args(sh);
+  a.kind = OP_ROWS;
+  a.in = in;
+  a.out = out;
+  a.Q = sh->N * sh->n_r;
+  a.in_bs = in_bs;
+  a.out_bs = out_bs;
+  a.g.K = a.g.K0 = K;
+  a.g.P = a.g.P0 = P;
+  a.g.in_rs = a.g.out_rs = a.Q;
+  a.g.ncols = (long long)nb * a.Q;
+  return launch(sh, a, W, Ws, dim3(1, 1), st);
+}
+
+int op_deriv_phi(const cffyn_shell* sh, const double* in, double* out, int nfields, cudaStream_t st) {
+  long long bs = (long long)sh->P;
+  return op_rows(sh, in, out, nfields, sh->J, sh->J, bs, bs, sh->Dph, &sh->sDph, st);
+}
+
+// phi analysis: S[f][j][i][k] -> C[f][row][i][k]
+int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
+  long long Q = (long long)sh->N * sh->n_r;
+  return op_rows(sh, in, out, nf, sh->J, sh->R, (long long)sh->J * Q, (long long)sh->R * Q, sh->Fan,
+                 &sh->sFan, st);
+}
+
+int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
+  long long Q = (long long)sh->N * sh->n_r;
+  return op_rows(sh, in, out, nf, sh->R, sh->J, (long long)sh->R * Q, (long long)sh->J * Q, sh->Fsy,
+                 &sh->sFsy, st);
+}
+
+// Projection of all spin classes, coefficients C -> C2 (same layout); one
+// launch per class covering every m = 0..L.
+int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* slots_r0, int n_r0,
+               const int* const slots_c[3], const int n_c[3], cudaStream_t st) {
+  const int N = sh->N;
+  const int nm = sh->L + 1;
+  if (n_r0 > 0) {
+    OpArgs a = base_args(sh);
+    a.in = C;
+    a.out = C2;
+    a.kind = OP_PROJ0;
+    a.slots = slots_r0;
+    a.nslots = n_r0;
+    a.batched_m = 1;
+    a.w_stride = (long long)N * N;
+    a.g.K = a.g.K0 = a.g.P = a.g.P0 = N;
+    a.g.in_rs = a.g.out_rs = sh->n_r;
+    a.g.ncols = (long long)n_r0 * 2 * sh->n_r;
+    int rc = launch(sh, a, sh->Fproj0, &sh->sF0, dim3(1, nm), st);
+    if (rc) return rc;
+  }
+  for (int s = 0; s < 3; ++s) {
+    if (n_c[s] <= 0) continue;
+    OpArgs b = base_args(sh);
+    b.in = C;
+    b.out = C2;
+    b.kind = OP_PROJC;
+    b.slots = slots_c[s];
+    b.nslots = n_c[s];
+    b.batched_m = 1;
+    b.w_stride = (long long)N * 2 * N;
+    b.g.K = 2 * N;
+    b.g.K0 = N;
+    b.g.P = b.g.P0 = N;
+    b.g.in_rs = b.g.out_rs = sh->n_r;
+    b.g.ncols = (long long)n_c[s] * 4 * sh->n_r;
+    int rc = launch(sh, b, sh->FprojC + (size_t)s * nm * N * 2 * N, &sh->sFC[s], dim3(1, nm), st);
+    if (rc) return rc;
+  }
+  return CFFYN_OK;
+}
+
+}  // namespace cffyn

@@ -1,0 +1,953 @@
+// Pointwise kernels of the hot path, templated on the arithmetic type
+// (double for the FP64 path, ff = FP32 pair for the mixed path):
+//
+//   k_rhs          Cartesian derivatives by the chain rule (eq. dvdx), the
+//                  first-order GHG right-hand side (App. A.1 eqs. gdot, Phidot,
+//                  Pidot, dependent quantities from eqs. normal, abgfromgab,
+//                  Gamma) and the freeze-incoming boundary condition on the
+//                  outermost sphere (App. A.2, B = E^-1 Z E).
+//   k_decompose    Cartesian tensor groups -> spin-weighted components
+//                  (Sec. 3.4, eq. tensorexpansion) written as real multiples of
+//                  the triad components: every tensor is first rotated to the
+//                  real orthonormal triad (r, theta, phi) of eq. tetrad, then
+//                  combined with constant coefficients into the m / mbar
+//                  contractions (m = (theta + i phi)/sqrt 2).  A component with
+//                  p legs on m and q legs on mbar has spin p - q.
+//   k_reconstruct  the inverse map, fused with the RK4 stage update (Sec. 2.5)
+//                  or writing the filtered tensor.
+//   k_cart         spherical -> Cartesian derivatives (chain rule only).
+//   k_gauge        H_a = -Gamma_a (eq. gauge).
+//   k_constraints  sums of squares of C_iab = d_i g_ab - Phi_iab and
+//                  C_a = H_a + Gamma_a (App. A.1).
+#include <cstdio>
+
+#include "common.cuh"
+#include "scalar.cuh"
+
+namespace cffyn {
+
+struct Geo {
+  int n_r, N, J, nv;
+  long long P;
+  const double *r, *sth, *cth, *sph, *cph;
+};
+
+// symmetric pair index of (a, b), a, b in 0..3 (tt,tx,ty,tz,xx,xy,xz,yy,yz,zz)
+__host__ __device__ constexpr int SI(int a, int b) {
+  return a > b ? SI(b, a) : (a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9)));
+}
+
+template <class T>
+struct Jac {
+  // d/dx^k = J[k][0] d_r + J[k][1] d_theta + J[k][2] d_phi
+  T j[3][3];
+  T st, ct, sp, cp;
+};
+
+template <class T>
+__device__ __forceinline__ Jac<T> jacobian(const Geo& g, int k, int i, int jj) {
+  Jac<T> J;
+  const T st = S<T>::c(g.sth[i]), ct = S<T>::c(g.cth[i]);
+  const T sp = S<T>::c(g.sph[jj]), cp = S<T>::c(g.cph[jj]);
+  const T one = S<T>::c(1.0);
+  const T ir = one / S<T>::c(g.r[k]);
+  const T irs = ir / st;
+  J.j[0][0] = st * cp; J.j[0][1] = ct * cp * ir; J.j[0][2] = -(sp * irs);
+  J.j[1][0] = st * sp; J.j[1][1] = ct * sp * ir; J.j[1][2] = cp * irs;
+  J.j[2][0] = ct;      J.j[2][1] = -(st * ir);   J.j[2][2] = S<T>::c(0.0);
+  J.st = st; J.ct = ct; J.sp = sp; J.cp = cp;
+  return J;
+}
+
+// Cartesian derivative d_k of field mu at point p from the three spherical
+// derivative arrays D[3][nv][P].
+template <class T>
+__device__ __forceinline__ void cart3(const Jac<T>& J, const double* __restrict__ D, long long P,
+                                      int nv, int mu, long long p, T out[3]) {
+  const T dr = S<T>::load(D + (long long)mu * P + p);
+  const T dt = S<T>::load(D + ((long long)nv + mu) * P + p);
+  const T dp = S<T>::load(D + ((long long)2 * nv + mu) * P + p);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) out[k] = J.j[k][0] * dr + J.j[k][1] * dt + J.j[k][2] * dp;
+}
+
+// 3+1 quantities and Christoffel symbols from the undifferentiated fields.
+template <class T>
+struct Metric {
+  T gi4[10];          // g^ab (symmetric pairs)
+  T gi[3][3];         // gamma^ij
+  T bu[3];            // beta^i
+  T alpha, ialpha;
+  T nu[4];            // n^a
+};
+
+template <class T>
+__device__ __forceinline__ void metric_from(const T g[10], Metric<T>& M) {
+  const T gxx = g[4], gxy = g[5], gxz = g[6], gyy = g[7], gyz = g[8], gzz = g[9];
+  const T cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
+  const T cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
+  const T idet = S<T>::c(1.0) / (gxx * cxx + gxy * cxy + gxz * cxz);
+  M.gi[0][0] = cxx * idet; M.gi[0][1] = M.gi[1][0] = cxy * idet; M.gi[0][2] = M.gi[2][0] = cxz * idet;
+  M.gi[1][1] = cyy * idet; M.gi[1][2] = M.gi[2][1] = cyz * idet; M.gi[2][2] = czz * idet;
+  const T b[3] = {g[1], g[2], g[3]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) M.bu[i] = M.gi[i][0] * b[0] + M.gi[i][1] * b[1] + M.gi[i][2] * b[2];
+  const T a2 = b[0] * M.bu[0] + b[1] * M.bu[1] + b[2] * M.bu[2] - g[0];
+  M.alpha = sqrt_s(a2);
+  M.ialpha = S<T>::c(1.0) / M.alpha;
+  const T ia2 = M.ialpha * M.ialpha;
+  M.nu[0] = M.ialpha;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) M.nu[i + 1] = -(M.bu[i] * M.ialpha);
+  M.gi4[0] = -ia2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) M.gi4[SI(0, i + 1)] = M.bu[i] * ia2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) M.gi4[SI(i + 1, j + 1)] = M.gi[i][j] - M.bu[i] * M.bu[j] * ia2;
+}
+
+// dg4[c][s] = d_c g_ab; Gam[c][s] = Gamma_cab; Gc[c] = Gamma_c
+template <class T>
+__device__ __forceinline__ void christoffel(const Metric<T>& M, const T Pi[10], const T Ph[3][10],
+                                            T dg4[4][10], T Gam[4][10], T Gc[4]) {
+#pragma unroll
+  for (int s = 0; s < 10; ++s) {
+    dg4[0][s] = M.bu[0] * Ph[0][s] + M.bu[1] * Ph[1][s] + M.bu[2] * Ph[2][s] - M.alpha * Pi[s];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dg4[i + 1][s] = Ph[i][s];
+  }
+  const T half = S<T>::c(0.5);
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b)
+        Gam[c][SI(a, b)] = half * (dg4[a][SI(b, c)] + dg4[b][SI(a, c)] - dg4[c][SI(a, b)]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T acc = S<T>::c(0.0);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc = acc + M.gi4[SI(a, b)] * Gam[c][SI(a, b)];
+    Gc[c] = acc;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_rhs(const double* __restrict__ u, const double* __restrict__ D,
+                                             const double* __restrict__ H,
+                                             const double* __restrict__ dH, double* __restrict__ out,
+                                             Geo geo) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int k = (int)(p % geo.n_r);
+  const int i = (int)((p / geo.n_r) % geo.N);
+  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const int nv = geo.nv;
+  const Jac<T> Jc = jacobian<T>(geo, k, i, jj);
+  const T zero = S<T>::c(0.0), half = S<T>::c(0.5), two = S<T>::c(2.0);
+
+  T g[10], Pi[10], Ph[3][10];
+#pragma unroll
+  for (int s = 0; s < 10; ++s) {
+    g[s] = S<T>::load(u + (long long)s * P + p);
+    Pi[s] = S<T>::load(u + (long long)(10 + s) * P + p);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Ph[a][s] = S<T>::load(u + (long long)(20 + 10 * a + s) * P + p);
+  }
+  Metric<T> M;
+  metric_from(g, M);
+  T dg4[4][10], Gam[4][10], Gc[4];
+  christoffel(M, Pi, Ph, dg4, Gam, Gc);
+
+  // gauge source and its derivatives
+  T Hd[4], dHd[4][4];  // dHd[a][b] = d_a H_b
+  if (nv == 50) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Hd[a] = S<T>::load(H + (long long)a * P + p);
+      dHd[0][a] = zero;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) dHd[x + 1][a] = S<T>::load(dH + ((long long)x * 4 + a) * P + p);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      Hd[a] = S<T>::load(u + (long long)(50 + a) * P + p);
+      dHd[0][a] = nv == 58 ? S<T>::load(u + (long long)(54 + a) * P + p) : zero;
+      T c3[3];
+      cart3(Jc, D, P, nv, 50 + a, p, c3);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) dHd[x + 1][a] = c3[x];
+    }
+  }
+  T C[4], Hup[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) C[a] = Hd[a] + Gc[a];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T acc = zero;
+#pragma unroll
+    for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Hd[d];
+    Hup[c] = acc;
+  }
+  const T nC = M.nu[0] * C[0] + M.nu[1] * C[1] + M.nu[2] * C[2] + M.nu[3] * C[3];
+
+  // ---- source part of d_t Pi_ab: SPi[s]
+  T SPi[10];
+  {
+    // Q2_ab = Pi_ac Pi_b^c, Pi_b^c = g^cd Pi_bd
+    T Piu[4][4];  // Piu[b][c]
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        T acc = zero;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Pi[SI(b, d)];
+        Piu[b][c] = acc;
+      }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        T acc = zero;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc = acc + Pi[SI(a, c)] * Piu[b][c];
+        SPi[SI(a, b)] = -acc;  // -Q2
+      }
+  }
+  {
+    // Q1_ab = sum_{i,c} Phi_iac V_ib^c, V_ib^c = gamma^ij Y_jb^c, Y_jb^c = g^cd Phi_jbd
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      T V[3][4];
+      {
+        T Y[3][4];
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            T acc = zero;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Ph[x][SI(b, d)];
+            Y[x][c] = acc;
+          }
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            V[x][c] = M.gi[x][0] * Y[0][c] + M.gi[x][1] * Y[1][c] + M.gi[x][2] * Y[2][c];
+      }
+#pragma unroll
+      for (int a = 0; a <= b; ++a) {
+        T acc = zero;
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc = acc + Ph[x][SI(a, c)] * V[x][c];
+        SPi[SI(a, b)] = SPi[SI(a, b)] + acc;  // + Q1
+      }
+    }
+  }
+  {
+    // Q3_ab = sum_{c,e} Gamma_ace Gamma_b^{ce}
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      T Gcf[4][4];  // Gamma_b^c_f = g^cd Gamma_bdf
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          T acc = zero;
+#pragma unroll
+          for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Gam[b][SI(d, f)];
+          Gcf[c][f] = acc;
+        }
+      T Gce[10];  // Gamma_b^{ce} (symmetric)
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int e = c; e < 4; ++e) {
+          T acc = zero;
+#pragma unroll
+          for (int f = 0; f < 4; ++f) acc = acc + M.gi4[SI(e, f)] * Gcf[c][f];
+          Gce[SI(c, e)] = acc;
+        }
+#pragma unroll
+      for (int a = 0; a <= b; ++a) {
+        T acc = zero;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc = acc + Gam[a][SI(c, e)] * Gce[SI(c, e)];
+        SPi[SI(a, b)] = SPi[SI(a, b)] - acc;  // - Q3
+      }
+    }
+  }
+  // remaining source terms of eq. Pidot
+  {
+    T nnPi = zero;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) nnPi = nnPi + M.nu[c] * M.nu[d] * Pi[SI(c, d)];
+    T nPi[3];  // n^c Pi_ci
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      T acc = zero;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = acc + M.nu[c] * Pi[SI(c, x + 1)];
+      nPi[x] = acc;
+    }
+    T Vj[3];
+#pragma unroll
+    for (int y = 0; y < 3; ++y) Vj[y] = nPi[0] * M.gi[0][y] + nPi[1] * M.gi[1][y] + nPi[2] * M.gi[2][y];
+    const T nlo0 = -M.alpha;  // n_a = (-alpha, 0, 0, 0)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        const int s = SI(a, b);
+        // nabla_(a H_b) = 1/2 (d_a H_b + d_b H_a) - Gamma_cab H^c
+        T DH = half * (dHd[a][b] + dHd[b][a]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) DH = DH - Gam[c][s] * Hup[c];
+        T v = two * M.alpha * SPi[s] - two * M.alpha * DH - half * M.alpha * nnPi * Pi[s];
+        T vphi = zero, bphi = zero;
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          vphi = vphi + Vj[x] * Ph[x][s];
+          bphi = bphi + M.bu[x] * Ph[x][s];
+        }
+        v = v - M.alpha * vphi + bphi;
+        // alpha (n_b C_a + n_a C_b - g_ab n^c C_c)
+        T nCab = -(g[s] * nC);
+        if (a == 0) nCab = nCab + nlo0 * C[b];
+        if (b == 0) nCab = nCab + nlo0 * C[a];
+        v = v + M.alpha * nCab;
+        SPi[s] = v;
+      }
+  }
+  // source part of d_t Phi_iab: SPh[x][s] (kept implicit: computed per s below)
+  T nnPhi[3], Mik[3][3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    T acc = zero;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) acc = acc + M.nu[c] * M.nu[d] * Ph[x][SI(c, d)];
+    nnPhi[x] = acc;
+    T nP[3];  // n^c Phi_x,(y+1),c
+#pragma unroll
+    for (int y = 0; y < 3; ++y) {
+      T a2 = zero;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a2 = a2 + M.nu[c] * Ph[x][SI(y + 1, c)];
+      nP[y] = a2;
+    }
+#pragma unroll
+    for (int z = 0; z < 3; ++z) Mik[x][z] = nP[0] * M.gi[0][z] + nP[1] * M.gi[1][z] + nP[2] * M.gi[2][z];
+  }
+
+  // boundary normal on the outermost sphere
+  const bool outer = (k == geo.n_r - 1);
+  T sl[3], su[3];
+  if (outer) {
+    const T l[3] = {Jc.st * Jc.cp, Jc.st * Jc.sp, Jc.ct};
+    T q = zero;
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) q = q + M.gi[x][y] * l[x] * l[y];
+    const T iq = S<T>::c(1.0) / sqrt_s(q);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) sl[x] = l[x] * iq;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) su[x] = M.gi[x][0] * sl[0] + M.gi[x][1] * sl[1] + M.gi[x][2] * sl[2];
+  }
+
+  // ---- principal parts and output, one symmetric pair at a time
+#pragma unroll
+  for (int s = 0; s < 10; ++s) {
+    T dg[3], dPi[3], dPh[3][3];
+    cart3(Jc, D, P, nv, s, p, dg);
+    cart3(Jc, D, P, nv, 10 + s, p, dPi);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) cart3(Jc, D, P, nv, 20 + 10 * x + s, p, dPh[x]);
+    const T rg = dg4[0][s];
+    T rPi = SPi[s];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      rPi = rPi + M.bu[x] * (dPi[x] - dg[x]);
+#pragma unroll
+      for (int y = 0; y < 3; ++y) rPi = rPi - M.alpha * M.gi[x][y] * dPh[x][y];
+    }
+    T rPh[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      T v = M.bu[0] * dPh[x][0] + M.bu[1] * dPh[x][1] + M.bu[2] * dPh[x][2];
+      v = v + M.alpha * (dg[x] - dPi[x] - Ph[x][s]);
+      v = v + half * M.alpha * nnPhi[x] * Pi[s];
+      T mp = zero;
+#pragma unroll
+      for (int z = 0; z < 3; ++z) mp = mp + Mik[x][z] * Ph[z][s];
+      rPh[x] = v + M.alpha * mp;
+    }
+    if (outer) {
+      const T sd = su[0] * rPh[0] + su[1] * rPh[1] + su[2] * rPh[2];
+      const T wplus = rPi + sd;
+      const T nPi = half * (rg + wplus);
+      const T w2 = half * (wplus - rg);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) rPh[x] = sl[x] * w2;
+      rPi = nPi;
+    }
+    out[(long long)s * P + p] = S<T>::to_double(rg);
+    out[(long long)(10 + s) * P + p] = S<T>::to_double(rPi);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) out[(long long)(20 + 10 * x + s) * P + p] = S<T>::to_double(rPh[x]);
+  }
+  if (nv > 50) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      out[(long long)(50 + a) * P + p] = nv == 58 ? u[(long long)(54 + a) * P + p] : 0.0;
+      if (nv == 58) out[(long long)(54 + a) * P + p] = 0.0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Spin decomposition in the real triad.  Rm rows: r, theta, phi.
+
+template <class T>
+struct Triad {
+  T R[3][3];
+};
+
+template <class T>
+__device__ __forceinline__ Triad<T> triad_at(const Geo& g, int i, int jj) {
+  Triad<T> t;
+  const T st = S<T>::c(g.sth[i]), ct = S<T>::c(g.cth[i]);
+  const T sp = S<T>::c(g.sph[jj]), cp = S<T>::c(g.cph[jj]);
+  t.R[0][0] = st * cp; t.R[0][1] = st * sp; t.R[0][2] = ct;
+  t.R[1][0] = ct * cp; t.R[1][1] = ct * sp; t.R[1][2] = -st;
+  t.R[2][0] = -sp;     t.R[2][1] = cp;      t.R[2][2] = S<T>::c(0.0);
+  return t;
+}
+
+template <class T>
+__device__ __forceinline__ void rot_vec(const Triad<T>& t, const T v[3], T o[3]) {
+#pragma unroll
+  for (int A = 0; A < 3; ++A) o[A] = t.R[A][0] * v[0] + t.R[A][1] * v[1] + t.R[A][2] * v[2];
+}
+template <class T>
+__device__ __forceinline__ void unrot_vec(const Triad<T>& t, const T o[3], T v[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[a] = t.R[0][a] * o[0] + t.R[1][a] * o[1] + t.R[2][a] * o[2];
+}
+// general 3x3: O_AB = R_Aa R_Bb T_ab
+template <class T>
+__device__ __forceinline__ void rot_mat(const Triad<T>& t, const T Tm[3][3], T O[3][3]) {
+  T X[3][3];
+#pragma unroll
+  for (int A = 0; A < 3; ++A)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) X[A][b] = t.R[A][0] * Tm[0][b] + t.R[A][1] * Tm[1][b] + t.R[A][2] * Tm[2][b];
+#pragma unroll
+  for (int A = 0; A < 3; ++A)
+#pragma unroll
+    for (int B = 0; B < 3; ++B) O[A][B] = X[A][0] * t.R[B][0] + X[A][1] * t.R[B][1] + X[A][2] * t.R[B][2];
+}
+template <class T>
+__device__ __forceinline__ void unrot_mat(const Triad<T>& t, const T O[3][3], T Tm[3][3]) {
+  T X[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int B = 0; B < 3; ++B) X[a][B] = t.R[0][a] * O[0][B] + t.R[1][a] * O[1][B] + t.R[2][a] * O[2][B];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Tm[a][b] = X[a][0] * t.R[0][b] + X[a][1] * t.R[1][b] + X[a][2] * t.R[2][b];
+}
+
+// Slot assignment (see SpinLayout in common.cuh); the numbers below are the
+// slots written by k_decompose and read back by k_reconstruct.
+#define SLOT_R0(n) (n)
+#define SLOT_C1(q) (16 + 2 * (q))
+#define SLOT_C2(q) (38 + 2 * (q))
+#define SLOT_C3 48
+
+template <class T>
+__device__ __forceinline__ T ld(const double* a, long long P, long long p, int f) {
+  return S<T>::load(a + (long long)f * P + p);
+}
+template <class T>
+__device__ __forceinline__ void st(double* a, long long P, long long p, int f, T v) {
+  a[(long long)f * P + p] = S<T>::to_double(v);
+}
+
+template <class T>
+__device__ __forceinline__ void decompose_point(const double* __restrict__ in, double* __restrict__ out,
+                                                long long P, long long p, const Triad<T>& t) {
+  const T half = S<T>::c(0.5), two = S<T>::c(2.0);
+  // rank 0
+  st(out, P, p, SLOT_R0(0), ld<T>(in, P, p, SI(0, 0)));
+  st(out, P, p, SLOT_R0(1), ld<T>(in, P, p, 10 + SI(0, 0)));
+  // rank 1: g_ti, Pi_ti, Phi_itt
+  {
+    const int base[3][3] = {{1, 2, 3}, {11, 12, 13}, {20, 30, 40}};
+    const int sr[3] = {2, 3, 4};
+#pragma unroll
+    for (int gph = 0; gph < 3; ++gph) {
+      T v[3], o[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v[a] = ld<T>(in, P, p, base[gph][a]);
+      rot_vec(t, v, o);
+      st(out, P, p, SLOT_R0(sr[gph]), o[0]);
+      st(out, P, p, SLOT_C1(gph), o[1]);
+      st(out, P, p, SLOT_C1(gph) + 1, o[2]);
+    }
+  }
+  // symmetric rank 2: g_ij, Pi_ij
+#pragma unroll
+  for (int gph = 0; gph < 2; ++gph) {
+    const int b0 = gph * 10;
+    T Tm[3][3], O[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, b0 + SI(a + 1, b + 1));
+    rot_mat(t, Tm, O);
+    st(out, P, p, SLOT_R0(5 + 2 * gph), O[0][0]);
+    st(out, P, p, SLOT_R0(6 + 2 * gph), O[1][1] + O[2][2]);
+    st(out, P, p, SLOT_C1(3 + gph), O[0][1]);
+    st(out, P, p, SLOT_C1(3 + gph) + 1, O[0][2]);
+    st(out, P, p, SLOT_C2(gph), O[1][1] - O[2][2]);
+    st(out, P, p, SLOT_C2(gph) + 1, two * O[1][2]);
+  }
+  // general rank 2: Phi_itj (i derivative index, j tensor index)
+  {
+    T Tm[3][3], O[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, 20 + 10 * a + SI(0, b + 1));
+    rot_mat(t, Tm, O);
+    st(out, P, p, SLOT_R0(9), O[0][0]);
+    st(out, P, p, SLOT_C1(5), O[0][1]);
+    st(out, P, p, SLOT_C1(5) + 1, O[0][2]);
+    st(out, P, p, SLOT_C1(6), O[1][0]);
+    st(out, P, p, SLOT_C1(6) + 1, O[2][0]);
+    st(out, P, p, SLOT_C2(2), O[1][1] - O[2][2]);
+    st(out, P, p, SLOT_C2(2) + 1, O[1][2] + O[2][1]);
+    st(out, P, p, SLOT_R0(12), O[1][1] + O[2][2]);
+    st(out, P, p, SLOT_R0(13), O[2][1] - O[1][2]);
+  }
+  // rank 3: Phi_ijk, symmetric in jk
+  {
+    T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];  // per first-leg A (r, theta, phi)
+    T Trot[3][3][3];                         // [a][B][C]: pair rotated, first leg Cartesian
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T Tm[3][3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Tm[b][c] = ld<T>(in, P, p, 20 + 10 * a + SI(b + 1, c + 1));
+      rot_mat(t, Tm, Trot[a]);
+    }
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+      T O[3][3];
+#pragma unroll
+      for (int B = 0; B < 3; ++B)
+#pragma unroll
+        for (int C = 0; C < 3; ++C)
+          O[B][C] = t.R[A][0] * Trot[0][B][C] + t.R[A][1] * Trot[1][B][C] + t.R[A][2] * Trot[2][B][C];
+      Pr[A] = O[0][0];
+      Pmb[A] = O[1][1] + O[2][2];
+      Prm[A][0] = O[0][1];
+      Prm[A][1] = O[0][2];
+      Pmm[A][0] = O[1][1] - O[2][2];
+      Pmm[A][1] = two * O[1][2];
+    }
+    st(out, P, p, SLOT_R0(10), Pr[0]);
+    st(out, P, p, SLOT_R0(11), Pmb[0]);
+    st(out, P, p, SLOT_C1(7), Prm[0][0]);
+    st(out, P, p, SLOT_C1(7) + 1, Prm[0][1]);
+    st(out, P, p, SLOT_C2(3), Pmm[0][0]);
+    st(out, P, p, SLOT_C2(3) + 1, Pmm[0][1]);
+    st(out, P, p, SLOT_C1(8), Pr[1]);
+    st(out, P, p, SLOT_C1(8) + 1, Pr[2]);
+    st(out, P, p, SLOT_C1(9), Pmb[1]);
+    st(out, P, p, SLOT_C1(9) + 1, Pmb[2]);
+    // (mbar; mm) = P_mm^theta - i P_mm^phi
+    st(out, P, p, SLOT_C1(10), Pmm[1][0] + Pmm[2][1]);
+    st(out, P, p, SLOT_C1(10) + 1, Pmm[1][1] - Pmm[2][0]);
+    // (m; rm) = P_rm^theta + i P_rm^phi
+    st(out, P, p, SLOT_C2(4), Prm[1][0] - Prm[2][1]);
+    st(out, P, p, SLOT_C2(4) + 1, Prm[1][1] + Prm[2][0]);
+    // (m; r mbar) = conj(P_rm^theta) + i conj(P_rm^phi)   (spin 0)
+    st(out, P, p, SLOT_R0(14), Prm[1][0] + Prm[2][1]);
+    st(out, P, p, SLOT_R0(15), Prm[2][0] - Prm[1][1]);
+    // (m; mm) = P_mm^theta + i P_mm^phi
+    st(out, P, p, SLOT_C3, Pmm[1][0] - Pmm[2][1]);
+    st(out, P, p, SLOT_C3 + 1, Pmm[1][1] + Pmm[2][0]);
+  }
+  (void)half;
+}
+
+// Inverse of decompose_point: spin slots -> Cartesian tensor components.
+template <class T>
+__device__ __forceinline__ void reconstruct_point(const double* __restrict__ sp, long long P, long long p,
+                                                  const Triad<T>& t, T cart[50]) {
+  const T half = S<T>::c(0.5);
+  cart[SI(0, 0)] = ld<T>(sp, P, p, SLOT_R0(0));
+  cart[10 + SI(0, 0)] = ld<T>(sp, P, p, SLOT_R0(1));
+  {
+    const int base[3][3] = {{1, 2, 3}, {11, 12, 13}, {20, 30, 40}};
+    const int sr[3] = {2, 3, 4};
+#pragma unroll
+    for (int gph = 0; gph < 3; ++gph) {
+      T o[3] = {ld<T>(sp, P, p, SLOT_R0(sr[gph])), ld<T>(sp, P, p, SLOT_C1(gph)),
+                ld<T>(sp, P, p, SLOT_C1(gph) + 1)};
+      T v[3];
+      unrot_vec(t, o, v);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) cart[base[gph][a]] = v[a];
+    }
+  }
+#pragma unroll
+  for (int gph = 0; gph < 2; ++gph) {
+    const int b0 = gph * 10;
+    const T rr = ld<T>(sp, P, p, SLOT_R0(5 + 2 * gph));
+    const T mmb = ld<T>(sp, P, p, SLOT_R0(6 + 2 * gph));
+    const T rmr = ld<T>(sp, P, p, SLOT_C1(3 + gph)), rmi = ld<T>(sp, P, p, SLOT_C1(3 + gph) + 1);
+    const T mmr = ld<T>(sp, P, p, SLOT_C2(gph)), mmi = ld<T>(sp, P, p, SLOT_C2(gph) + 1);
+    T O[3][3], Tm[3][3];
+    O[0][0] = rr;
+    O[0][1] = O[1][0] = rmr;
+    O[0][2] = O[2][0] = rmi;
+    O[1][1] = half * (mmb + mmr);
+    O[2][2] = half * (mmb - mmr);
+    O[1][2] = O[2][1] = half * mmi;
+    unrot_mat(t, O, Tm);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b) cart[b0 + SI(a + 1, b + 1)] = Tm[a][b];
+  }
+  {
+    const T s9 = ld<T>(sp, P, p, SLOT_R0(9));
+    const T s12 = ld<T>(sp, P, p, SLOT_R0(12)), s13 = ld<T>(sp, P, p, SLOT_R0(13));
+    const T s42 = ld<T>(sp, P, p, SLOT_C2(2)), s43 = ld<T>(sp, P, p, SLOT_C2(2) + 1);
+    T O[3][3], Tm[3][3];
+    O[0][0] = s9;
+    O[0][1] = ld<T>(sp, P, p, SLOT_C1(5));
+    O[0][2] = ld<T>(sp, P, p, SLOT_C1(5) + 1);
+    O[1][0] = ld<T>(sp, P, p, SLOT_C1(6));
+    O[2][0] = ld<T>(sp, P, p, SLOT_C1(6) + 1);
+    O[1][1] = half * (s42 + s12);
+    O[2][2] = half * (s12 - s42);
+    O[1][2] = half * (s43 - s13);
+    O[2][1] = half * (s43 + s13);
+    unrot_mat(t, O, Tm);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) cart[20 + 10 * a + SI(0, b + 1)] = Tm[a][b];
+  }
+  {
+    T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];
+    Pr[0] = ld<T>(sp, P, p, SLOT_R0(10));
+    Pmb[0] = ld<T>(sp, P, p, SLOT_R0(11));
+    Prm[0][0] = ld<T>(sp, P, p, SLOT_C1(7));
+    Prm[0][1] = ld<T>(sp, P, p, SLOT_C1(7) + 1);
+    Pmm[0][0] = ld<T>(sp, P, p, SLOT_C2(3));
+    Pmm[0][1] = ld<T>(sp, P, p, SLOT_C2(3) + 1);
+    Pr[1] = ld<T>(sp, P, p, SLOT_C1(8));
+    Pr[2] = ld<T>(sp, P, p, SLOT_C1(8) + 1);
+    Pmb[1] = ld<T>(sp, P, p, SLOT_C1(9));
+    Pmb[2] = ld<T>(sp, P, p, SLOT_C1(9) + 1);
+    {
+      // X = (m; rm) = P^th + i P^ph, Y = (m; r mbar) = conj(P^th) + i conj(P^ph)
+      const T xr = ld<T>(sp, P, p, SLOT_C2(4)), xi = ld<T>(sp, P, p, SLOT_C2(4) + 1);
+      const T yr = ld<T>(sp, P, p, SLOT_R0(14)), yi = ld<T>(sp, P, p, SLOT_R0(15));
+      Prm[1][0] = half * (xr + yr);
+      Prm[1][1] = half * (xi - yi);
+      Prm[2][0] = half * (xi + yi);
+      Prm[2][1] = half * (yr - xr);
+    }
+    {
+      // X = (m; mm) = P^th + i P^ph, Z = (mbar; mm) = P^th - i P^ph
+      const T xr = ld<T>(sp, P, p, SLOT_C3), xi = ld<T>(sp, P, p, SLOT_C3 + 1);
+      const T zr = ld<T>(sp, P, p, SLOT_C1(10)), zi = ld<T>(sp, P, p, SLOT_C1(10) + 1);
+      Pmm[1][0] = half * (xr + zr);
+      Pmm[1][1] = half * (xi + zi);
+      Pmm[2][0] = half * (xi - zi);
+      Pmm[2][1] = half * (zr - xr);
+    }
+    T Trot[3][3][3];  // [A][B][C] in the triad
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+      Trot[A][0][0] = Pr[A];
+      Trot[A][0][1] = Trot[A][1][0] = Prm[A][0];
+      Trot[A][0][2] = Trot[A][2][0] = Prm[A][1];
+      Trot[A][1][1] = half * (Pmb[A] + Pmm[A][0]);
+      Trot[A][2][2] = half * (Pmb[A] - Pmm[A][0]);
+      Trot[A][1][2] = Trot[A][2][1] = half * Pmm[A][1];
+    }
+    // back to Cartesian: first the pair, then the first leg
+    T X[3][3][3];  // [A][b][c]
+#pragma unroll
+    for (int A = 0; A < 3; ++A) unrot_mat(t, Trot[A], X[A]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int c = b; c < 3; ++c)
+          cart[20 + 10 * a + SI(b + 1, c + 1)] =
+              t.R[0][a] * X[0][b][c] + t.R[1][a] * X[1][b][c] + t.R[2][a] * X[2][b][c];
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in, double* __restrict__ out,
+                                                   Geo geo) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= geo.P) return;
+  const int i = (int)((p / geo.n_r) % geo.N);
+  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const Triad<T> t = triad_at<T>(geo, i, jj);
+  decompose_point<T>(in, out, geo.P, p, t);
+}
+
+// mode: 0 = write filtered tensor to `dst`;
+//       1..4 = RK4 stage s (1-based) with filtered rhs k_s = reconstruct(sp);
+//       5..8 = RK4 stage without filter: k_s read as Cartesian from sp.
+struct StepArgs {
+  double* u;        // state u_n (read; written at stage 4)
+  double* U;        // next stage state
+  double* kacc;     // accumulator
+  double dt;
+  int* flag;
+};
+
+template <class T>
+__global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
+                                                     Geo geo, int mode, StepArgs sa) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int nv = geo.nv;
+  T cart[50];
+  if (mode <= 4) {
+    const int i = (int)((p / geo.n_r) % geo.N);
+    const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+    const Triad<T> t = triad_at<T>(geo, i, jj);
+    reconstruct_point<T>(sp, P, p, t, cart);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 50; ++f) cart[f] = ld<T>(sp, P, p, f);
+  }
+  if (mode == 0) {
+#pragma unroll
+    for (int f = 0; f < 50; ++f) dst[(long long)f * P + p] = S<T>::to_double(cart[f]);
+    return;
+  }
+  const int stage = (mode - 1) % 4;  // 0..3
+  const double dt = sa.dt;
+  const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
+  const T wk = S<T>::c(stage == 0 ? 1.0 : 2.0);
+  const T sixth = S<T>::c(dt / 6.0);
+  bool bad = false;
+#pragma unroll
+  for (int f = 0; f < 50; ++f) {
+    const long long o = (long long)f * P + p;
+    const T kf = cart[f];
+    const double kd = S<T>::to_double(kf);
+    bad |= !isfinite(kd);
+    if (stage < 3) {
+      if (stage == 0)
+        sa.kacc[o] = kd;
+      else
+        sa.kacc[o] = S<T>::to_double(S<T>::load(sa.kacc + o) + wk * kf);
+      sa.U[o] = sa.u[o] + S<T>::to_double(cU * kf);
+    } else {
+      const T inc = sixth * (S<T>::load(sa.kacc + o) + kf);
+      sa.u[o] = sa.u[o] + S<T>::to_double(inc);
+    }
+  }
+  (void)nv;
+  if (bad) atomicOr(sa.flag, 1);
+}
+
+// Spherical -> Cartesian derivatives: D[3][nf][P] -> out[3][nf][P]
+__global__ void k_cart(const double* __restrict__ D, double* __restrict__ out, int nf, Geo geo) {
+  const long long P = geo.P;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= P * nf) return;
+  const long long p = t % P;
+  const int mu = (int)(t / P);
+  const int k = (int)(p % geo.n_r);
+  const int i = (int)((p / geo.n_r) % geo.N);
+  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const Jac<double> J = jacobian<double>(geo, k, i, jj);
+  double c3[3];
+  cart3(J, D, P, nf, mu, p, c3);
+#pragma unroll
+  for (int x = 0; x < 3; ++x) out[((long long)x * nf + mu) * P + p] = c3[x];
+}
+
+// H_a = -Gamma_a(u), pointwise (FP64)
+__global__ void k_gauge(const double* __restrict__ u, double* __restrict__ H, long long Hstride, Geo geo) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double g[10], Pi[10], Ph[3][10];
+  for (int s = 0; s < 10; ++s) {
+    g[s] = u[(long long)s * P + p];
+    Pi[s] = u[(long long)(10 + s) * P + p];
+    for (int a = 0; a < 3; ++a) Ph[a][s] = u[(long long)(20 + 10 * a + s) * P + p];
+  }
+  Metric<double> M;
+  metric_from(g, M);
+  double dg4[4][10], Gam[4][10], Gc[4];
+  christoffel(M, Pi, Ph, dg4, Gam, Gc);
+  for (int a = 0; a < 4; ++a) H[(long long)a * Hstride + p] = -Gc[a];
+}
+
+// sum over points of C_iab^2 (30 components) and C_a^2 (4) -> red[0], red[1]
+__global__ void k_constraints(const double* __restrict__ u, const double* __restrict__ dcart /*[3][10][P]*/,
+                              const double* __restrict__ H, long long Hstride, Geo geo, double* red) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double s3 = 0.0, s1 = 0.0;
+  if (p < P) {
+    double g[10], Pi[10], Ph[3][10];
+    for (int s = 0; s < 10; ++s) {
+      g[s] = u[(long long)s * P + p];
+      Pi[s] = u[(long long)(10 + s) * P + p];
+      for (int a = 0; a < 3; ++a) Ph[a][s] = u[(long long)(20 + 10 * a + s) * P + p];
+    }
+    for (int x = 0; x < 3; ++x)
+      for (int s = 0; s < 10; ++s) {
+        double c = dcart[((long long)x * 10 + s) * P + p] - Ph[x][s];
+        s3 += c * c;
+      }
+    Metric<double> M;
+    metric_from(g, M);
+    double dg4[4][10], Gam[4][10], Gc[4];
+    christoffel(M, Pi, Ph, dg4, Gam, Gc);
+    for (int a = 0; a < 4; ++a) {
+      double c = H[(long long)a * Hstride + p] + Gc[a];
+      s1 += c * c;
+    }
+  }
+  __shared__ double r3[128], r1[128];
+  r3[threadIdx.x] = s3;
+  r1[threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      r3[threadIdx.x] += r3[threadIdx.x + w];
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(red, r3[0]);
+    atomicAdd(red + 1, r1[0]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+
+static Geo geo_of(const cffyn_shell* sh) {
+  Geo g;
+  g.n_r = sh->n_r;
+  g.N = sh->N;
+  g.J = sh->J;
+  g.nv = sh->nv;
+  g.P = (long long)sh->P;
+  g.r = sh->r;
+  g.sth = sh->sth;
+  g.cth = sh->cth;
+  g.sph = sh->sph;
+  g.cph = sh->cph;
+  return g;
+}
+
+static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int pw_rhs(const cffyn_shell* sh, const double* u, const double* D, double* out, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  if (sh->d.precision == CFFYN_MIXED)
+    k_rhs<ff><<<blocks_for(g.P, 128), 128, 0, st>>>(u, D, sh->H, sh->dH, out, g);
+  else
+    k_rhs<double><<<blocks_for(g.P, 128), 128, 0, st>>>(u, D, sh->H, sh->dH, out, g);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+int pw_decompose(const cffyn_shell* sh, const double* in, double* out, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  if (sh->d.precision == CFFYN_MIXED)
+    k_decompose<ff><<<blocks_for(g.P, 128), 128, 0, st>>>(in, out, g);
+  else
+    k_decompose<double><<<blocks_for(g.P, 128), 128, 0, st>>>(in, out, g);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mode, double* u, double* U,
+                   double* kacc, double dt, int* flag, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  StepArgs sa{u, U, kacc, dt, flag};
+  if (sh->d.precision == CFFYN_MIXED)
+    k_reconstruct<ff><<<blocks_for(g.P, 128), 128, 0, st>>>(sp, dst, g, mode, sa);
+  else
+    k_reconstruct<double><<<blocks_for(g.P, 128), 128, 0, st>>>(sp, dst, g, mode, sa);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  k_cart<<<blocks_for(g.P * nf, 256), 256, 0, st>>>(D, out, nf, g);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+int pw_gauge(const cffyn_shell* sh, const double* u, double* H, long long Hstride, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  k_gauge<<<blocks_for(g.P, 128), 128, 0, st>>>(u, H, Hstride, g);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+int pw_constraints(const cffyn_shell* sh, const double* u, const double* dcart, const double* H,
+                   long long Hstride, double* red, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  k_constraints<<<blocks_for(g.P, 128), 128, 0, st>>>(u, dcart, H, Hstride, g, red);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+}  // namespace cffyn

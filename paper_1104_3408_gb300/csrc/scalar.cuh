@@ -1,0 +1,170 @@
+// Scalar types for the pointwise kernels: plain double (FP64 path) and a
+// double-float "ff" (FP32 pair, hi + lo) for the mixed path.
+//
+// ff arithmetic uses the error-free transformations TwoSum (Knuth, TAOCP
+// vol. 2, 4.2.2) and TwoProd via a fused multiply-add (Dekker 1971; FMA form
+// as in Muller et al., Handbook of Floating-Point Arithmetic, 2nd ed., 4.4),
+// with the "sloppy" double-word addition and the double-word times
+// double-word product of Joldes, Muller and Popescu, "Tight and rigorous
+// error bounds for basic building blocks of double-word arithmetic", ACM TOMS
+// 44 (2017), Algorithms 5 and 11 (FMA variant).  Division and square root take
+// one Newton correction of the FP32 quotient / root computed by CUDA's own
+// operators.  The relative error of one operation is O(2^-44) except under
+// cancellation in the sloppy addition, whose absolute error stays O(2^-44)
+// times the operands' magnitude: the quantity the pointwise kernels are
+// checked against.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cffyn {
+
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_from_float(float a) { return ff{a, 0.0f}; }
+
+// v * 2^sc as a double (round to nearest, integer operations only); v != 0
+// handled, v == 0 gives 0.  Used where the FP64 / conversion pipes of this part
+// would be the bottleneck.
+__device__ __forceinline__ double u64_scaled_to_double(unsigned long long v, int sc, bool neg) {
+  if (v == 0) return 0.0;
+  const int nb = 64 - __clzll((long long)v);
+  int ex = nb - 1 + sc;
+  unsigned long long m;
+  if (nb > 53) {
+    const int sh = nb - 53;
+    m = (v + (1ull << (sh - 1))) >> sh;
+    if (m >> 53) {
+      m >>= 1;
+      ex += 1;
+    }
+  } else {
+    m = v << (53 - nb);
+  }
+  if (ex + 1023 <= 0) return 0.0;
+  if (ex + 1023 >= 2047) return neg ? -__longlong_as_double(0x7ff0000000000000ll)
+                                    : __longlong_as_double(0x7ff0000000000000ll);
+  const unsigned long long bits = (neg ? 0x8000000000000000ull : 0ull) |
+                                  ((unsigned long long)(ex + 1023) << 52) |
+                                  (m & 0x000fffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
+// v * 2^sc as a float (truncating), integer operations only.
+__device__ __forceinline__ float u64_scaled_to_float(unsigned long long v, int sc, bool neg) {
+  if (v == 0) return 0.0f;
+  const int nb = 64 - __clzll((long long)v);
+  int ex = nb - 1 + sc;
+  unsigned int m = nb > 24 ? (unsigned int)(v >> (nb - 24)) : (unsigned int)(v << (24 - nb));
+  if (ex + 127 <= 0) return 0.0f;  // below the normal range: flushed
+  const unsigned int bits = (neg ? 0x80000000u : 0u) | ((unsigned int)(ex + 127) << 23) | (m & 0x7fffffu);
+  return __uint_as_float(bits);
+}
+
+// Split an FP64 value into hi + lo with integer operations only: hi keeps the
+// leading 24 significand bits (truncated), lo the next 24 (truncated), so
+// |x - hi - lo| <= 2^-47 |x|.  Values outside the FP32 normal range are
+// flushed to 0 / +-Inf; NaN stays NaN.
+__device__ __forceinline__ ff ff_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const bool neg = (b >> 63) != 0;
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e == 0) return ff{0.0f, 0.0f};
+  if (e == 0x7ff) return ff{(float)x, 0.0f};   // Inf / NaN: rare, conversion is fine
+  const int E = e - 1023;
+  if (E > 127) return ff{neg ? -__int_as_float(0x7f800000) : __int_as_float(0x7f800000), 0.0f};
+  if (E < -126) return ff{0.0f, 0.0f};
+  const unsigned long long m = b & 0x000fffffffffffffull;
+  const unsigned int hbits = (neg ? 0x80000000u : 0u) | ((unsigned int)(E + 127) << 23) |
+                             (unsigned int)(m >> 29);
+  const float hi = __uint_as_float(hbits);
+  const float lo = u64_scaled_to_float(m & ((1ull << 29) - 1), E - 52, neg);
+  return ff{hi, lo};
+}
+
+// hi + lo as a double with integer operations only.
+__device__ __forceinline__ double ff_to_double(ff a) {
+  const unsigned int uh = __float_as_uint(a.hi), ul = __float_as_uint(a.lo);
+  const int eh = (int)((uh >> 23) & 0xff), el = (int)((ul >> 23) & 0xff);
+  if (eh == 0xff) return (double)a.hi;         // Inf / NaN
+  if (eh == 0) {                                // hi zero (or FP32 denormal): lo alone
+    if (el == 0) return 0.0;
+    return u64_scaled_to_double((ul & 0x7fffffu) | 0x800000u, el - 150, (ul >> 31) != 0);
+  }
+  const long long Mh = (long long)((uh & 0x7fffffu) | 0x800000u) << 29;  // unit 2^(eh-127-52)
+  long long V = (uh >> 31) ? -Mh : Mh;
+  if (el != 0) {
+    const long long Ml = (long long)((ul & 0x7fffffu) | 0x800000u);
+    const int sh = el - eh + 29;                  // lo relative to the unit
+    long long Lv = 0;
+    if (sh >= 0) Lv = Ml << sh;
+    else if (sh > -40) Lv = Ml >> (-sh);
+    V += (ul >> 31) ? -Lv : Lv;
+  }
+  const bool neg = V < 0;
+  return u64_scaled_to_double(neg ? (unsigned long long)(-V) : (unsigned long long)V, eh - 127 - 52, neg);
+}
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return ff{s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {
+  float s = a + b;
+  float e = b - (s - a);
+  return ff{s, e};
+}
+__device__ __forceinline__ ff operator+(ff x, ff y) {
+  ff s = two_sum(x.hi, y.hi);
+  float v = s.lo + (x.lo + y.lo);
+  return fast_two_sum(s.hi, v);
+}
+__device__ __forceinline__ ff operator-(ff x) { return ff{-x.hi, -x.lo}; }
+__device__ __forceinline__ ff operator-(ff x, ff y) { return x + (-y); }
+__device__ __forceinline__ ff operator*(ff x, ff y) {
+  float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  float t = fmaf(x.hi, y.lo, x.lo * y.hi);
+  return fast_two_sum(p, e + t);
+}
+__device__ __forceinline__ ff operator*(ff x, float c) {
+  float p = x.hi * c;
+  float e = fmaf(x.hi, c, -p);
+  return fast_two_sum(p, fmaf(x.lo, c, e));
+}
+__device__ __forceinline__ ff operator*(float c, ff x) { return x * c; }
+__device__ __forceinline__ ff operator/(ff x, ff y) {
+  float q = x.hi / y.hi;
+  ff r = x - y * q;                 // residual
+  float q2 = r.hi / y.hi;
+  return fast_two_sum(q, q2);
+}
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) { a = a + b; return a; }
+__device__ __forceinline__ ff& operator-=(ff& a, ff b) { a = a - b; return a; }
+__device__ __forceinline__ ff sqrt_s(ff x) {
+  if (x.hi <= 0.0f) return ff{sqrtf(x.hi), 0.0f};
+  float s = sqrtf(x.hi);
+  ff ss = ff{s, 0.0f} * ff{s, 0.0f};
+  ff r = x - ss;
+  return fast_two_sum(s, r.hi / (2.0f * s));
+}
+__device__ __forceinline__ double sqrt_s(double x) { return sqrt(x); }
+
+// Uniform helpers so that templated code reads the same for both types.
+template <class T> struct S;
+template <> struct S<double> {
+  static __device__ __forceinline__ double c(double v) { return v; }
+  static __device__ __forceinline__ double load(const double* p) { return *p; }
+  static __device__ __forceinline__ double to_double(double v) { return v; }
+};
+template <> struct S<ff> {
+  static __device__ __forceinline__ ff c(double v) { return ff_from_double(v); }
+  static __device__ __forceinline__ ff load(const double* p) { return ff_from_double(__ldg(p)); }
+  static __device__ __forceinline__ double to_double(ff v) { return ff_to_double(v); }
+};
+
+}  // namespace cffyn

@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol that
+include/cffyn.h declares; argument checks run on the host.  No GPU needed
+(no compute call is made)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1104_3408_gb300 import _build, cffyn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return cffyn.load()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "cffyn.h")) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"CFFYN_API\s+[\w\s\*]+?\b(cffyn_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_names():
+    names = _declared()
+    assert names == sorted(cffyn.EXPORTED)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_error_strings(lib):
+    assert b"sm_103a" in lib.cffyn_version()
+    assert isinstance(lib.cffyn_last_error(), bytes)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n_r=2), dict(n_theta=1, n_phi=2), dict(n_phi=30), dict(r_in=0.0), dict(r_out=1.0),
+    dict(L=12), dict(L=-1), dict(precision=7), dict(filter_mode=3), dict(n_fields=49),
+    dict(n_theta=97, n_phi=194),
+])
+def test_create_rejects_bad_arguments_on_host(lib, bad):
+    kw = dict(n_r=9, n_theta=12, n_phi=24, r_in=1.8, r_out=11.0, L=10, n_fields=50,
+              precision=cffyn.MIXED, filter_mode=cffyn.FILTER_SUBSTEP, courant=0.25)
+    kw.update(bad)
+    desc = cffyn.ShellDesc(kw["n_r"], kw["n_theta"], kw["n_phi"], kw["r_in"], kw["r_out"],
+                           kw["L"], kw["n_fields"], kw["precision"], kw["filter_mode"],
+                           kw["courant"])
+    h = ctypes.c_void_p(1)
+    rc = lib.cffyn_create_shell_ex(ctypes.byref(desc), ctypes.byref(h))
+    assert rc == cffyn.EINVAL
+    assert h.value is None
+    assert len(lib.cffyn_last_error()) > 0
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.cffyn_destroy(None) == cffyn.OK
+    assert lib.cffyn_rhs(None, None, None, None) == cffyn.EINVAL
+    assert lib.cffyn_filter(None, None, None, None) == cffyn.EINVAL
+    assert lib.cffyn_rk4_step(None, None, 0.1, 1, None) == cffyn.EINVAL
+    assert lib.cffyn_create_shell_ex(None, None) == cffyn.EINVAL

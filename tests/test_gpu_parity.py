@@ -1,0 +1,185 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle on seeded
+inputs.  Tolerances: FP64 path 1e-12 relative (summation order only); mixed
+path 1e-10 relative for derivatives, right-hand side and filter, 1e-8 for
+fields after RK4 steps.  "Relative" is max|difference| over an output array
+divided by max|reference| of that array; for the right-hand side of
+near-static Kerr-Schild data (which is truncation error, ~1e-8, far below the
+size of the terms that cancel in it) the denominator is max|d_k u|."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import cff, swsh
+from paper_1104_3408_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-10}   # FP64, MIXED
+
+
+@pytest.fixture(scope="module")
+def cf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3408_gb300 import cffyn
+    return cffyn
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def rel(got, ref, axis=None):
+    if axis is None:
+        return np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+    d = np.abs(got - ref).reshape(ref.shape[0], -1).max(axis=1)
+    r = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1)
+    return (d / np.maximum(r, 1e-300)).max()
+
+
+SHAPES = [(9, 12, 24, 10), (13, 9, 18, 6), (33, 32, 64, 30)]
+
+
+@pytest.mark.parametrize("n_r,N,J,L", SHAPES[:2] + [(17, 16, 32, 0), (5, 6, 12, 5)])
+def test_operator_matrices_match_oracle(cf, n_r, N, J, L):
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=cf.FP64)
+    Dr = cff.radial_diff_matrix(n_r, 1.8, 11.0)
+    assert rel(sh.get_operator(0), Dr) < 1e-13
+    FD = cff.fourier_diff_matrix(2 * N)
+    assert np.abs(sh.get_operator(1) - FD[:N]).max() < 1e-13 * np.abs(FD).max()
+    assert rel(sh.get_operator(2), cff.fourier_diff_matrix(J)) < 1e-13
+    _, t, _ = cff.grid(n_r, N, J, 1.8, 11.0)
+    sl = swsh.SpinLegendre(t, N - 1)
+    worst = 0.0
+    for n in range(-3, 4):
+        for m in range(0, L + 1):
+            F = swsh.filter_matrix(sl, n, m, N, L)
+            G = sh.get_filter_matrix(n, m)
+            worst = max(worst, np.abs(F - G).max())
+    sh.destroy()
+    assert worst < 1e-11
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n_r,N,J,L", SHAPES)
+def test_cartesian_derivatives(cf, prec, n_r, N, J, L):
+    u0 = inputs.band_limited_fields(n_r, N, J, 1.8, 11.0, seed=1)
+    ref = cff.cartesian_derivatives(u0, 1.8, 11.0)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec)
+    out = torch.empty((3,) + u0.shape, dtype=torch.float64, device="cuda")
+    sh.derivs(dev(u0), out)
+    got = out.cpu().numpy()
+    sh.destroy()
+    e = max(rel(got[d], ref[d], axis=0) for d in range(3))
+    assert e < TOL[prec], e
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n_r,N,J,L", SHAPES)
+def test_filter(cf, prec, n_r, N, J, L):
+    u0 = inputs.band_limited_fields(n_r, N, J, 1.8, 11.0, seed=2)
+    ref = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L).filter(u0)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec)
+    out = torch.empty_like(dev(u0))
+    sh.filter(dev(u0), out)
+    got = out.cpu().numpy()
+    sh.destroy()
+    e = rel(got, ref, axis=0)
+    assert e < TOL[prec], e
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n_r,N,J,L", SHAPES)
+def test_rhs_with_boundary(cf, prec, n_r, N, J, L):
+    u0 = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-4, ell=4, seed=3)
+    ref_sh = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L)
+    ref_sh.init_gauge_from_state(u0)
+    ref = ref_sh.rhs(u0)
+    scale = np.abs(ref_sh.derivs(u0)).max()
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec)
+    u = dev(u0)
+    sh.init_gauge_from_state(u)
+    out = torch.empty_like(u)
+    sh.rhs(u, out)
+    got = out.cpu().numpy()
+    sh.destroy()
+    e = np.abs(got - ref).max() / scale
+    assert e < TOL[prec], e
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rk4_ten_steps_small_shell(cf, prec):
+    # 9 x 12 x 24, L = 10, amplitude 1e-6, l <= 2, dt = 0.25 min dx, 10 steps
+    n_r, N, J, L = 9, 12, 24, 10
+    u0 = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-6, ell=2, seed=0)
+    rs = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L)
+    rs.init_gauge_from_state(u0)
+    dt = 0.25 * rs.dx_min()
+    uf = rs.filter(u0)
+    ref = rs.rk4_step(uf, dt, 10)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec)
+    assert abs(sh.default_dt() - dt) < 1e-15
+    u = dev(u0)
+    sh.init_gauge_from_state(u)
+    v = torch.empty_like(u)
+    sh.filter(u, v)
+    sh.rk4_step(v, dt, 10)
+    got = v.cpu().numpy()
+    sh.destroy()
+    e = rel(got, ref)
+    assert e < (1e-12 if prec == 0 else 1e-8), e
+    # the evolution really moved the state
+    assert np.abs(ref - uf).max() > 1e-9
+
+
+def test_rk4_per_step_filter_mode(cf):
+    n_r, N, J, L = 9, 12, 24, 10
+    u0 = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-5, ell=2, seed=4)
+    rs = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L, filter_mode="step")
+    rs.init_gauge_from_state(u0)
+    dt = 0.25 * rs.dx_min()
+    ref = rs.rk4_step(u0, dt, 3)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=cf.MIXED, filter_mode=cf.FILTER_STEP)
+    u = dev(u0)
+    sh.init_gauge_from_state(u)
+    sh.rk4_step(u, dt, 3)
+    got = u.cpu().numpy()
+    sh.destroy()
+    assert rel(got, ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_constraint_norms(cf, prec):
+    n_r, N, J, L = 13, 12, 24, 10
+    u0 = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-3, ell=2, seed=5)
+    rs = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L)
+    rs.init_gauge_from_state(u0)
+    c3, c1 = rs.constraint_norms(u0)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec)
+    u = dev(u0)
+    sh.init_gauge_from_state(u)
+    g3, g1 = sh.constraint_norms(u)
+    sh.destroy()
+    assert abs(g3 - c3) < 1e-9 * max(c3, 1e-30) + 1e-14
+    assert g1 < 1e-14 and c1 < 1e-14
+
+
+def test_nonfinite_state_is_reported(cf):
+    n_r, N, J, L = 5, 6, 12, 4
+    u0 = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=0.0)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L)
+    u = dev(u0)
+    sh.init_gauge_from_state(u)
+    u[25, 3, 2, 1] = float("nan")
+    with pytest.raises(cf.CffynError) as ei:
+        sh.rk4_step(u, 0.0, 1)
+    assert ei.value.code == cf.ENONFINITE
+    # the handle stays usable
+    v = dev(u0)
+    sh.rk4_step(v, 0.0, 1)
+    assert torch.isfinite(v).all()
+    sh.destroy()
