@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point x field RK4 updates per second on one spherical shell.
+
+Default workload (the full-RK4 single-shell configuration): 33 x 48 x 96 shell,
+r in [1.8, 11], 50 GHG fields, Kerr-Schild Schwarzschild plus a seeded l <= 4
+perturbation of amplitude 1e-4, Yn filter (L = 46) on every stage right-hand
+side, dt = 0.25 min dx.  A "step" is one full RK4 step: four evaluations of
+derivatives + GHG right-hand side + boundary condition + Yn filter, and the
+stage updates.  Inputs are synthetic (seeded generator).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Multi-GPU (torchrun): one independent shell per rank
+(replicas, weak scaling, no data-path collective); value = all ranks' units
+divided by the slowest rank's time.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pt·field RK4 updates/s, mixed vs FP64 path on GB300 at ≤1e-10 err vs FP64 oracle"
+UNIT = "pt·field/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ks_33x48x96")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 0, 1, None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group("gloo")
+    return dist.get_rank(), int(os.environ.get("LOCAL_RANK", "0")), ws, dist
+
+
+def _workload(name):
+    from paper_1104_3408_gb300 import inputs
+    w = dict(inputs.WORKLOADS[name])
+    w["name"] = name
+    return w
+
+
+def _state(w):
+    from paper_1104_3408_gb300 import inputs
+    return inputs.kerr_schild_state(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"],
+                                    amp=w["amp"], ell=w["ell"], seed=w["seed"])
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return p.get("hbm_gbs", 6800.0), p.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) > 8:
+                for k, n in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _time_steps(sh, u, dt, K, flush, torch):
+    """K single RK4 steps, L2 flushed (256 MiB write) before each; CUDA events
+    on the launching stream around each step.  Returns total ms."""
+    st = torch.cuda.current_stream()
+    total = 0.0
+    evs = []
+    for _ in range(K):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        sh.rk4_step(u, dt, 1)
+        b.record(st)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    for a, b in evs:
+        total += a.elapsed_time(b)
+    return total
+
+
+def _op_units(w, phase):
+    """Algorithmic work of one launch of an operator group (per stage), as
+    (FP64-equivalent flops, issued BF16 digit-product flops, bytes)."""
+    n_r, N, J, L, nv = w["n_r"], w["n_theta"], w["n_phi"], w["L"], w["n_fields"]
+    P = n_r * N * J
+    R = 2 * L + 1
+    pairs = 21
+    if phase == "d_r":
+        fl = 2.0 * n_r * n_r * nv * J * N
+    elif phase == "d_theta":
+        fl = 2.0 * (2 * N) * (2 * N) * nv * (J // 2) * n_r
+    elif phase == "d_phi":
+        fl = 2.0 * J * J * nv * N * n_r
+    elif phase == "dft_fwd":
+        fl = 2.0 * R * J * nv * N * n_r
+    elif phase == "dft_inv":
+        fl = 2.0 * J * R * nv * N * n_r
+    else:
+        return None
+    byts = 8.0 * nv * P * 2  # read + write of one field array, FP64
+    return fl, fl * pairs, byts
+
+
+def run_ours(args, rank, local_rank, ws, dist):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3408_gb300 import cffyn
+
+    torch.cuda.set_device(local_rank)
+    w = _workload(args.workload)
+    n_r, N, J, L = w["n_r"], w["n_theta"], w["n_phi"], w["L"]
+    P = n_r * N * J
+    units_per_step = P * w["n_fields"]
+    u0 = _state(w)
+
+    sh = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, precision=cffyn.MIXED)
+    dt = w["lam"] * sh.default_dt() / 0.25
+    u = torch.from_numpy(u0).cuda()
+    sh.init_gauge_from_state(u)
+    uf = torch.empty_like(u)
+    sh.filter(u, uf)
+    u.copy_(uf)
+    for _ in range(max(args.warmup, 3)):
+        sh.rk4_step(u, dt, 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sh.set_trace(True)
+    sh.rk4_step(u, dt, 1)          # capture the traced graph outside the timed region
+    sh.set_trace(True)             # reset totals
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    # keep the GPU loaded for ~1 s before the timed region so that the 200 ms
+    # clock samples cover a loaded period that ends in the timed region
+    sh.set_trace(False)
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 1.0:
+        sh.rk4_step(u, dt, 1)
+    sh.set_trace(True)
+    sh.rk4_step(u, dt, 1)
+    sh.set_trace(True)
+    torch.cuda.synchronize()
+    t_ms = _time_steps(sh, u, dt, args.steps, flush, torch)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    trace_ms, launches, tsteps = sh.get_trace()
+    sh.set_trace(False)
+    t_max = t_ms
+    if dist:
+        t = torch.tensor([t_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = units_per_step * args.steps * ws / (t_max * 1e-3)
+
+    if rank != 0:
+        return None
+
+    # ---- dominant kernel group, live from the traced timed region
+    hbm, bf16, peak_kind = _peaks()
+    per_step = {k: v / max(tsteps, 1) for k, v in trace_ms.items()}
+    dom = max(per_step, key=per_step.get)
+    nl = max(launches[dom], 1)
+    launch_ms = per_step[dom] / nl
+    units = _op_units(w, dom)
+    if units is not None:
+        fl64, flbf, byts = units
+        achieved = flbf / (launch_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k_op_ozaki (" + dom + ")", "achieved": achieved,
+                "peak": bf16, "unit": "TFLOP/s", "frac": achieved / bf16, "traffic": None,
+                "peak_source": f"bf16_tflops ({peak_kind})",
+                "fp64_equiv_tflops": fl64 / (launch_ms * 1e-3) / 1e12,
+                "launch_ms": launch_ms}
+    else:
+        # pointwise groups: algorithmic bytes of the group's FP64 arrays
+        nvP = w["n_fields"] * P * 8.0
+        byts = {"rhs": nvP * (1 + 3 + 1) + 16 * P * 8.0, "decompose": 2 * nvP,
+                "reconstruct": 5 * nvP, "project": 2 * nvP * (2 * L + 1) / J}[dom]
+        achieved = byts / (launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": f"hbm_gbs ({peak_kind})",
+                "launch_ms": launch_ms}
+
+    # ---- plain FP64 GPU path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        s64 = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, precision=cffyn.FP64)
+        v = torch.from_numpy(u0).cuda()
+        s64.init_gauge_from_state(v)
+        vf = torch.empty_like(v)
+        s64.filter(v, vf)
+        v.copy_(vf)
+        for _ in range(2):
+            s64.rk4_step(v, dt, 1)
+        k64 = max(2, min(args.steps, 5))
+        t64 = _time_steps(s64, v, dt, k64, flush, torch)
+        fp64_value = units_per_step * k64 / (t64 * 1e-3)
+        # accuracy: 100 steps of both paths from the same filtered state
+        a = torch.from_numpy(u0).cuda()
+        sh.init_gauge_from_state(a)
+        sh.filter(a, uf)
+        a.copy_(uf)
+        b = a.clone()
+        sh.rk4_step(a, dt, 100)
+        s64.rk4_step(b, dt, 100)
+        err = float((a - b).abs().max() / b.abs().max())
+        s64.destroy()
+        fp64 = {"value": fp64_value, "steps": k64, "mixed_over_fp64": value / ws / fp64_value,
+                "err_fields_100_steps_vs_fp64_gpu": err}
+
+    # ---- end to end through the C-ABI with host buffers
+    hu = torch.from_numpy(u0).pin_memory()
+    hout = torch.empty_like(hu).pin_memory()
+    dbuf = torch.empty_like(u)
+    sh.init_gauge_from_state(dbuf.copy_(hu))
+    ke = max(3, min(args.steps, 10))
+    st = torch.cuda.current_stream()
+    dbuf.copy_(hu, non_blocking=True)
+    sh.rk4_step(dbuf, dt, 1)
+    torch.cuda.synchronize()
+    a_ev = torch.cuda.Event(enable_timing=True)
+    b_ev = torch.cuda.Event(enable_timing=True)
+    a_ev.record(st)
+    for _ in range(ke):
+        dbuf.copy_(hu, non_blocking=True)
+        sh.rk4_step(dbuf, dt, 1)
+        hout.copy_(dbuf, non_blocking=True)
+    b_ev.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = a_ev.elapsed_time(b_ev)
+    e2e = {"value": units_per_step * ke / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": int(u.numel() * 8), "d2h_bytes_per_step": int(u.numel() * 8),
+           "steps": ke}
+
+    # ---- CPU oracle on a bounded sample
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = _cpu_baseline(w, u0)
+
+    launches_per_step = sum(launches.values())
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: bf16-digit tensor products (exact fp32 sums, int64 recombination), "
+                 "fp32-pair pointwise, f64 state",
+        "data": "synthetic (seeded Kerr-Schild + l<=4 perturbation, amplitude 1e-4)",
+        "config": {"workload": w["name"], "n_r": n_r, "n_theta": N, "n_phi": J,
+                   "n_fields": w["n_fields"], "L": L, "r": [w["r_in"], w["r_out"]],
+                   "dt": dt, "filter": "Yn on every stage rhs", "precision": "mixed",
+                   "parallelism": f"replicas x{ws}",
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "roofline": roof,
+        "phase_ms_per_step": per_step,
+        "launches_per_step": launches,
+        "gpu_launches": launches_per_step * args.steps,
+        "fp64_gpu": fp64,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    sh.destroy()
+    return out
+
+
+def _cpu_baseline(w, u0, nthreads=None):
+    """The oracle, as it stands, on one RK4 stage (derivatives + right-hand side
+    + boundary + Yn filter) of the same workload: a quarter of a step."""
+    import oracle
+    t0 = time.perf_counter()
+    sh = oracle.OracleShell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"])
+    sh.init_gauge_from_state(u0)
+    _ = sh.sf
+    t1 = time.perf_counter()
+    k = sh.stage(u0)
+    t2 = time.perf_counter()
+    del k
+    units = w["n_r"] * w["n_theta"] * w["n_phi"] * w["n_fields"] / 4.0
+    return {"value": units / (t2 - t1), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one RK4 stage (rhs + BC + Yn filter) of the same shell = 1/4 step; "
+                      f"setup {t1 - t0:.1f} s excluded; numpy FP64",
+            "seconds": t2 - t1}
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle on the host cores, same workload and metric;
+    each step is one RK4 stage sample (a quarter of a full step)."""
+    if rank != 0:
+        return None
+    w = _workload(args.workload)
+    u0 = _state(w)
+    import oracle
+    sh = oracle.OracleShell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"])
+    sh.init_gauge_from_state(u0)
+    _ = sh.sf
+    for _ in range(min(args.warmup, 1)):
+        sh.stage(u0)
+    budget = 240.0
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sh.stage(u0)
+        times.append(time.perf_counter() - t0)
+        if sum(times) > budget:
+            break
+    units = w["n_r"] * w["n_theta"] * w["n_phi"] * w["n_fields"] / 4.0
+    value = units * len(times) / sum(times)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": len(times),
+        "steps_requested": args.steps, "warmup": min(args.warmup, 1),
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": w["name"], "n_r": w["n_r"], "n_theta": w["n_theta"],
+                   "n_phi": w["n_phi"], "n_fields": w["n_fields"], "L": w["L"],
+                   "step": "one RK4 stage (rhs + BC + Yn filter) = 1/4 RK4 step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "one RK4 stage of the same shell per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = _args()
+    rank, local_rank, ws, dist = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        out = run_ours(args, rank, local_rank, ws, dist)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -172,6 +172,17 @@ CFFYN_API int cffyn_get_operator(const cffyn_shell* sh, int which, double* host_
 CFFYN_API int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out,
                                  int* launches_out, void* stream);
 
+/* Live tracing of cffyn_rk4_step: with tracing on, the captured step graph
+ * records a CUDA event after every kernel group (same groups as
+ * cffyn_profile_step) and each cffyn_rk4_step call adds the group durations
+ * of its last replay (times n_steps) to per-group totals.  Switching tracing
+ * on or off resets the totals and re-captures the graph on the next step. */
+CFFYN_API int cffyn_set_trace(cffyn_shell* sh, int on);
+/* Per-group totals in ms, kernel launches per step per group, and the number
+ * of traced steps.  Host memory, CFFYN_PROFILE_PHASES entries each. */
+CFFYN_API int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launches_out,
+                              long long* steps);
+
 /* Message of the last failing call on this thread (never NULL). */
 CFFYN_API const char* cffyn_last_error(void);
 

@@ -22,7 +22,7 @@ EXPORTED = [
     "cffyn_default_dt", "cffyn_set_gauge", "cffyn_init_gauge_from_state", "cffyn_derivs",
     "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_constraint_norms",
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
-    "cffyn_profile_step",
+    "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace",
 ]
 PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs", "decompose", "dft_fwd", "project", "dft_inv",
                   "reconstruct"]
@@ -73,6 +73,9 @@ def load(path=LIB_PATH):
         "cffyn_get_operator": ([vp, i, ctypes.POINTER(ctypes.c_double)], i),
         "cffyn_profile_step": ([vp, dp, d, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_int), vp], i),
+        "cffyn_set_trace": ([vp, i], i),
+        "cffyn_get_trace": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_longlong)], i),
         "cffyn_last_error": ([], ctypes.c_char_p),
         "cffyn_version": ([], ctypes.c_char_p),
     }
@@ -170,6 +173,19 @@ class Shell:
         la = (ctypes.c_int * n)()
         _check(load().cffyn_profile_step(self.h, _ptr(u, "u"), float(dt), ms, la, _stream(stream)))
         return {k: (float(ms[i]), int(la[i])) for i, k in enumerate(PROFILE_PHASES)}
+
+    def set_trace(self, on=True):
+        _check(load().cffyn_set_trace(self.h, 1 if on else 0))
+
+    def get_trace(self):
+        """({group: total ms}, {group: launches per step}, traced steps)."""
+        n = len(PROFILE_PHASES)
+        ms = (ctypes.c_double * n)()
+        la = (ctypes.c_int * n)()
+        st = ctypes.c_longlong()
+        _check(load().cffyn_get_trace(self.h, ms, la, ctypes.byref(st)))
+        return ({k: float(ms[i]) for i, k in enumerate(PROFILE_PHASES)},
+                {k: int(la[i]) for i, k in enumerate(PROFILE_PHASES)}, int(st.value))
 
     def constraint_norms(self, u, stream=None):
         out = (ctypes.c_double * 2)()

@@ -111,6 +111,8 @@ void free_shell(cffyn_shell* sh) {
   if (sh->flag_host) cudaFreeHost(sh->flag_host);
   if (sh->flag) cudaFree(sh->flag);
   if (sh->graph) cudaGraphExecDestroy(sh->graph);
+  for (int i = 0; i < cffyn_shell::kMaxMarks; ++i)
+    if (sh->marks[i]) cudaEventDestroy(sh->marks[i]);
   delete sh;
 }
 
@@ -308,31 +310,71 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
   return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
 }
 
-// One RK4 step on u (enqueued on st); see cffyn_rk4_step.
+// One RK4 step on u (enqueued on st); see cffyn_rk4_step.  With tracing on,
+// an event is recorded after every kernel group; mark_phase says which group
+// ended at each mark, launches_per_step counts kernel launches per group.
 static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) {
   const size_t nvP = (size_t)sh->nv * sh->P;
   const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
+  const bool tr = sh->trace != 0;
   int rc;
+  int nm = 0;
+  for (int k = 0; k < cffyn_shell::kPhases; ++k) sh->launches_per_step[k] = 0;
+  auto mark = [&](int phase) -> int {
+    if (!tr) return CFFYN_OK;
+    if (nm >= cffyn_shell::kMaxMarks || !sh->marks[nm]) return CFFYN_OK;
+    sh->mark_phase[nm] = phase;
+    // inside a capture a plain record only joins streams; External makes it an
+    // event-record node of the graph
+    CF_CUDA(cudaEventRecordWithFlags(sh->marks[nm], st, cudaEventRecordExternal));
+    ++nm;
+    return CFFYN_OK;
+  };
+  auto run = [&](int phase, auto&& fn) -> int {
+    long long l0 = g_launches;
+    int r = fn();
+    if (r) return r;
+    sh->launches_per_step[phase] += (int)(g_launches - l0);
+    return mark(phase);
+  };
+  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  if ((rc = mark(-1))) return rc;
   for (int s = 0; s < 4; ++s) {
     const double* X = s == 0 ? u : sh->U;
-    if ((rc = derivs_spherical(sh, X, sh->D, sh->nv, st))) return rc;
-    if ((rc = pw_rhs(sh, X, sh->D, sh->S, st))) return rc;
+    double* spin = sh->D + 2 * nvP;  // derivatives are dead after the rhs
+    if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, st); }))) return rc;
+    if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, st); }))) return rc;
+    if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, st); }))) return rc;
+    if ((rc = run(3, [&] { return pw_rhs(sh, X, sh->D, sh->S, st); }))) return rc;
     if (per_sub) {
-      double* spin = sh->D;  // derivatives are dead after the rhs
-      if ((rc = pw_decompose(sh, sh->S, spin + 2 * nvP, st))) return rc;
-      // filter_spin_slots uses D[0..2nvP) as coefficient scratch
-      if ((rc = filter_spin_slots(sh, spin + 2 * nvP, st))) return rc;
-      if ((rc = pw_reconstruct(sh, spin + 2 * nvP, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st)))
+      if ((rc = run(4, [&] { return pw_decompose(sh, sh->S, spin, st); }))) return rc;
+      if ((rc = run(5, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return rc;
+      if ((rc = run(6, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+        return rc;
+      if ((rc = run(7, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) return rc;
+      if ((rc = run(8, [&] {
+             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+           })))
         return rc;
     } else {
-      if ((rc = pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st))) return rc;
+      if ((rc = run(8, [&] {
+             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+           })))
+        return rc;
     }
   }
   if (!per_sub) {
-    if ((rc = pw_decompose(sh, u, sh->S, st))) return rc;
-    if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
-    if ((rc = pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st))) return rc;
+    if ((rc = run(4, [&] { return pw_decompose(sh, u, sh->S, st); }))) return rc;
+    if ((rc = run(5, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); }))) return rc;
+    if ((rc = run(6, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+      return rc;
+    if ((rc = run(7, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); }))) return rc;
+    if ((rc = run(8, [&] {
+           return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+         })))
+      return rc;
   }
+  sh->n_marks = nm;
   return CFFYN_OK;
 }
 
@@ -348,7 +390,7 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
   if (n_steps == 0) return CFFYN_OK;
   if (!(dt > 0)) dt = sh->dt_default;
   cudaStream_t st = (cudaStream_t)stream;
-  if (!sh->graph || sh->graph_u != u || sh->graph_dt != dt) {
+  if (!sh->graph || sh->graph_u != u || sh->graph_dt != dt || sh->graph_trace != sh->trace) {
     if (sh->graph) {
       cudaGraphExecDestroy(sh->graph);
       sh->graph = nullptr;
@@ -371,15 +413,51 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
     }
     sh->graph_u = u;
     sh->graph_dt = dt;
+    sh->graph_trace = sh->trace;
   }
   CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
   for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
   CF_CUDA(cudaMemcpyAsync(sh->flag_host, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(cudaStreamSynchronize(st));
+  if (sh->trace && sh->graph_trace && sh->n_marks > 1) {
+    // the marks hold the last replay; count it n_steps times
+    for (int i = 1; i < sh->n_marks; ++i) {
+      float ms = 0.f;
+      cudaError_t e = cudaEventElapsedTime(&ms, sh->marks[i - 1], sh->marks[i]);
+      if (e != cudaSuccess) {
+        cudaGetLastError();  // do not leave the failure for the next launch check
+        set_error("trace: %s", cudaGetErrorString(e));
+        return CFFYN_ECUDA;
+      }
+      if (sh->mark_phase[i] >= 0) sh->trace_ms[sh->mark_phase[i]] += (double)ms * n_steps;
+    }
+    sh->trace_steps += n_steps;
+  }
   if (*sh->flag_host) {
     set_error("non-finite value in a stage right-hand side");
     return CFFYN_ENONFINITE;
   }
+  return CFFYN_OK;
+}
+
+int cffyn_set_trace(cffyn_shell* sh, int on) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  sh->trace = on ? 1 : 0;
+  if (sh->trace)  // events are created here, never during a stream capture
+    for (int i = 0; i < cffyn_shell::kMaxMarks; ++i)
+      if (!sh->marks[i]) CF_CUDA(cudaEventCreate(&sh->marks[i]));
+  for (int k = 0; k < cffyn_shell::kPhases; ++k) sh->trace_ms[k] = 0.0;
+  sh->trace_steps = 0;
+  return CFFYN_OK;
+}
+
+int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launches_out, long long* steps) {
+  if (!sh || !ms_out || !launches_out || !steps) { set_error("NULL argument"); return CFFYN_EINVAL; }
+  for (int k = 0; k < cffyn_shell::kPhases; ++k) {
+    ms_out[k] = sh->trace_ms[k];
+    launches_out[k] = sh->launches_per_step[k];
+  }
+  *steps = sh->trace_steps;
   return CFFYN_OK;
 }
 

@@ -109,5 +109,17 @@ struct cffyn_shell {
   cudaGraphExec_t graph = nullptr;
   double* graph_u = nullptr;
   double graph_dt = 0.0;
+  int graph_trace = 0;
   cudaStream_t graph_stream = nullptr;
+
+  // tracing: event nodes at every phase boundary of the captured step
+  int trace = 0;
+  static constexpr int kPhases = 9;
+  static constexpr int kMaxMarks = 64;
+  cudaEvent_t marks[kMaxMarks] = {};
+  int mark_phase[kMaxMarks] = {};   // phase that ends at mark i (-1: start)
+  int n_marks = 0;
+  int launches_per_step[kPhases] = {};
+  double trace_ms[kPhases] = {};
+  long long trace_steps = 0;
 };

@@ -183,3 +183,30 @@ def test_nonfinite_state_is_reported(cf):
     sh.rk4_step(v, 0.0, 1)
     assert torch.isfinite(v).all()
     sh.destroy()
+
+
+def test_trace_and_profile_report_every_kernel_group(cf):
+    n_r, N, J, L = 9, 12, 24, 10
+    u0 = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-6, ell=2, seed=0)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L)
+    u = dev(u0)
+    sh.init_gauge_from_state(u)
+    sh.set_trace(True)
+    for _ in range(3):
+        sh.rk4_step(u, 0.0, 1)
+    ms, launches, steps = sh.get_trace()
+    assert steps == 3
+    assert all(v > 0 for v in ms.values())
+    assert launches["project"] == 16 and launches["d_r"] == 4 and sum(launches.values()) == 48
+    # tracing does not change the result
+    v = dev(u0)
+    w = dev(u0)
+    sh.set_trace(False)
+    sh.rk4_step(v, 0.0, 2)
+    sh.set_trace(True)
+    sh.rk4_step(w, 0.0, 2)
+    assert torch.equal(v, w)
+    prof = sh.profile_step(dev(u0))
+    assert all(t > 0 and n > 0 for t, n in prof.values())
+    assert {k: n for k, (t, n) in prof.items()} == launches
+    sh.destroy()
