@@ -100,7 +100,7 @@ void free_shell(cffyn_shell* sh) {
   double** ptrs[] = {&sh->r,     &sh->sth,    &sh->cth,    &sh->sph, &sh->cph,  &sh->Dr,   &sh->Dth2,
                      &sh->Dph,   &sh->Fan,    &sh->Fsy,    &sh->Fraw, &sh->Fproj0, &sh->FprojC,
                      &sh->H,     &sh->dH,     &sh->U,      &sh->kacc, &sh->D,    &sh->S,
-                     &sh->red};
+                     &sh->Rsrc,  &sh->red};
   for (double** p : ptrs)
     if (*p) cudaFree(*p);
   SlicedOp* so[] = {&sh->sDr, &sh->sDth2, &sh->sDph, &sh->sFan, &sh->sFsy, &sh->sF0,
@@ -200,7 +200,7 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     return CFFYN_OK;
   };
   if ((rc = alloc(&sh->U, nvP)) || (rc = alloc(&sh->kacc, nvP)) || (rc = alloc(&sh->D, 3 * nvP)) ||
-      (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, 12 * sh->P)) ||
+      (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->Rsrc, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, 12 * sh->P)) ||
       (rc = alloc(&sh->red, 2)))
     return fail(rc);
   {

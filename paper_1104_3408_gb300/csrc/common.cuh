@@ -99,6 +99,7 @@ struct cffyn_shell {
   double* kacc = nullptr;  // RK4 accumulator [nv][P]
   double* D = nullptr;     // spherical derivatives [3][nv][P] (also DFT coefficients)
   double* S = nullptr;     // rhs / spin functions [nv][P]
+  double* Rsrc = nullptr;  // right-hand-side source terms [nv][P]
   double* red = nullptr;   // device reduction words (2 doubles)
   int* flag = nullptr;     // device non-finite flag
   int* flag_host = nullptr;  // pinned host copy of the flag

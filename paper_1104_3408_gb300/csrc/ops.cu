@@ -226,14 +226,15 @@ constexpr int OZ_QT = 32;        // columns per CTA (4 n-tiles of 8)
 constexpr int OZ_NT = OZ_QT / 8;
 constexpr int OZ_MAXK = 192;
 constexpr int OZ_KCHUNK = 6;     // k-steps (of 16) per exact partial sum
+constexpr int OZ_ITEMS = 16;     // (k pair, column) items per thread in the prologue
 
 __device__ __forceinline__ int exp_field(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
-// 47-bit fixed point of x relative to 2^E, cut into six balanced base-256
-// digits (d0 most significant), each returned as BF16 bits.
-__device__ __forceinline__ void digits_bf16(double x, int E, unsigned short out[kSlices]) {
+// 47-bit fixed point Z = round(x 2^(47-E)) of x relative to 2^E (|x| < 2^E),
+// integer operations only.
+__device__ __forceinline__ long long fixed47(double x, int E) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7ff);
   long long Z = 0;
@@ -243,16 +244,27 @@ __device__ __forceinline__ void digits_bf16(double x, int E, unsigned short out[
     if (sh < 54) Z = (long long)((M + (1ull << (sh - 1))) >> sh);
     if (b >> 63) Z = -Z;
   }
-#pragma unroll
-  for (int i = kSlices - 1; i >= 1; --i) {
-    int lo = (int)(Z & 255);
-    lo = lo >= 128 ? lo - 256 : lo;
-    Z = (Z - lo) >> 8;
-    float f = __int_as_float(0x4B400000 + lo) - 12582912.0f;  // exact small integer
-    out[i] = (unsigned short)(__float_as_uint(f) >> 16);
-  }
-  float f0 = __int_as_float(0x4B400000 + (int)Z) - 12582912.0f;
-  out[0] = (unsigned short)(__float_as_uint(f0) >> 16);
+  return Z;
+}
+
+// Balanced base-256 digits of Z (|Z| <= 2^47): with Zb = Z + sum_{k<5} 128*256^k
+// byte k of Zb is e_k + 128 for the five low digits and Zb >> 40 is the top
+// digit.  Returned as BF16 bit patterns, slice 0 = most significant.
+__device__ __forceinline__ void digits_bf16(long long Z, unsigned int out[kSlices]) {
+  const long long Zb = Z + 0x8080808080ll;
+  const unsigned int lo = (unsigned int)Zb;
+  const int hi = (int)(Zb >> 32);
+  // bf16(b - 128) for a byte b: exact small integer through the 1.5*2^23 trick
+  auto bf = [](int b) -> unsigned int {
+    return __float_as_uint(__int_as_float(0x4B400000 + b) - 12583040.0f) >> 16;
+  };
+  out[5] = bf((int)(lo & 255u));
+  out[4] = bf((int)((lo >> 8) & 255u));
+  out[3] = bf((int)((lo >> 16) & 255u));
+  out[2] = bf((int)(lo >> 24));
+  out[1] = bf(hi & 255);
+  const int top = hi >> 8;  // arithmetic shift: the signed top digit
+  out[0] = __float_as_uint(__int_as_float(0x4B400000 + top) - 12582912.0f) >> 16;
 }
 
 // FP32 value holding an exact integer |v| < 2^24 -> int, integer ops only.
@@ -319,23 +331,40 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
   __syncthreads();
   const bool kfast = a.kind == OP_R;
   const int Kp = ksteps * 16;
-  // pass 1: column exponents
-  for (int e = tid; e < K * OZ_QT; e += nthr) {
-    int k, c;
-    if (kfast) { k = e % K; c = e / K; } else { c = e % OZ_QT; k = e / OZ_QT; }
-    double v = load_elem(a, cols[c], k);
-    if (v != 0.0) atomicMax(&colE[c], exp_field(v) - 1022);
+  const int KH = Kp / 2;                 // k pairs per column
+  const int KPW = KP / 2;                // row pitch in 32-bit words
+  unsigned int* Bw = reinterpret_cast<unsigned int*>(Bs);
+  const int nitems = KH * OZ_QT;
+  // one pass over global memory: values stay in registers between the column
+  // exponent reduction and the digit extraction
+  double v0[OZ_ITEMS], v1[OZ_ITEMS];
+#pragma unroll
+  for (int it = 0; it < OZ_ITEMS; ++it) {
+    const int e = tid + it * nthr;
+    v0[it] = v1[it] = 0.0;
+    if (e < nitems) {
+      int kp, c;
+      if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
+      v0[it] = load_elem(a, cols[c], 2 * kp);
+      v1[it] = load_elem(a, cols[c], 2 * kp + 1);
+      const int ex = max(v0[it] != 0.0 ? exp_field(v0[it]) : 0, v1[it] != 0.0 ? exp_field(v1[it]) : 0);
+      if (ex) atomicMax(&colE[c], ex - 1022);
+    }
   }
   __syncthreads();
-  // pass 2: digits (re-read: the tile is L1/L2 resident)
-  for (int e = tid; e < Kp * OZ_QT; e += nthr) {
-    int k, c;
-    if (kfast) { k = e % Kp; c = e / Kp; } else { c = e % OZ_QT; k = e / OZ_QT; }
-    double v = k < K ? load_elem(a, cols[c], k) : 0.0;
-    unsigned short dg[kSlices];
-    digits_bf16(v, colE[c], dg);
 #pragma unroll
-    for (int s = 0; s < kSlices; ++s) Bs[((size_t)s * OZ_QT + c) * KP + k] = dg[s];
+  for (int it = 0; it < OZ_ITEMS; ++it) {
+    const int e = tid + it * nthr;
+    if (e < nitems) {
+      int kp, c;
+      if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
+      const int E = colE[c];
+      unsigned int d0[kSlices], d1[kSlices];
+      digits_bf16(fixed47(v0[it], E), d0);
+      digits_bf16(fixed47(v1[it], E), d1);
+#pragma unroll
+      for (int s2 = 0; s2 < kSlices; ++s2) Bw[((size_t)s2 * OZ_QT + c) * KPW + kp] = d0[s2] | (d1[s2] << 16);
+    }
   }
   __syncthreads();
 
@@ -413,7 +442,10 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
     unsigned gx = (unsigned)((a.g.ncols + OZ_QT - 1) / OZ_QT);
     int KP = Ws->ksteps * 16 + 8;
     size_t smem = (size_t)kSlices * OZ_QT * KP * sizeof(unsigned short);
-    int threads = Ws->mtiles * 32;
+    // one warp per m-tile, and enough threads that the prologue's items fit
+    int KH = Ws->ksteps * 8;
+    int warps = max(Ws->mtiles, (KH + OZ_ITEMS - 1) / OZ_ITEMS);
+    int threads = warps * 32;
     k_op_ozaki<<<dim3(gx, extra.y), threads, smem, st>>>(a, *Ws);
     count_launch();
   }

@@ -21,407 +21,9 @@
 //                  C_a = H_a + Gamma_a (App. A.1).
 #include <cstdio>
 
-#include "common.cuh"
-#include "scalar.cuh"
+#include "pw_common.cuh"
 
 namespace cffyn {
-
-struct Geo {
-  int n_r, N, J, nv;
-  long long P;
-  const double *r, *sth, *cth, *sph, *cph;
-};
-
-// symmetric pair index of (a, b), a, b in 0..3 (tt,tx,ty,tz,xx,xy,xz,yy,yz,zz)
-__host__ __device__ constexpr int SI(int a, int b) {
-  return a > b ? SI(b, a) : (a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9)));
-}
-
-template <class T>
-struct Jac {
-  // d/dx^k = J[k][0] d_r + J[k][1] d_theta + J[k][2] d_phi
-  T j[3][3];
-  T st, ct, sp, cp;
-};
-
-template <class T>
-__device__ __forceinline__ Jac<T> jacobian(const Geo& g, int k, int i, int jj) {
-  Jac<T> J;
-  const T st = S<T>::c(g.sth[i]), ct = S<T>::c(g.cth[i]);
-  const T sp = S<T>::c(g.sph[jj]), cp = S<T>::c(g.cph[jj]);
-  const T one = S<T>::c(1.0);
-  const T ir = one / S<T>::c(g.r[k]);
-  const T irs = ir / st;
-  J.j[0][0] = st * cp; J.j[0][1] = ct * cp * ir; J.j[0][2] = -(sp * irs);
-  J.j[1][0] = st * sp; J.j[1][1] = ct * sp * ir; J.j[1][2] = cp * irs;
-  J.j[2][0] = ct;      J.j[2][1] = -(st * ir);   J.j[2][2] = S<T>::c(0.0);
-  J.st = st; J.ct = ct; J.sp = sp; J.cp = cp;
-  return J;
-}
-
-// Cartesian derivative d_k of field mu at point p from the three spherical
-// derivative arrays D[3][nv][P].
-template <class T>
-__device__ __forceinline__ void cart3(const Jac<T>& J, const double* __restrict__ D, long long P,
-                                      int nv, int mu, long long p, T out[3]) {
-  const T dr = S<T>::load(D + (long long)mu * P + p);
-  const T dt = S<T>::load(D + ((long long)nv + mu) * P + p);
-  const T dp = S<T>::load(D + ((long long)2 * nv + mu) * P + p);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) out[k] = J.j[k][0] * dr + J.j[k][1] * dt + J.j[k][2] * dp;
-}
-
-// 3+1 quantities and Christoffel symbols from the undifferentiated fields.
-template <class T>
-struct Metric {
-  T gi4[10];          // g^ab (symmetric pairs)
-  T gi[3][3];         // gamma^ij
-  T bu[3];            // beta^i
-  T alpha, ialpha;
-  T nu[4];            // n^a
-};
-
-template <class T>
-__device__ __forceinline__ void metric_from(const T g[10], Metric<T>& M) {
-  const T gxx = g[4], gxy = g[5], gxz = g[6], gyy = g[7], gyz = g[8], gzz = g[9];
-  const T cxx = gyy * gzz - gyz * gyz, cxy = gxz * gyz - gxy * gzz, cxz = gxy * gyz - gxz * gyy;
-  const T cyy = gxx * gzz - gxz * gxz, cyz = gxy * gxz - gxx * gyz, czz = gxx * gyy - gxy * gxy;
-  const T idet = S<T>::c(1.0) / (gxx * cxx + gxy * cxy + gxz * cxz);
-  M.gi[0][0] = cxx * idet; M.gi[0][1] = M.gi[1][0] = cxy * idet; M.gi[0][2] = M.gi[2][0] = cxz * idet;
-  M.gi[1][1] = cyy * idet; M.gi[1][2] = M.gi[2][1] = cyz * idet; M.gi[2][2] = czz * idet;
-  const T b[3] = {g[1], g[2], g[3]};
-#pragma unroll
-  for (int i = 0; i < 3; ++i) M.bu[i] = M.gi[i][0] * b[0] + M.gi[i][1] * b[1] + M.gi[i][2] * b[2];
-  const T a2 = b[0] * M.bu[0] + b[1] * M.bu[1] + b[2] * M.bu[2] - g[0];
-  M.alpha = sqrt_s(a2);
-  M.ialpha = S<T>::c(1.0) / M.alpha;
-  const T ia2 = M.ialpha * M.ialpha;
-  M.nu[0] = M.ialpha;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) M.nu[i + 1] = -(M.bu[i] * M.ialpha);
-  M.gi4[0] = -ia2;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) M.gi4[SI(0, i + 1)] = M.bu[i] * ia2;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = i; j < 3; ++j) M.gi4[SI(i + 1, j + 1)] = M.gi[i][j] - M.bu[i] * M.bu[j] * ia2;
-}
-
-// dg4[c][s] = d_c g_ab; Gam[c][s] = Gamma_cab; Gc[c] = Gamma_c
-template <class T>
-__device__ __forceinline__ void christoffel(const Metric<T>& M, const T Pi[10], const T Ph[3][10],
-                                            T dg4[4][10], T Gam[4][10], T Gc[4]) {
-#pragma unroll
-  for (int s = 0; s < 10; ++s) {
-    dg4[0][s] = M.bu[0] * Ph[0][s] + M.bu[1] * Ph[1][s] + M.bu[2] * Ph[2][s] - M.alpha * Pi[s];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) dg4[i + 1][s] = Ph[i][s];
-  }
-  const T half = S<T>::c(0.5);
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b)
-        Gam[c][SI(a, b)] = half * (dg4[a][SI(b, c)] + dg4[b][SI(a, c)] - dg4[c][SI(a, b)]);
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    T acc = S<T>::c(0.0);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc = acc + M.gi4[SI(a, b)] * Gam[c][SI(a, b)];
-    Gc[c] = acc;
-  }
-}
-
-template <class T>
-__global__ void __launch_bounds__(128) k_rhs(const double* __restrict__ u, const double* __restrict__ D,
-                                             const double* __restrict__ H,
-                                             const double* __restrict__ dH, double* __restrict__ out,
-                                             Geo geo) {
-  const long long P = geo.P;
-  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const int k = (int)(p % geo.n_r);
-  const int i = (int)((p / geo.n_r) % geo.N);
-  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
-  const int nv = geo.nv;
-  const Jac<T> Jc = jacobian<T>(geo, k, i, jj);
-  const T zero = S<T>::c(0.0), half = S<T>::c(0.5), two = S<T>::c(2.0);
-
-  T g[10], Pi[10], Ph[3][10];
-#pragma unroll
-  for (int s = 0; s < 10; ++s) {
-    g[s] = S<T>::load(u + (long long)s * P + p);
-    Pi[s] = S<T>::load(u + (long long)(10 + s) * P + p);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) Ph[a][s] = S<T>::load(u + (long long)(20 + 10 * a + s) * P + p);
-  }
-  Metric<T> M;
-  metric_from(g, M);
-  T dg4[4][10], Gam[4][10], Gc[4];
-  christoffel(M, Pi, Ph, dg4, Gam, Gc);
-
-  // gauge source and its derivatives
-  T Hd[4], dHd[4][4];  // dHd[a][b] = d_a H_b
-  if (nv == 50) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      Hd[a] = S<T>::load(H + (long long)a * P + p);
-      dHd[0][a] = zero;
-#pragma unroll
-      for (int x = 0; x < 3; ++x) dHd[x + 1][a] = S<T>::load(dH + ((long long)x * 4 + a) * P + p);
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      Hd[a] = S<T>::load(u + (long long)(50 + a) * P + p);
-      dHd[0][a] = nv == 58 ? S<T>::load(u + (long long)(54 + a) * P + p) : zero;
-      T c3[3];
-      cart3(Jc, D, P, nv, 50 + a, p, c3);
-#pragma unroll
-      for (int x = 0; x < 3; ++x) dHd[x + 1][a] = c3[x];
-    }
-  }
-  T C[4], Hup[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) C[a] = Hd[a] + Gc[a];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    T acc = zero;
-#pragma unroll
-    for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Hd[d];
-    Hup[c] = acc;
-  }
-  const T nC = M.nu[0] * C[0] + M.nu[1] * C[1] + M.nu[2] * C[2] + M.nu[3] * C[3];
-
-  // ---- source part of d_t Pi_ab: SPi[s]
-  T SPi[10];
-  {
-    // Q2_ab = Pi_ac Pi_b^c, Pi_b^c = g^cd Pi_bd
-    T Piu[4][4];  // Piu[b][c]
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        T acc = zero;
-#pragma unroll
-        for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Pi[SI(b, d)];
-        Piu[b][c] = acc;
-      }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b) {
-        T acc = zero;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc = acc + Pi[SI(a, c)] * Piu[b][c];
-        SPi[SI(a, b)] = -acc;  // -Q2
-      }
-  }
-  {
-    // Q1_ab = sum_{i,c} Phi_iac V_ib^c, V_ib^c = gamma^ij Y_jb^c, Y_jb^c = g^cd Phi_jbd
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      T V[3][4];
-      {
-        T Y[3][4];
-#pragma unroll
-        for (int x = 0; x < 3; ++x)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            T acc = zero;
-#pragma unroll
-            for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Ph[x][SI(b, d)];
-            Y[x][c] = acc;
-          }
-#pragma unroll
-        for (int x = 0; x < 3; ++x)
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            V[x][c] = M.gi[x][0] * Y[0][c] + M.gi[x][1] * Y[1][c] + M.gi[x][2] * Y[2][c];
-      }
-#pragma unroll
-      for (int a = 0; a <= b; ++a) {
-        T acc = zero;
-#pragma unroll
-        for (int x = 0; x < 3; ++x)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc = acc + Ph[x][SI(a, c)] * V[x][c];
-        SPi[SI(a, b)] = SPi[SI(a, b)] + acc;  // + Q1
-      }
-    }
-  }
-  {
-    // Q3_ab = sum_{c,e} Gamma_ace Gamma_b^{ce}
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      T Gcf[4][4];  // Gamma_b^c_f = g^cd Gamma_bdf
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          T acc = zero;
-#pragma unroll
-          for (int d = 0; d < 4; ++d) acc = acc + M.gi4[SI(c, d)] * Gam[b][SI(d, f)];
-          Gcf[c][f] = acc;
-        }
-      T Gce[10];  // Gamma_b^{ce} (symmetric)
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int e = c; e < 4; ++e) {
-          T acc = zero;
-#pragma unroll
-          for (int f = 0; f < 4; ++f) acc = acc + M.gi4[SI(e, f)] * Gcf[c][f];
-          Gce[SI(c, e)] = acc;
-        }
-#pragma unroll
-      for (int a = 0; a <= b; ++a) {
-        T acc = zero;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc = acc + Gam[a][SI(c, e)] * Gce[SI(c, e)];
-        SPi[SI(a, b)] = SPi[SI(a, b)] - acc;  // - Q3
-      }
-    }
-  }
-  // remaining source terms of eq. Pidot
-  {
-    T nnPi = zero;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int d = 0; d < 4; ++d) nnPi = nnPi + M.nu[c] * M.nu[d] * Pi[SI(c, d)];
-    T nPi[3];  // n^c Pi_ci
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      T acc = zero;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc = acc + M.nu[c] * Pi[SI(c, x + 1)];
-      nPi[x] = acc;
-    }
-    T Vj[3];
-#pragma unroll
-    for (int y = 0; y < 3; ++y) Vj[y] = nPi[0] * M.gi[0][y] + nPi[1] * M.gi[1][y] + nPi[2] * M.gi[2][y];
-    const T nlo0 = -M.alpha;  // n_a = (-alpha, 0, 0, 0)
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b) {
-        const int s = SI(a, b);
-        // nabla_(a H_b) = 1/2 (d_a H_b + d_b H_a) - Gamma_cab H^c
-        T DH = half * (dHd[a][b] + dHd[b][a]);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) DH = DH - Gam[c][s] * Hup[c];
-        T v = two * M.alpha * SPi[s] - two * M.alpha * DH - half * M.alpha * nnPi * Pi[s];
-        T vphi = zero, bphi = zero;
-#pragma unroll
-        for (int x = 0; x < 3; ++x) {
-          vphi = vphi + Vj[x] * Ph[x][s];
-          bphi = bphi + M.bu[x] * Ph[x][s];
-        }
-        v = v - M.alpha * vphi + bphi;
-        // alpha (n_b C_a + n_a C_b - g_ab n^c C_c)
-        T nCab = -(g[s] * nC);
-        if (a == 0) nCab = nCab + nlo0 * C[b];
-        if (b == 0) nCab = nCab + nlo0 * C[a];
-        v = v + M.alpha * nCab;
-        SPi[s] = v;
-      }
-  }
-  // source part of d_t Phi_iab: SPh[x][s] (kept implicit: computed per s below)
-  T nnPhi[3], Mik[3][3];
-#pragma unroll
-  for (int x = 0; x < 3; ++x) {
-    T acc = zero;
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int d = 0; d < 4; ++d) acc = acc + M.nu[c] * M.nu[d] * Ph[x][SI(c, d)];
-    nnPhi[x] = acc;
-    T nP[3];  // n^c Phi_x,(y+1),c
-#pragma unroll
-    for (int y = 0; y < 3; ++y) {
-      T a2 = zero;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) a2 = a2 + M.nu[c] * Ph[x][SI(y + 1, c)];
-      nP[y] = a2;
-    }
-#pragma unroll
-    for (int z = 0; z < 3; ++z) Mik[x][z] = nP[0] * M.gi[0][z] + nP[1] * M.gi[1][z] + nP[2] * M.gi[2][z];
-  }
-
-  // boundary normal on the outermost sphere
-  const bool outer = (k == geo.n_r - 1);
-  T sl[3], su[3];
-  if (outer) {
-    const T l[3] = {Jc.st * Jc.cp, Jc.st * Jc.sp, Jc.ct};
-    T q = zero;
-#pragma unroll
-    for (int x = 0; x < 3; ++x)
-#pragma unroll
-      for (int y = 0; y < 3; ++y) q = q + M.gi[x][y] * l[x] * l[y];
-    const T iq = S<T>::c(1.0) / sqrt_s(q);
-#pragma unroll
-    for (int x = 0; x < 3; ++x) sl[x] = l[x] * iq;
-#pragma unroll
-    for (int x = 0; x < 3; ++x) su[x] = M.gi[x][0] * sl[0] + M.gi[x][1] * sl[1] + M.gi[x][2] * sl[2];
-  }
-
-  // ---- principal parts and output, one symmetric pair at a time
-#pragma unroll
-  for (int s = 0; s < 10; ++s) {
-    T dg[3], dPi[3], dPh[3][3];
-    cart3(Jc, D, P, nv, s, p, dg);
-    cart3(Jc, D, P, nv, 10 + s, p, dPi);
-#pragma unroll
-    for (int x = 0; x < 3; ++x) cart3(Jc, D, P, nv, 20 + 10 * x + s, p, dPh[x]);
-    const T rg = dg4[0][s];
-    T rPi = SPi[s];
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      rPi = rPi + M.bu[x] * (dPi[x] - dg[x]);
-#pragma unroll
-      for (int y = 0; y < 3; ++y) rPi = rPi - M.alpha * M.gi[x][y] * dPh[x][y];
-    }
-    T rPh[3];
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      T v = M.bu[0] * dPh[x][0] + M.bu[1] * dPh[x][1] + M.bu[2] * dPh[x][2];
-      v = v + M.alpha * (dg[x] - dPi[x] - Ph[x][s]);
-      v = v + half * M.alpha * nnPhi[x] * Pi[s];
-      T mp = zero;
-#pragma unroll
-      for (int z = 0; z < 3; ++z) mp = mp + Mik[x][z] * Ph[z][s];
-      rPh[x] = v + M.alpha * mp;
-    }
-    if (outer) {
-      const T sd = su[0] * rPh[0] + su[1] * rPh[1] + su[2] * rPh[2];
-      const T wplus = rPi + sd;
-      const T nPi = half * (rg + wplus);
-      const T w2 = half * (wplus - rg);
-#pragma unroll
-      for (int x = 0; x < 3; ++x) rPh[x] = sl[x] * w2;
-      rPi = nPi;
-    }
-    out[(long long)s * P + p] = S<T>::to_double(rg);
-    out[(long long)(10 + s) * P + p] = S<T>::to_double(rPi);
-#pragma unroll
-    for (int x = 0; x < 3; ++x) out[(long long)(20 + 10 * x + s) * P + p] = S<T>::to_double(rPh[x]);
-  }
-  if (nv > 50) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      out[(long long)(50 + a) * P + p] = nv == 58 ? u[(long long)(54 + a) * P + p] : 0.0;
-      if (nv == 58) out[(long long)(54 + a) * P + p] = 0.0;
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Spin decomposition in the real triad.  Rm rows: r, theta, phi.
@@ -872,34 +474,6 @@ __global__ void k_constraints(const double* __restrict__ u, const double* __rest
 
 // ---------------------------------------------------------------------------
 // Host launchers
-
-static Geo geo_of(const cffyn_shell* sh) {
-  Geo g;
-  g.n_r = sh->n_r;
-  g.N = sh->N;
-  g.J = sh->J;
-  g.nv = sh->nv;
-  g.P = (long long)sh->P;
-  g.r = sh->r;
-  g.sth = sh->sth;
-  g.cth = sh->cth;
-  g.sph = sh->sph;
-  g.cph = sh->cph;
-  return g;
-}
-
-static unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
-
-int pw_rhs(const cffyn_shell* sh, const double* u, const double* D, double* out, cudaStream_t st) {
-  Geo g = geo_of(sh);
-  if (sh->d.precision == CFFYN_MIXED)
-    k_rhs<ff><<<blocks_for(g.P, 128), 128, 0, st>>>(u, D, sh->H, sh->dH, out, g);
-  else
-    k_rhs<double><<<blocks_for(g.P, 128), 128, 0, st>>>(u, D, sh->H, sh->dH, out, g);
-  count_launch();
-  CF_CUDA(cudaGetLastError());
-  return CFFYN_OK;
-}
 
 int pw_decompose(const cffyn_shell* sh, const double* in, double* out, cudaStream_t st) {
   Geo g = geo_of(sh);

@@ -1,0 +1,486 @@
+// GHG right-hand side (paper App. A.1, eqs. gdot, Phidot, Pidot; gamma_0 =
+// gamma_2 = 1, gamma_1 = -1) with the freeze-incoming boundary condition of
+// App. A.2, as three pointwise kernels so that none of them spills registers
+// (the state of one point alone is 50 values; in the double-float path that
+// is 100 registers):
+//
+//   k_rhs_gamma  3+1 quantities (eqs. normal, abgfromgab), d_t g_ab (eq. gdot,
+//                written as the first ten outputs), Christoffel symbols from
+//                undifferentiated fields (eq. Gamma), Gamma_c, the gauge
+//                constraint C_a = H_a + Gamma_a, nabla_(a H_b), and the
+//                Gamma-Gamma term of eq. Pidot -> partial source of d_t Pi.
+//   k_rhs_quad   the Phi-Phi and Pi-Pi terms of eq. Pidot, the remaining
+//                algebraic terms of eqs. Pidot and Phidot -> sources.
+//   k_rhs_pp     principal parts -A^k d_k u from the spherical derivatives,
+//                with the chain rule (eq. dvdx) contracted into the shift and
+//                inverse metric once per point, plus the boundary condition
+//                on the outermost sphere.
+//
+// Source buffer src[50][P]: [0,10) source of d_t Pi_ab, [10,40) source of
+// d_t Phi_iab (10 + 10 i + s), 40 alpha, [41,44) beta^i, [44,50) gamma^ij
+// (xx, xy, xz, yy, yz, zz).
+#include "pw_common.cuh"
+
+namespace cffyn {
+
+template <class T>
+__device__ __forceinline__ T ldT(const double* a, long long P, long long p, int f) {
+  return S<T>::load(a + (long long)f * P + p);
+}
+template <class T>
+__device__ __forceinline__ void stT(double* a, long long P, long long p, int f, T v) {
+  a[(long long)f * P + p] = S<T>::to_double(v);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
+                                                   const double* __restrict__ H,
+                                                   const double* __restrict__ dH,
+                                                   double* __restrict__ src, double* __restrict__ out,
+                                                   Geo geo) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const T zero = S<T>::c(0.0), half = S<T>::c(0.5);
+
+  T g[10];
+#pragma unroll
+  for (int s = 0; s < 10; ++s) g[s] = ldT<T>(u, P, p, s);
+  Metric<T> M;
+  metric_from(g, M);
+  stT(src, P, p, 40, M.alpha);
+#pragma unroll
+  for (int x = 0; x < 3; ++x) stT(src, P, p, 41 + x, M.bu[x]);
+  stT(src, P, p, 44, M.gi[0][0]);
+  stT(src, P, p, 45, M.gi[0][1]);
+  stT(src, P, p, 46, M.gi[0][2]);
+  stT(src, P, p, 47, M.gi[1][1]);
+  stT(src, P, p, 48, M.gi[1][2]);
+  stT(src, P, p, 49, M.gi[2][2]);
+
+  // d_t g_ab (eq. gdot) and the Christoffel symbols
+  T Gam[4][10];
+  {
+    T dtg[10], Ph[3][10];
+#pragma unroll
+    for (int s = 0; s < 10; ++s) {
+#pragma unroll
+      for (int x = 0; x < 3; ++x) Ph[x][s] = ldT<T>(u, P, p, 20 + 10 * x + s);
+      Acc<T> a;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) a.fma_(M.bu[x], Ph[x][s]);
+      a.fma_(-M.alpha, ldT<T>(u, P, p, 10 + s));
+      dtg[s] = a.get();
+      stT(out, P, p, s, dtg[s]);
+    }
+    auto dg4 = [&](int c, int s) -> T { return c == 0 ? dtg[s] : Ph[c - 1][s]; };
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a; b < 4; ++b)
+          Gam[c][SI(a, b)] = half * (dg4(a, SI(b, c)) + dg4(b, SI(a, c)) - dg4(c, SI(a, b)));
+  }
+  // Gamma_c = g^ab Gamma_cab (symmetric pairs counted twice off the diagonal)
+  T C[4], Hup[4], Hd[4];
+  T nC;
+  {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) Hd[a] = ldT<T>(H, P, p, a);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Acc<T> acc;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a; b < 4; ++b) {
+          const T w = (a == b) ? M.gi4[SI(a, b)] : M.gi4[SI(a, b)] + M.gi4[SI(a, b)];
+          acc.fma_(w, Gam[c][SI(a, b)]);
+        }
+      acc.add(Hd[c]);
+      C[c] = acc.get();
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      Acc<T> acc;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Hd[d]);
+      Hup[c] = acc.get();
+    }
+    Acc<T> acc;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc.fma_(M.nu[c], C[c]);
+    nC = acc.get();
+  }
+  // -2 alpha nabla_(a H_b) + alpha (n_b C_a + n_a C_b - g_ab n^c C_c)
+  T SPi[10];
+  {
+    const T twoal = M.alpha + M.alpha;
+    const T nlo0 = -M.alpha;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        const int s = SI(a, b);
+        const T dHab = a == 0 ? zero : ldT<T>(dH, P, p, (a - 1) * 4 + b);
+        const T dHba = b == 0 ? zero : ldT<T>(dH, P, p, (b - 1) * 4 + a);
+        Acc<T> acc;
+        acc.fma_(half, dHab + dHba);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc.fma_(-Gam[c][s], Hup[c]);
+        const T DH = acc.get();
+        Acc<T> v;
+        v.fma_(-twoal, DH);
+        v.fma_(-M.alpha * g[s], nC);
+        if (a == 0) v.fma_(M.alpha * nlo0, C[b]);
+        if (b == 0) v.fma_(M.alpha * nlo0, C[a]);
+        SPi[s] = v.get();
+      }
+  }
+  // -2 alpha g^cd g^ef Gamma_ace Gamma_bdf
+  {
+    const T m2al = -(M.alpha + M.alpha);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      T Gcf[4][4];  // Gamma_b^c_f = g^cd Gamma_bdf
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          Acc<T> acc;
+#pragma unroll
+          for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Gam[b][SI(d, f)]);
+          Gcf[c][f] = acc.get();
+        }
+      T Gce[10];  // Gamma_b^{ce}, symmetric
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int e = c; e < 4; ++e) {
+          Acc<T> acc;
+#pragma unroll
+          for (int f = 0; f < 4; ++f) acc.fma_(M.gi4[SI(e, f)], Gcf[c][f]);
+          Gce[SI(c, e)] = (c == e) ? acc.get() : acc.get() + acc.get();  // off-diagonal weight 2
+        }
+#pragma unroll
+      for (int a = 0; a <= b; ++a) {
+        Acc<T> acc;
+        acc.add(SPi[SI(a, b)]);
+        T q = zero;
+        {
+          Acc<T> qa;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int e = c; e < 4; ++e) qa.fma_(Gam[a][SI(c, e)], Gce[SI(c, e)]);
+          q = qa.get();
+        }
+        acc.fma_(m2al, q);
+        SPi[SI(a, b)] = acc.get();
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 10; ++s) stT(src, P, p, s, SPi[s]);
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, double* __restrict__ src,
+                                                  Geo geo) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const T zero = S<T>::c(0.0), half = S<T>::c(0.5);
+  T g[10], Pi[10], Ph[3][10];
+#pragma unroll
+  for (int s = 0; s < 10; ++s) g[s] = ldT<T>(u, P, p, s);
+  Metric<T> M;
+  metric_from(g, M);
+#pragma unroll
+  for (int s = 0; s < 10; ++s) {
+    Pi[s] = ldT<T>(u, P, p, 10 + s);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) Ph[x][s] = ldT<T>(u, P, p, 20 + 10 * x + s);
+  }
+  const T twoal = M.alpha + M.alpha;
+  T Q[10];  // Q1 - Q2
+  // Q2_ab = Pi_ac g^cd Pi_db
+  {
+    T Piu[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        Acc<T> acc;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Pi[SI(b, d)]);
+        Piu[b][c] = acc.get();
+      }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = a; b < 4; ++b) {
+        Acc<T> acc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc.fma_(-Pi[SI(a, c)], Piu[b][c]);
+        Q[SI(a, b)] = acc.get();
+      }
+  }
+  // Q1_ab = gamma^ij g^cd Phi_iac Phi_jbd
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    T V[3][4];
+    {
+      T Y[3][4];
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          Acc<T> acc;
+#pragma unroll
+          for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Ph[x][SI(b, d)]);
+          Y[x][c] = acc.get();
+        }
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          Acc<T> acc;
+#pragma unroll
+          for (int y = 0; y < 3; ++y) acc.fma_(M.gi[x][y], Y[y][c]);
+          V[x][c] = acc.get();
+        }
+    }
+#pragma unroll
+    for (int a = 0; a <= b; ++a) {
+      Acc<T> acc;
+      acc.add(Q[SI(a, b)]);
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc.fma_(Ph[x][SI(a, c)], V[x][c]);
+      Q[SI(a, b)] = acc.get();
+    }
+  }
+  // remaining algebraic terms of eq. Pidot
+  T nnPi;
+  {
+    Acc<T> acc;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int d = 0; d < 4; ++d) acc.fma_(M.nu[c] * M.nu[d], Pi[SI(c, d)]);
+    nnPi = acc.get();
+  }
+  T Vj[3];  // n^c Pi_ci gamma^ij
+  {
+    T nPi[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Acc<T> acc;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc.fma_(M.nu[c], Pi[SI(c, x + 1)]);
+      nPi[x] = acc.get();
+    }
+#pragma unroll
+    for (int y = 0; y < 3; ++y) {
+      Acc<T> acc;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) acc.fma_(nPi[x], M.gi[x][y]);
+      Vj[y] = acc.get();
+    }
+  }
+  const T hal = half * M.alpha;
+#pragma unroll
+  for (int s = 0; s < 10; ++s) {
+    Acc<T> acc;
+    acc.add(ldT<T>(src, P, p, s));
+    acc.fma_(twoal, Q[s]);
+    acc.fma_(-(hal * nnPi), Pi[s]);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) acc.fma_(M.bu[x] - M.alpha * Vj[x], Ph[x][s]);
+    stT(src, P, p, s, acc.get());
+  }
+  // algebraic terms of eq. Phidot
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    T nnPhi;
+    {
+      Acc<T> acc;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc.fma_(M.nu[c] * M.nu[d], Ph[x][SI(c, d)]);
+      nnPhi = acc.get();
+    }
+    T Mk[3];  // gamma^jk n^c Phi_x,j,c
+    {
+      T nP[3];
+#pragma unroll
+      for (int y = 0; y < 3; ++y) {
+        Acc<T> acc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc.fma_(M.nu[c], Ph[x][SI(y + 1, c)]);
+        nP[y] = acc.get();
+      }
+#pragma unroll
+      for (int z = 0; z < 3; ++z) {
+        Acc<T> acc;
+#pragma unroll
+        for (int y = 0; y < 3; ++y) acc.fma_(nP[y], M.gi[y][z]);
+        Mk[z] = M.alpha * acc.get();
+      }
+    }
+    const T hnn = hal * nnPhi;
+#pragma unroll
+    for (int s = 0; s < 10; ++s) {
+      Acc<T> acc;
+      acc.fma_(hnn, Pi[s]);
+#pragma unroll
+      for (int z = 0; z < 3; ++z) acc.fma_(Mk[z], Ph[z][s]);
+      acc.fma_(-M.alpha, Ph[x][s]);
+      stT(src, P, p, 10 + 10 * x + s, acc.get());
+    }
+  }
+  (void)zero;
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, const double* __restrict__ src,
+                                                double* __restrict__ out, Geo geo) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int k = (int)(p % geo.n_r);
+  const int i = (int)((p / geo.n_r) % geo.N);
+  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const int nv = geo.nv;
+  const T half = S<T>::c(0.5);
+  const Jac<T> J = jacobian<T>(geo, k, i, jj);
+  const T alpha = ldT<T>(src, P, p, 40);
+  T bu[3], gi[3][3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) bu[x] = ldT<T>(src, P, p, 41 + x);
+  gi[0][0] = ldT<T>(src, P, p, 44);
+  gi[0][1] = gi[1][0] = ldT<T>(src, P, p, 45);
+  gi[0][2] = gi[2][0] = ldT<T>(src, P, p, 46);
+  gi[1][1] = ldT<T>(src, P, p, 47);
+  gi[1][2] = gi[2][1] = ldT<T>(src, P, p, 48);
+  gi[2][2] = ldT<T>(src, P, p, 49);
+  // beta^k d_k = sum_m b_m D_m; alpha gamma^ik d_k = sum_m G_im D_m; J_xm for d_x
+  T b[3], G[3][3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    Acc<T> acc;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) acc.fma_(bu[x], J.j[x][m]);
+    b[m] = acc.get();
+  }
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      Acc<T> acc;
+#pragma unroll
+      for (int y = 0; y < 3; ++y) acc.fma_(gi[x][y], J.j[y][m]);
+      G[x][m] = alpha * acc.get();
+    }
+  T aJ[3][3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) aJ[x][m] = alpha * J.j[x][m];
+  const bool outer = (k == geo.n_r - 1);
+  T sl[3], su[3];
+  if (outer) {
+    const T l[3] = {J.st * J.cp, J.st * J.sp, J.ct};
+    Acc<T> q;
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+#pragma unroll
+      for (int y = 0; y < 3; ++y) q.fma_(gi[x][y] * l[x], l[y]);
+    const T iq = S<T>::c(1.0) / sqrt_s(q.get());
+#pragma unroll
+    for (int x = 0; x < 3; ++x) sl[x] = l[x] * iq;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Acc<T> acc;
+#pragma unroll
+      for (int y = 0; y < 3; ++y) acc.fma_(gi[x][y], sl[y]);
+      su[x] = acc.get();
+    }
+  }
+#pragma unroll 2
+  for (int s = 0; s < 10; ++s) {
+    T Dd[3], DPh[3][3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const long long base = (long long)m * nv * P + p;
+      const T dg = S<T>::load(D + base + (long long)s * P);
+      const T dpi = S<T>::load(D + base + (long long)(10 + s) * P);
+      Dd[m] = dg - dpi;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) DPh[x][m] = S<T>::load(D + base + (long long)(20 + 10 * x + s) * P);
+    }
+    Acc<T> aPi;
+    aPi.add(ldT<T>(src, P, p, s));
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      aPi.fma_(-b[m], Dd[m]);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) aPi.fma_(-G[x][m], DPh[x][m]);
+    }
+    T rPi = aPi.get();
+    T rPh[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Acc<T> a;
+      a.add(ldT<T>(src, P, p, 10 + 10 * x + s));
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        a.fma_(b[m], DPh[x][m]);
+        a.fma_(aJ[x][m], Dd[m]);
+      }
+      rPh[x] = a.get();
+    }
+    if (outer) {
+      const T rg = ldT<T>(out, P, p, s);
+      Acc<T> sd;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) sd.fma_(su[x], rPh[x]);
+      const T wplus = rPi + sd.get();
+      const T w2 = half * (wplus - rg);
+      rPi = half * (rg + wplus);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) rPh[x] = sl[x] * w2;
+    }
+    stT(out, P, p, 10 + s, rPi);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) stT(out, P, p, 20 + 10 * x + s, rPh[x]);
+  }
+}
+
+int pw_rhs(const cffyn_shell* sh, const double* u, const double* D, double* out, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  const unsigned nb = blocks_for(g.P, 128);
+  if (sh->d.precision == CFFYN_MIXED) {
+    k_rhs_gamma<ff><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+    count_launch();
+    k_rhs_quad<ff><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+    count_launch();
+    k_rhs_pp<ff><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
+    count_launch();
+  } else {
+    k_rhs_gamma<double><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+    count_launch();
+    k_rhs_quad<double><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+    count_launch();
+    k_rhs_pp<double><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
+    count_launch();
+  }
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+}  // namespace cffyn

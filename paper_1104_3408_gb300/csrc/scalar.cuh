@@ -107,52 +107,95 @@ __device__ __forceinline__ double ff_to_double(ff a) {
   return u64_scaled_to_double(neg ? (unsigned long long)(-V) : (unsigned long long)V, eh - 127 - 52, neg);
 }
 
+// All additions and products inside the error-free transformations use the
+// _rn intrinsics: the compiler never contracts those into fused multiply-adds,
+// which would silently break the exactness of TwoSum / TwoProd.
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+
 __device__ __forceinline__ ff two_sum(float a, float b) {
-  float s = a + b;
-  float bb = s - a;
-  float e = (a - (s - bb)) + (b - bb);
+  const float s = fa(a, b);
+  const float bb = fs(s, a);
+  const float e = fa(fs(a, fs(s, bb)), fs(b, bb));
   return ff{s, e};
 }
 __device__ __forceinline__ ff fast_two_sum(float a, float b) {
-  float s = a + b;
-  float e = b - (s - a);
+  const float s = fa(a, b);
+  const float e = fs(b, fs(s, a));
   return ff{s, e};
 }
 __device__ __forceinline__ ff operator+(ff x, ff y) {
-  ff s = two_sum(x.hi, y.hi);
-  float v = s.lo + (x.lo + y.lo);
+  const ff s = two_sum(x.hi, y.hi);
+  const float v = fa(s.lo, fa(x.lo, y.lo));
   return fast_two_sum(s.hi, v);
 }
 __device__ __forceinline__ ff operator-(ff x) { return ff{-x.hi, -x.lo}; }
 __device__ __forceinline__ ff operator-(ff x, ff y) { return x + (-y); }
 __device__ __forceinline__ ff operator*(ff x, ff y) {
-  float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  float t = fmaf(x.hi, y.lo, x.lo * y.hi);
-  return fast_two_sum(p, e + t);
+  const float p = fm(x.hi, y.hi);
+  const float e = fmaf(x.hi, y.hi, -p);
+  const float t = fmaf(x.hi, y.lo, fm(x.lo, y.hi));
+  return fast_two_sum(p, fa(e, t));
 }
 __device__ __forceinline__ ff operator*(ff x, float c) {
-  float p = x.hi * c;
-  float e = fmaf(x.hi, c, -p);
+  const float p = fm(x.hi, c);
+  const float e = fmaf(x.hi, c, -p);
   return fast_two_sum(p, fmaf(x.lo, c, e));
 }
 __device__ __forceinline__ ff operator*(float c, ff x) { return x * c; }
 __device__ __forceinline__ ff operator/(ff x, ff y) {
-  float q = x.hi / y.hi;
-  ff r = x - y * q;                 // residual
-  float q2 = r.hi / y.hi;
+  const float q = __fdiv_rn(x.hi, y.hi);
+  const ff r = x - y * q;  // residual
+  const float q2 = __fdiv_rn(r.hi, y.hi);
   return fast_two_sum(q, q2);
 }
 __device__ __forceinline__ ff& operator+=(ff& a, ff b) { a = a + b; return a; }
 __device__ __forceinline__ ff& operator-=(ff& a, ff b) { a = a - b; return a; }
 __device__ __forceinline__ ff sqrt_s(ff x) {
-  if (x.hi <= 0.0f) return ff{sqrtf(x.hi), 0.0f};
-  float s = sqrtf(x.hi);
-  ff ss = ff{s, 0.0f} * ff{s, 0.0f};
-  ff r = x - ss;
-  return fast_two_sum(s, r.hi / (2.0f * s));
+  if (x.hi <= 0.0f) return ff{__fsqrt_rn(x.hi), 0.0f};
+  const float s = __fsqrt_rn(x.hi);
+  const ff ss = ff{s, 0.0f} * ff{s, 0.0f};
+  const ff r = x - ss;
+  return fast_two_sum(s, __fdiv_rn(r.hi, fm(2.0f, s)));
 }
 __device__ __forceinline__ double sqrt_s(double x) { return sqrt(x); }
+
+// Dot-product accumulator.  double: plain FMA.  ff: the compensated dot
+// product "Dot2" of Ogita, Rump and Oishi ("Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26 (2005)): every product is split exactly by TwoProd
+// (with the cross terms of the low parts folded in), the running sum by
+// TwoSum, and all error terms collect in one FP32 word that is added back at
+// the end.
+template <class T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void fma_(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ void add(double a) { s += a; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<ff> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void fma_(ff a, ff b) {
+    const float p = fm(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float t = fa(s, p);
+    const float bb = fs(t, s);
+    const float err = fa(fs(s, fs(t, bb)), fs(p, bb));
+    s = t;
+    c = fa(c, fa(err, e));
+  }
+  __device__ __forceinline__ void add(ff a) {
+    const float t = fa(s, a.hi);
+    const float bb = fs(t, s);
+    const float err = fa(fs(s, fs(t, bb)), fs(a.hi, bb));
+    s = t;
+    c = fa(c, fa(err, a.lo));
+  }
+  __device__ __forceinline__ ff get() const { return two_sum(s, c); }
+};
 
 // Uniform helpers so that templated code reads the same for both types.
 template <class T> struct S;
