@@ -233,10 +233,13 @@ def run_ours(args, rank, local_rank, ws, dist):
                 "fp64_equiv_tflops": fl64 / (launch_ms * 1e-3) / 1e12,
                 "launch_ms": launch_ms}
     else:
-        # pointwise groups: algorithmic bytes of the group's FP64 arrays
-        nvP = w["n_fields"] * P * 8.0
-        byts = {"rhs": nvP * (1 + 3 + 1) + 16 * P * 8.0, "decompose": 2 * nvP,
-                "reconstruct": 5 * nvP, "project": 2 * nvP * (2 * L + 1) / J}[dom]
+        # pointwise groups: algorithmic bytes of the arrays one launch reads and
+        # writes (8-byte values per point)
+        P8 = P * 8.0
+        nvP = w["n_fields"] * P8
+        byts = {"rhs_gamma": 126 * P8, "rhs_quad": 100 * P8, "rhs_pp": 240 * P8,
+                "decompose": 2 * nvP, "reconstruct": 5 * nvP,
+                "project": 2 * nvP * (2 * L + 1) / J}[dom]
         achieved = byts / (launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": None, "peak_source": f"hbm_gbs ({peak_kind})",

@@ -24,8 +24,8 @@ EXPORTED = [
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace",
 ]
-PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs", "decompose", "dft_fwd", "project", "dft_inv",
-                  "reconstruct"]
+PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
+                  "dft_fwd", "project", "dft_inv", "reconstruct"]
 
 
 class ShellDesc(ctypes.Structure):

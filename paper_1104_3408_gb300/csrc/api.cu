@@ -38,6 +38,7 @@ int build_operators(cffyn_shell*);
 void free_sliced(SlicedOp&);
 // pointwise.cu
 int pw_rhs(const cffyn_shell*, const double*, const double*, double*, cudaStream_t);
+int pw_rhs_part(const cffyn_shell*, const double*, const double*, double*, int, cudaStream_t);
 int pw_decompose(const cffyn_shell*, const double*, double*, cudaStream_t);
 int pw_reconstruct(const cffyn_shell*, const double*, double*, int, double*, double*, double*, double,
                    int*, cudaStream_t);
@@ -345,31 +346,33 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
     if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, st); }))) return rc;
     if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, st); }))) return rc;
     if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, st); }))) return rc;
-    if ((rc = run(3, [&] { return pw_rhs(sh, X, sh->D, sh->S, st); }))) return rc;
+    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, st); }))) return rc;
+    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, st); }))) return rc;
+    if ((rc = run(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, st); }))) return rc;
     if (per_sub) {
-      if ((rc = run(4, [&] { return pw_decompose(sh, sh->S, spin, st); }))) return rc;
-      if ((rc = run(5, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return rc;
-      if ((rc = run(6, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+      if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, st); }))) return rc;
+      if ((rc = run(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return rc;
+      if ((rc = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
         return rc;
-      if ((rc = run(7, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) return rc;
-      if ((rc = run(8, [&] {
+      if ((rc = run(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) return rc;
+      if ((rc = run(10, [&] {
              return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
            })))
         return rc;
     } else {
-      if ((rc = run(8, [&] {
+      if ((rc = run(10, [&] {
              return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
            })))
         return rc;
     }
   }
   if (!per_sub) {
-    if ((rc = run(4, [&] { return pw_decompose(sh, u, sh->S, st); }))) return rc;
-    if ((rc = run(5, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); }))) return rc;
-    if ((rc = run(6, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+    if ((rc = run(6, [&] { return pw_decompose(sh, u, sh->S, st); }))) return rc;
+    if ((rc = run(7, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); }))) return rc;
+    if ((rc = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
       return rc;
-    if ((rc = run(7, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); }))) return rc;
-    if ((rc = run(8, [&] {
+    if ((rc = run(9, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); }))) return rc;
+    if ((rc = run(10, [&] {
            return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
          })))
       return rc;
@@ -557,34 +560,36 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     if ((rc = phase(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, st); }))) break;
     if ((rc = phase(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, st); }))) break;
     if ((rc = phase(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, st); }))) break;
-    if ((rc = phase(3, [&] { return pw_rhs(sh, X, sh->D, sh->S, st); }))) break;
+    if ((rc = phase(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, st); }))) break;
+    if ((rc = phase(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, st); }))) break;
+    if ((rc = phase(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, st); }))) break;
     if (per_sub) {
-      if ((rc = phase(4, [&] { return pw_decompose(sh, sh->S, spin, st); }))) break;
-      if ((rc = phase(5, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) break;
-      if ((rc = phase(6, [&] {
+      if ((rc = phase(6, [&] { return pw_decompose(sh, sh->S, spin, st); }))) break;
+      if ((rc = phase(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) break;
+      if ((rc = phase(8, [&] {
              return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
            })))
         break;
-      if ((rc = phase(7, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) break;
-      if ((rc = phase(8, [&] {
+      if ((rc = phase(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) break;
+      if ((rc = phase(10, [&] {
              return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
            })))
         break;
     } else {
-      if ((rc = phase(8, [&] {
+      if ((rc = phase(10, [&] {
              return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
            })))
         break;
     }
   }
   if (!rc && !per_sub) {
-    rc = phase(4, [&] { return pw_decompose(sh, u, sh->S, st); });
-    if (!rc) rc = phase(5, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); });
+    rc = phase(6, [&] { return pw_decompose(sh, u, sh->S, st); });
+    if (!rc) rc = phase(7, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); });
     if (!rc)
-      rc = phase(6, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); });
-    if (!rc) rc = phase(7, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); });
+      rc = phase(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); });
+    if (!rc) rc = phase(9, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); });
     if (!rc)
-      rc = phase(8, [&] {
+      rc = phase(10, [&] {
         return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
       });
   }

@@ -31,7 +31,7 @@ namespace cffyn {
 
 struct ColDesc {
   long long in0, in1, out0, out1;  // base offsets of the two row segments
-  float sign1;                     // sign of the second input segment
+  int sgn1;                        // second input segment: 0 as is, 1 negated, 2 zero
   int valid;
 };
 
@@ -66,7 +66,7 @@ struct OpArgs {
 __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
   ColDesc d;
   d.valid = c < a.g.ncols;
-  d.sign1 = 1.0f;
+  d.sgn1 = 0;
   if (!d.valid) c = 0;
   switch (a.kind) {
     case OP_R: {
@@ -124,12 +124,12 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
       };
       long long aR = base(fre, ra), aI = base(fim, ra);
       long long bR = a.m ? base(fre, rb) : aR, bI = a.m ? base(fim, rb) : aI;
-      float s0 = a.m ? 1.0f : 0.0f;
+      // at m = 0 the F_d half of the operator is zero: gather nothing there
       switch (part) {
-        case 0: d.in0 = aR; d.in1 = bI; d.sign1 = s0; d.out0 = aR; break;
-        case 1: d.in0 = aI; d.in1 = bR; d.sign1 = -s0; d.out0 = aI; break;
-        case 2: d.in0 = bR; d.in1 = aI; d.sign1 = -s0; d.out0 = bR; break;
-        default: d.in0 = bI; d.in1 = aR; d.sign1 = s0; d.out0 = bI; break;
+        case 0: d.in0 = aR; d.in1 = bI; d.sgn1 = a.m ? 0 : 2; d.out0 = aR; break;
+        case 1: d.in0 = aI; d.in1 = bR; d.sgn1 = a.m ? 1 : 2; d.out0 = aI; break;
+        case 2: d.in0 = bR; d.in1 = aI; d.sgn1 = a.m ? 1 : 2; d.out0 = bR; break;
+        default: d.in0 = bI; d.in1 = aR; d.sgn1 = a.m ? 0 : 2; d.out0 = bI; break;
       }
       d.out1 = 0;
       break;
@@ -141,9 +141,11 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
 __device__ __forceinline__ double load_elem(const OpArgs& a, const ColDesc& d, int k) {
   if (!d.valid || k >= a.g.K) return 0.0;
   if (k < a.g.K0) return __ldg(a.in + d.in0 + (long long)k * a.g.in_rs);
+  if (d.sgn1 == 2) return 0.0;
   int kk = a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0);
-  double v = __ldg(a.in + d.in1 + (long long)kk * a.g.in_rs);
-  return d.sign1 == 1.0f ? v : (d.sign1 == -1.0f ? -v : 0.0);
+  const double v = __ldg(a.in + d.in1 + (long long)kk * a.g.in_rs);
+  // sign flip on the bit pattern (no FP64 instruction)
+  return __longlong_as_double(__double_as_longlong(v) ^ ((long long)d.sgn1 << 63));
 }
 
 __device__ __forceinline__ void store_elem(const OpArgs& a, const ColDesc& d, int p, double v) {
@@ -300,6 +302,16 @@ __device__ __forceinline__ double i64_scaled_to_double(long long T, int sc) {
   return __longlong_as_double((long long)bits);
 }
 
+// Four 8x8 BF16 tiles from shared memory; lane l addresses row (l % 8) of tile
+// (l / 8) and receives, per tile, the pair at row lane/4, columns 2*(lane%4).
+__device__ __forceinline__ void ldmatrix_x4(unsigned int& r0, unsigned int& r1, unsigned int& r2,
+                                            unsigned int& r3, const void* p) {
+  const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
 __device__ __forceinline__ void mma_bf16(float c[4], const uint4& a, unsigned int b0, unsigned int b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
@@ -347,7 +359,7 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
       if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
       v0[it] = load_elem(a, cols[c], 2 * kp);
       v1[it] = load_elem(a, cols[c], 2 * kp + 1);
-      const int ex = max(v0[it] != 0.0 ? exp_field(v0[it]) : 0, v1[it] != 0.0 ? exp_field(v1[it]) : 0);
+      const int ex = max(exp_field(v0[it]), exp_field(v1[it]));  // 0 for zero
       if (ex) atomicMax(&colE[c], ex - 1022);
     }
   }
@@ -389,15 +401,17 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
       for (int i = 0; i <= d; ++i) {
         const int j = d - i;
         const uint4* Af = W.frag + ((size_t)(i * W.mtiles + mt) * ksteps) * 32 + lane;
-        const unsigned short* Bj = Bs + (size_t)j * OZ_QT * KP;
+        // ldmatrix row addresses: tile q = lane/8 is (n-tile q/2, k half q%2)
+        const unsigned short* Bj = Bs + (size_t)j * OZ_QT * KP +
+                                   (size_t)(((lane >> 4) * 8) + (lane & 7)) * KP + ((lane >> 3) & 1) * 8;
         for (int ks = kc; ks < kend; ++ks) {
           const uint4 af = __ldg(Af + (size_t)ks * 32);
 #pragma unroll
-          for (int n = 0; n < OZ_NT; ++n) {
-            const unsigned short* col = Bj + (size_t)(n * 8 + g) * KP + ks * 16 + 2 * tg;
-            const unsigned int b0 = *reinterpret_cast<const unsigned int*>(col);
-            const unsigned int b1 = *reinterpret_cast<const unsigned int*>(col + 8);
-            mma_bf16(acc[n], af, b0, b1);
+          for (int n = 0; n < OZ_NT; n += 2) {
+            unsigned int b00, b01, b10, b11;
+            ldmatrix_x4(b00, b01, b10, b11, Bj + (size_t)n * 8 * KP + ks * 16);
+            mma_bf16(acc[n], af, b00, b01);
+            mma_bf16(acc[n + 1], af, b10, b11);
           }
         }
       }

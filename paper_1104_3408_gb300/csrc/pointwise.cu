@@ -96,229 +96,245 @@ __device__ __forceinline__ void st(double* a, long long P, long long p, int f, T
   a[(long long)f * P + p] = S<T>::to_double(v);
 }
 
+// Tensor groups handled by one thread each (blockIdx.y), so that a thread
+// holds at most the 18 components of Phi_ijk:
+//   0: g_tt, Pi_tt   1: g_ti   2: Pi_ti   3: Phi_itt   4: g_ij   5: Pi_ij
+//   6: Phi_itj       7: Phi_ijk
+constexpr int kGroups = 8;
+
 template <class T>
-__device__ __forceinline__ void decompose_point(const double* __restrict__ in, double* __restrict__ out,
-                                                long long P, long long p, const Triad<T>& t) {
-  const T half = S<T>::c(0.5), two = S<T>::c(2.0);
-  // rank 0
-  st(out, P, p, SLOT_R0(0), ld<T>(in, P, p, SI(0, 0)));
-  st(out, P, p, SLOT_R0(1), ld<T>(in, P, p, 10 + SI(0, 0)));
-  // rank 1: g_ti, Pi_ti, Phi_itt
-  {
-    const int base[3][3] = {{1, 2, 3}, {11, 12, 13}, {20, 30, 40}};
-    const int sr[3] = {2, 3, 4};
-#pragma unroll
-    for (int gph = 0; gph < 3; ++gph) {
+__device__ __forceinline__ void decompose_group(int grp, const double* __restrict__ in,
+                                                double* __restrict__ out, long long P, long long p,
+                                                const Triad<T>& t) {
+  const T two = S<T>::c(2.0);
+  switch (grp) {
+    case 0:
+      st(out, P, p, SLOT_R0(0), ld<T>(in, P, p, SI(0, 0)));
+      st(out, P, p, SLOT_R0(1), ld<T>(in, P, p, 10 + SI(0, 0)));
+      break;
+    case 1:
+    case 2:
+    case 3: {
+      const int gph = grp - 1;
+      const int b0 = gph == 0 ? 1 : (gph == 1 ? 11 : 20);
+      const int st_ = gph == 2 ? 10 : 1;
       T v[3], o[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) v[a] = ld<T>(in, P, p, base[gph][a]);
+      for (int a = 0; a < 3; ++a) v[a] = ld<T>(in, P, p, b0 + st_ * a);
       rot_vec(t, v, o);
-      st(out, P, p, SLOT_R0(sr[gph]), o[0]);
+      st(out, P, p, SLOT_R0(2 + gph), o[0]);
       st(out, P, p, SLOT_C1(gph), o[1]);
       st(out, P, p, SLOT_C1(gph) + 1, o[2]);
+      break;
+    }
+    case 4:
+    case 5: {
+      const int gph = grp - 4;
+      const int b0 = gph * 10;
+      T Tm[3][3], O[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, b0 + SI(a + 1, b + 1));
+      rot_mat(t, Tm, O);
+      st(out, P, p, SLOT_R0(5 + 2 * gph), O[0][0]);
+      st(out, P, p, SLOT_R0(6 + 2 * gph), O[1][1] + O[2][2]);
+      st(out, P, p, SLOT_C1(3 + gph), O[0][1]);
+      st(out, P, p, SLOT_C1(3 + gph) + 1, O[0][2]);
+      st(out, P, p, SLOT_C2(gph), O[1][1] - O[2][2]);
+      st(out, P, p, SLOT_C2(gph) + 1, two * O[1][2]);
+      break;
+    }
+    case 6: {
+      T Tm[3][3], O[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, 20 + 10 * a + SI(0, b + 1));
+      rot_mat(t, Tm, O);
+      st(out, P, p, SLOT_R0(9), O[0][0]);
+      st(out, P, p, SLOT_C1(5), O[0][1]);
+      st(out, P, p, SLOT_C1(5) + 1, O[0][2]);
+      st(out, P, p, SLOT_C1(6), O[1][0]);
+      st(out, P, p, SLOT_C1(6) + 1, O[2][0]);
+      st(out, P, p, SLOT_C2(2), O[1][1] - O[2][2]);
+      st(out, P, p, SLOT_C2(2) + 1, O[1][2] + O[2][1]);
+      st(out, P, p, SLOT_R0(12), O[1][1] + O[2][2]);
+      st(out, P, p, SLOT_R0(13), O[2][1] - O[1][2]);
+      break;
+    }
+    default: {
+      T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];
+      T Trot[3][3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T Tm[3][3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) Tm[b][c] = ld<T>(in, P, p, 20 + 10 * a + SI(b + 1, c + 1));
+        rot_mat(t, Tm, Trot[a]);
+      }
+#pragma unroll
+      for (int A = 0; A < 3; ++A) {
+        T O[3][3];
+#pragma unroll
+        for (int B = 0; B < 3; ++B)
+#pragma unroll
+          for (int C = 0; C < 3; ++C)
+            O[B][C] = t.R[A][0] * Trot[0][B][C] + t.R[A][1] * Trot[1][B][C] + t.R[A][2] * Trot[2][B][C];
+        Pr[A] = O[0][0];
+        Pmb[A] = O[1][1] + O[2][2];
+        Prm[A][0] = O[0][1];
+        Prm[A][1] = O[0][2];
+        Pmm[A][0] = O[1][1] - O[2][2];
+        Pmm[A][1] = two * O[1][2];
+      }
+      st(out, P, p, SLOT_R0(10), Pr[0]);
+      st(out, P, p, SLOT_R0(11), Pmb[0]);
+      st(out, P, p, SLOT_C1(7), Prm[0][0]);
+      st(out, P, p, SLOT_C1(7) + 1, Prm[0][1]);
+      st(out, P, p, SLOT_C2(3), Pmm[0][0]);
+      st(out, P, p, SLOT_C2(3) + 1, Pmm[0][1]);
+      st(out, P, p, SLOT_C1(8), Pr[1]);
+      st(out, P, p, SLOT_C1(8) + 1, Pr[2]);
+      st(out, P, p, SLOT_C1(9), Pmb[1]);
+      st(out, P, p, SLOT_C1(9) + 1, Pmb[2]);
+      // (mbar; mm) = P_mm^theta - i P_mm^phi
+      st(out, P, p, SLOT_C1(10), Pmm[1][0] + Pmm[2][1]);
+      st(out, P, p, SLOT_C1(10) + 1, Pmm[1][1] - Pmm[2][0]);
+      // (m; rm) = P_rm^theta + i P_rm^phi
+      st(out, P, p, SLOT_C2(4), Prm[1][0] - Prm[2][1]);
+      st(out, P, p, SLOT_C2(4) + 1, Prm[1][1] + Prm[2][0]);
+      // (m; r mbar) = conj(P_rm^theta) + i conj(P_rm^phi)   (spin 0)
+      st(out, P, p, SLOT_R0(14), Prm[1][0] + Prm[2][1]);
+      st(out, P, p, SLOT_R0(15), Prm[2][0] - Prm[1][1]);
+      // (m; mm) = P_mm^theta + i P_mm^phi
+      st(out, P, p, SLOT_C3, Pmm[1][0] - Pmm[2][1]);
+      st(out, P, p, SLOT_C3 + 1, Pmm[1][1] + Pmm[2][0]);
     }
   }
-  // symmetric rank 2: g_ij, Pi_ij
-#pragma unroll
-  for (int gph = 0; gph < 2; ++gph) {
-    const int b0 = gph * 10;
-    T Tm[3][3], O[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, b0 + SI(a + 1, b + 1));
-    rot_mat(t, Tm, O);
-    st(out, P, p, SLOT_R0(5 + 2 * gph), O[0][0]);
-    st(out, P, p, SLOT_R0(6 + 2 * gph), O[1][1] + O[2][2]);
-    st(out, P, p, SLOT_C1(3 + gph), O[0][1]);
-    st(out, P, p, SLOT_C1(3 + gph) + 1, O[0][2]);
-    st(out, P, p, SLOT_C2(gph), O[1][1] - O[2][2]);
-    st(out, P, p, SLOT_C2(gph) + 1, two * O[1][2]);
-  }
-  // general rank 2: Phi_itj (i derivative index, j tensor index)
-  {
-    T Tm[3][3], O[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, 20 + 10 * a + SI(0, b + 1));
-    rot_mat(t, Tm, O);
-    st(out, P, p, SLOT_R0(9), O[0][0]);
-    st(out, P, p, SLOT_C1(5), O[0][1]);
-    st(out, P, p, SLOT_C1(5) + 1, O[0][2]);
-    st(out, P, p, SLOT_C1(6), O[1][0]);
-    st(out, P, p, SLOT_C1(6) + 1, O[2][0]);
-    st(out, P, p, SLOT_C2(2), O[1][1] - O[2][2]);
-    st(out, P, p, SLOT_C2(2) + 1, O[1][2] + O[2][1]);
-    st(out, P, p, SLOT_R0(12), O[1][1] + O[2][2]);
-    st(out, P, p, SLOT_R0(13), O[2][1] - O[1][2]);
-  }
-  // rank 3: Phi_ijk, symmetric in jk
-  {
-    T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];  // per first-leg A (r, theta, phi)
-    T Trot[3][3][3];                         // [a][B][C]: pair rotated, first leg Cartesian
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      T Tm[3][3];
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Tm[b][c] = ld<T>(in, P, p, 20 + 10 * a + SI(b + 1, c + 1));
-      rot_mat(t, Tm, Trot[a]);
-    }
-#pragma unroll
-    for (int A = 0; A < 3; ++A) {
-      T O[3][3];
-#pragma unroll
-      for (int B = 0; B < 3; ++B)
-#pragma unroll
-        for (int C = 0; C < 3; ++C)
-          O[B][C] = t.R[A][0] * Trot[0][B][C] + t.R[A][1] * Trot[1][B][C] + t.R[A][2] * Trot[2][B][C];
-      Pr[A] = O[0][0];
-      Pmb[A] = O[1][1] + O[2][2];
-      Prm[A][0] = O[0][1];
-      Prm[A][1] = O[0][2];
-      Pmm[A][0] = O[1][1] - O[2][2];
-      Pmm[A][1] = two * O[1][2];
-    }
-    st(out, P, p, SLOT_R0(10), Pr[0]);
-    st(out, P, p, SLOT_R0(11), Pmb[0]);
-    st(out, P, p, SLOT_C1(7), Prm[0][0]);
-    st(out, P, p, SLOT_C1(7) + 1, Prm[0][1]);
-    st(out, P, p, SLOT_C2(3), Pmm[0][0]);
-    st(out, P, p, SLOT_C2(3) + 1, Pmm[0][1]);
-    st(out, P, p, SLOT_C1(8), Pr[1]);
-    st(out, P, p, SLOT_C1(8) + 1, Pr[2]);
-    st(out, P, p, SLOT_C1(9), Pmb[1]);
-    st(out, P, p, SLOT_C1(9) + 1, Pmb[2]);
-    // (mbar; mm) = P_mm^theta - i P_mm^phi
-    st(out, P, p, SLOT_C1(10), Pmm[1][0] + Pmm[2][1]);
-    st(out, P, p, SLOT_C1(10) + 1, Pmm[1][1] - Pmm[2][0]);
-    // (m; rm) = P_rm^theta + i P_rm^phi
-    st(out, P, p, SLOT_C2(4), Prm[1][0] - Prm[2][1]);
-    st(out, P, p, SLOT_C2(4) + 1, Prm[1][1] + Prm[2][0]);
-    // (m; r mbar) = conj(P_rm^theta) + i conj(P_rm^phi)   (spin 0)
-    st(out, P, p, SLOT_R0(14), Prm[1][0] + Prm[2][1]);
-    st(out, P, p, SLOT_R0(15), Prm[2][0] - Prm[1][1]);
-    // (m; mm) = P_mm^theta + i P_mm^phi
-    st(out, P, p, SLOT_C3, Pmm[1][0] - Pmm[2][1]);
-    st(out, P, p, SLOT_C3 + 1, Pmm[1][1] + Pmm[2][0]);
-  }
-  (void)half;
 }
 
-// Inverse of decompose_point: spin slots -> Cartesian tensor components.
-template <class T>
-__device__ __forceinline__ void reconstruct_point(const double* __restrict__ sp, long long P, long long p,
-                                                  const Triad<T>& t, T cart[50]) {
+// Inverse of decompose_group: the group's spin slots -> its Cartesian
+// components, each handed to emit(field, value).
+template <class T, class Emit>
+__device__ __forceinline__ void reconstruct_group(int grp, const double* __restrict__ sp, long long P,
+                                                  long long p, const Triad<T>& t, Emit&& emit) {
   const T half = S<T>::c(0.5);
-  cart[SI(0, 0)] = ld<T>(sp, P, p, SLOT_R0(0));
-  cart[10 + SI(0, 0)] = ld<T>(sp, P, p, SLOT_R0(1));
-  {
-    const int base[3][3] = {{1, 2, 3}, {11, 12, 13}, {20, 30, 40}};
-    const int sr[3] = {2, 3, 4};
-#pragma unroll
-    for (int gph = 0; gph < 3; ++gph) {
-      T o[3] = {ld<T>(sp, P, p, SLOT_R0(sr[gph])), ld<T>(sp, P, p, SLOT_C1(gph)),
+  switch (grp) {
+    case 0:
+      emit(SI(0, 0), ld<T>(sp, P, p, SLOT_R0(0)));
+      emit(10 + SI(0, 0), ld<T>(sp, P, p, SLOT_R0(1)));
+      break;
+    case 1:
+    case 2:
+    case 3: {
+      const int gph = grp - 1;
+      const int b0 = gph == 0 ? 1 : (gph == 1 ? 11 : 20);
+      const int st_ = gph == 2 ? 10 : 1;
+      T o[3] = {ld<T>(sp, P, p, SLOT_R0(2 + gph)), ld<T>(sp, P, p, SLOT_C1(gph)),
                 ld<T>(sp, P, p, SLOT_C1(gph) + 1)};
       T v[3];
       unrot_vec(t, o, v);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) cart[base[gph][a]] = v[a];
+      for (int a = 0; a < 3; ++a) emit(b0 + st_ * a, v[a]);
+      break;
     }
-  }
+    case 4:
+    case 5: {
+      const int gph = grp - 4;
+      const int b0 = gph * 10;
+      const T rr = ld<T>(sp, P, p, SLOT_R0(5 + 2 * gph));
+      const T mmb = ld<T>(sp, P, p, SLOT_R0(6 + 2 * gph));
+      const T rmr = ld<T>(sp, P, p, SLOT_C1(3 + gph)), rmi = ld<T>(sp, P, p, SLOT_C1(3 + gph) + 1);
+      const T mmr = ld<T>(sp, P, p, SLOT_C2(gph)), mmi = ld<T>(sp, P, p, SLOT_C2(gph) + 1);
+      T O[3][3], Tm[3][3];
+      O[0][0] = rr;
+      O[0][1] = O[1][0] = rmr;
+      O[0][2] = O[2][0] = rmi;
+      O[1][1] = half * (mmb + mmr);
+      O[2][2] = half * (mmb - mmr);
+      O[1][2] = O[2][1] = half * mmi;
+      unrot_mat(t, O, Tm);
 #pragma unroll
-  for (int gph = 0; gph < 2; ++gph) {
-    const int b0 = gph * 10;
-    const T rr = ld<T>(sp, P, p, SLOT_R0(5 + 2 * gph));
-    const T mmb = ld<T>(sp, P, p, SLOT_R0(6 + 2 * gph));
-    const T rmr = ld<T>(sp, P, p, SLOT_C1(3 + gph)), rmi = ld<T>(sp, P, p, SLOT_C1(3 + gph) + 1);
-    const T mmr = ld<T>(sp, P, p, SLOT_C2(gph)), mmi = ld<T>(sp, P, p, SLOT_C2(gph) + 1);
-    T O[3][3], Tm[3][3];
-    O[0][0] = rr;
-    O[0][1] = O[1][0] = rmr;
-    O[0][2] = O[2][0] = rmi;
-    O[1][1] = half * (mmb + mmr);
-    O[2][2] = half * (mmb - mmr);
-    O[1][2] = O[2][1] = half * mmi;
-    unrot_mat(t, O, Tm);
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = a; b < 3; ++b) cart[b0 + SI(a + 1, b + 1)] = Tm[a][b];
-  }
-  {
-    const T s9 = ld<T>(sp, P, p, SLOT_R0(9));
-    const T s12 = ld<T>(sp, P, p, SLOT_R0(12)), s13 = ld<T>(sp, P, p, SLOT_R0(13));
-    const T s42 = ld<T>(sp, P, p, SLOT_C2(2)), s43 = ld<T>(sp, P, p, SLOT_C2(2) + 1);
-    T O[3][3], Tm[3][3];
-    O[0][0] = s9;
-    O[0][1] = ld<T>(sp, P, p, SLOT_C1(5));
-    O[0][2] = ld<T>(sp, P, p, SLOT_C1(5) + 1);
-    O[1][0] = ld<T>(sp, P, p, SLOT_C1(6));
-    O[2][0] = ld<T>(sp, P, p, SLOT_C1(6) + 1);
-    O[1][1] = half * (s42 + s12);
-    O[2][2] = half * (s12 - s42);
-    O[1][2] = half * (s43 - s13);
-    O[2][1] = half * (s43 + s13);
-    unrot_mat(t, O, Tm);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) cart[20 + 10 * a + SI(0, b + 1)] = Tm[a][b];
-  }
-  {
-    T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];
-    Pr[0] = ld<T>(sp, P, p, SLOT_R0(10));
-    Pmb[0] = ld<T>(sp, P, p, SLOT_R0(11));
-    Prm[0][0] = ld<T>(sp, P, p, SLOT_C1(7));
-    Prm[0][1] = ld<T>(sp, P, p, SLOT_C1(7) + 1);
-    Pmm[0][0] = ld<T>(sp, P, p, SLOT_C2(3));
-    Pmm[0][1] = ld<T>(sp, P, p, SLOT_C2(3) + 1);
-    Pr[1] = ld<T>(sp, P, p, SLOT_C1(8));
-    Pr[2] = ld<T>(sp, P, p, SLOT_C1(8) + 1);
-    Pmb[1] = ld<T>(sp, P, p, SLOT_C1(9));
-    Pmb[2] = ld<T>(sp, P, p, SLOT_C1(9) + 1);
-    {
-      // X = (m; rm) = P^th + i P^ph, Y = (m; r mbar) = conj(P^th) + i conj(P^ph)
-      const T xr = ld<T>(sp, P, p, SLOT_C2(4)), xi = ld<T>(sp, P, p, SLOT_C2(4) + 1);
-      const T yr = ld<T>(sp, P, p, SLOT_R0(14)), yi = ld<T>(sp, P, p, SLOT_R0(15));
-      Prm[1][0] = half * (xr + yr);
-      Prm[1][1] = half * (xi - yi);
-      Prm[2][0] = half * (xi + yi);
-      Prm[2][1] = half * (yr - xr);
+        for (int b = a; b < 3; ++b) emit(b0 + SI(a + 1, b + 1), Tm[a][b]);
+      break;
     }
-    {
-      // X = (m; mm) = P^th + i P^ph, Z = (mbar; mm) = P^th - i P^ph
-      const T xr = ld<T>(sp, P, p, SLOT_C3), xi = ld<T>(sp, P, p, SLOT_C3 + 1);
-      const T zr = ld<T>(sp, P, p, SLOT_C1(10)), zi = ld<T>(sp, P, p, SLOT_C1(10) + 1);
-      Pmm[1][0] = half * (xr + zr);
-      Pmm[1][1] = half * (xi + zi);
-      Pmm[2][0] = half * (xi - zi);
-      Pmm[2][1] = half * (zr - xr);
+    case 6: {
+      const T s9 = ld<T>(sp, P, p, SLOT_R0(9));
+      const T s12 = ld<T>(sp, P, p, SLOT_R0(12)), s13 = ld<T>(sp, P, p, SLOT_R0(13));
+      const T s42 = ld<T>(sp, P, p, SLOT_C2(2)), s43 = ld<T>(sp, P, p, SLOT_C2(2) + 1);
+      T O[3][3], Tm[3][3];
+      O[0][0] = s9;
+      O[0][1] = ld<T>(sp, P, p, SLOT_C1(5));
+      O[0][2] = ld<T>(sp, P, p, SLOT_C1(5) + 1);
+      O[1][0] = ld<T>(sp, P, p, SLOT_C1(6));
+      O[2][0] = ld<T>(sp, P, p, SLOT_C1(6) + 1);
+      O[1][1] = half * (s42 + s12);
+      O[2][2] = half * (s12 - s42);
+      O[1][2] = half * (s43 - s13);
+      O[2][1] = half * (s43 + s13);
+      unrot_mat(t, O, Tm);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) emit(20 + 10 * a + SI(0, b + 1), Tm[a][b]);
+      break;
     }
-    T Trot[3][3][3];  // [A][B][C] in the triad
+    default: {
+      T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];
+      Pr[0] = ld<T>(sp, P, p, SLOT_R0(10));
+      Pmb[0] = ld<T>(sp, P, p, SLOT_R0(11));
+      Prm[0][0] = ld<T>(sp, P, p, SLOT_C1(7));
+      Prm[0][1] = ld<T>(sp, P, p, SLOT_C1(7) + 1);
+      Pmm[0][0] = ld<T>(sp, P, p, SLOT_C2(3));
+      Pmm[0][1] = ld<T>(sp, P, p, SLOT_C2(3) + 1);
+      Pr[1] = ld<T>(sp, P, p, SLOT_C1(8));
+      Pr[2] = ld<T>(sp, P, p, SLOT_C1(8) + 1);
+      Pmb[1] = ld<T>(sp, P, p, SLOT_C1(9));
+      Pmb[2] = ld<T>(sp, P, p, SLOT_C1(9) + 1);
+      {
+        // X = (m; rm) = P^th + i P^ph, Y = (m; r mbar) = conj(P^th) + i conj(P^ph)
+        const T xr = ld<T>(sp, P, p, SLOT_C2(4)), xi = ld<T>(sp, P, p, SLOT_C2(4) + 1);
+        const T yr = ld<T>(sp, P, p, SLOT_R0(14)), yi = ld<T>(sp, P, p, SLOT_R0(15));
+        Prm[1][0] = half * (xr + yr);
+        Prm[1][1] = half * (xi - yi);
+        Prm[2][0] = half * (xi + yi);
+        Prm[2][1] = half * (yr - xr);
+      }
+      {
+        // X = (m; mm) = P^th + i P^ph, Z = (mbar; mm) = P^th - i P^ph
+        const T xr = ld<T>(sp, P, p, SLOT_C3), xi = ld<T>(sp, P, p, SLOT_C3 + 1);
+        const T zr = ld<T>(sp, P, p, SLOT_C1(10)), zi = ld<T>(sp, P, p, SLOT_C1(10) + 1);
+        Pmm[1][0] = half * (xr + zr);
+        Pmm[1][1] = half * (xi + zi);
+        Pmm[2][0] = half * (xi - zi);
+        Pmm[2][1] = half * (zr - xr);
+      }
+      T X[3][3][3];  // [A][b][c]: pair back in Cartesian, first leg in the triad
 #pragma unroll
-    for (int A = 0; A < 3; ++A) {
-      Trot[A][0][0] = Pr[A];
-      Trot[A][0][1] = Trot[A][1][0] = Prm[A][0];
-      Trot[A][0][2] = Trot[A][2][0] = Prm[A][1];
-      Trot[A][1][1] = half * (Pmb[A] + Pmm[A][0]);
-      Trot[A][2][2] = half * (Pmb[A] - Pmm[A][0]);
-      Trot[A][1][2] = Trot[A][2][1] = half * Pmm[A][1];
+      for (int A = 0; A < 3; ++A) {
+        T Trot[3][3];
+        Trot[0][0] = Pr[A];
+        Trot[0][1] = Trot[1][0] = Prm[A][0];
+        Trot[0][2] = Trot[2][0] = Prm[A][1];
+        Trot[1][1] = half * (Pmb[A] + Pmm[A][0]);
+        Trot[2][2] = half * (Pmb[A] - Pmm[A][0]);
+        Trot[1][2] = Trot[2][1] = half * Pmm[A][1];
+        unrot_mat(t, Trot, X[A]);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int c = b; c < 3; ++c)
+            emit(20 + 10 * a + SI(b + 1, c + 1),
+                 t.R[0][a] * X[0][b][c] + t.R[1][a] * X[1][b][c] + t.R[2][a] * X[2][b][c]);
     }
-    // back to Cartesian: first the pair, then the first leg
-    T X[3][3][3];  // [A][b][c]
-#pragma unroll
-    for (int A = 0; A < 3; ++A) unrot_mat(t, Trot[A], X[A]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int c = b; c < 3; ++c)
-          cart[20 + 10 * a + SI(b + 1, c + 1)] =
-              t.R[0][a] * X[0][b][c] + t.R[1][a] * X[1][b][c] + t.R[2][a] * X[2][b][c];
   }
 }
 
@@ -330,67 +346,60 @@ __global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in
   const int i = (int)((p / geo.n_r) % geo.N);
   const int jj = (int)(p / ((long long)geo.n_r * geo.N));
   const Triad<T> t = triad_at<T>(geo, i, jj);
-  decompose_point<T>(in, out, geo.P, p, t);
+  decompose_group<T>((int)blockIdx.y, in, out, geo.P, p, t);
 }
 
 // mode: 0 = write filtered tensor to `dst`;
 //       1..4 = RK4 stage s (1-based) with filtered rhs k_s = reconstruct(sp);
 //       5..8 = RK4 stage without filter: k_s read as Cartesian from sp.
-struct StepArgs {
-  double* u;        // state u_n (read; written at stage 4)
-  double* U;        // next stage state
-  double* kacc;     // accumulator
-  double dt;
-  int* flag;
-};
+// Stage updates: k_1: acc = k, U = u + dt/2 k; k_2: acc += 2k, U = u + dt/2 k;
+// k_3: acc += 2k, U = u + dt k; k_4: u = u + dt/6 (acc + k) (classical RK4).
+// The state sums are FP64 additions; the increments are formed in T.
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
+}
 
 template <class T>
 __global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
-                                                     Geo geo, int mode, StepArgs sa) {
+                                                     Geo geo, int mode, double* __restrict__ u,
+                                                     double* __restrict__ U, double* __restrict__ kacc,
+                                                     double dt, int* __restrict__ flag) {
   const long long P = geo.P;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const int nv = geo.nv;
-  T cart[50];
-  if (mode <= 4) {
-    const int i = (int)((p / geo.n_r) % geo.N);
-    const int jj = (int)(p / ((long long)geo.n_r * geo.N));
-    const Triad<T> t = triad_at<T>(geo, i, jj);
-    reconstruct_point<T>(sp, P, p, t, cart);
-  } else {
-#pragma unroll
-    for (int f = 0; f < 50; ++f) cart[f] = ld<T>(sp, P, p, f);
-  }
-  if (mode == 0) {
-#pragma unroll
-    for (int f = 0; f < 50; ++f) dst[(long long)f * P + p] = S<T>::to_double(cart[f]);
-    return;
-  }
-  const int stage = (mode - 1) % 4;  // 0..3
-  const double dt = sa.dt;
+  const int grp = (int)blockIdx.y;
+  const int stage = (mode - 1) % 4;  // 0..3 for modes 1..8
   const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
   const T wk = S<T>::c(stage == 0 ? 1.0 : 2.0);
   const T sixth = S<T>::c(dt / 6.0);
   bool bad = false;
-#pragma unroll
-  for (int f = 0; f < 50; ++f) {
+  auto emit = [&](int f, T kf) {
     const long long o = (long long)f * P + p;
-    const T kf = cart[f];
-    const double kd = S<T>::to_double(kf);
-    bad |= !isfinite(kd);
-    if (stage < 3) {
-      if (stage == 0)
-        sa.kacc[o] = kd;
-      else
-        sa.kacc[o] = S<T>::to_double(S<T>::load(sa.kacc + o) + wk * kf);
-      sa.U[o] = sa.u[o] + S<T>::to_double(cU * kf);
-    } else {
-      const T inc = sixth * (S<T>::load(sa.kacc + o) + kf);
-      sa.u[o] = sa.u[o] + S<T>::to_double(inc);
+    if (mode == 0) {
+      dst[o] = S<T>::to_double(kf);
+      return;
     }
+    const double kd = S<T>::to_double(kf);
+    bad |= nonfinite_bits(kd);
+    const double uv = u[o];
+    if (stage < 3) {
+      kacc[o] = stage == 0 ? kd : S<T>::to_double(S<T>::load(kacc + o) + wk * kf);
+      U[o] = uv + S<T>::to_double(cU * kf);
+    } else {
+      u[o] = uv + S<T>::to_double(sixth * (S<T>::load(kacc + o) + kf));
+    }
+  };
+  if (mode == 0 || mode <= 4) {
+    const int i = (int)((p / geo.n_r) % geo.N);
+    const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+    const Triad<T> t = triad_at<T>(geo, i, jj);
+    reconstruct_group<T>(grp, sp, P, p, t, emit);
+  } else {
+    // unfiltered stage: the group's Cartesian components straight from sp
+    const int lo = grp * 7, hi = min(50, lo + 7);  // 8 blocks of fields
+    for (int f = lo; f < hi; ++f) emit(f, ld<T>(sp, P, p, f));
   }
-  (void)nv;
-  if (bad) atomicOr(sa.flag, 1);
+  if (bad) atomicOr(flag, 1);
 }
 
 // Spherical -> Cartesian derivatives: D[3][nf][P] -> out[3][nf][P]
@@ -478,9 +487,9 @@ __global__ void k_constraints(const double* __restrict__ u, const double* __rest
 int pw_decompose(const cffyn_shell* sh, const double* in, double* out, cudaStream_t st) {
   Geo g = geo_of(sh);
   if (sh->d.precision == CFFYN_MIXED)
-    k_decompose<ff><<<blocks_for(g.P, 128), 128, 0, st>>>(in, out, g);
+    k_decompose<ff><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(in, out, g);
   else
-    k_decompose<double><<<blocks_for(g.P, 128), 128, 0, st>>>(in, out, g);
+    k_decompose<double><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(in, out, g);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
@@ -489,11 +498,12 @@ int pw_decompose(const cffyn_shell* sh, const double* in, double* out, cudaStrea
 int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mode, double* u, double* U,
                    double* kacc, double dt, int* flag, cudaStream_t st) {
   Geo g = geo_of(sh);
-  StepArgs sa{u, U, kacc, dt, flag};
   if (sh->d.precision == CFFYN_MIXED)
-    k_reconstruct<ff><<<blocks_for(g.P, 128), 128, 0, st>>>(sp, dst, g, mode, sa);
+    k_reconstruct<ff><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(sp, dst, g, mode, u, U, kacc,
+                                                                             dt, flag);
   else
-    k_reconstruct<double><<<blocks_for(g.P, 128), 128, 0, st>>>(sp, dst, g, mode, sa);
+    k_reconstruct<double><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(sp, dst, g, mode, u, U,
+                                                                                 kacc, dt, flag);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;

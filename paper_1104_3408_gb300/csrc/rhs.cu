@@ -461,26 +461,40 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
   }
 }
 
-int pw_rhs(const cffyn_shell* sh, const double* u, const double* D, double* out, cudaStream_t st) {
+// stage = 0: all three kernels; 1: sources with Christoffels; 2: quadratic
+// sources; 3: principal parts + boundary.
+int pw_rhs_part(const cffyn_shell* sh, const double* u, const double* D, double* out, int stage,
+                cudaStream_t st) {
   Geo g = geo_of(sh);
   const unsigned nb = blocks_for(g.P, 128);
-  if (sh->d.precision == CFFYN_MIXED) {
-    k_rhs_gamma<ff><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+  const bool mixed = sh->d.precision == CFFYN_MIXED;
+  if (stage == 0 || stage == 1) {
+    if (mixed)
+      k_rhs_gamma<ff><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+    else
+      k_rhs_gamma<double><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
     count_launch();
-    k_rhs_quad<ff><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+  }
+  if (stage == 0 || stage == 2) {
+    if (mixed)
+      k_rhs_quad<ff><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+    else
+      k_rhs_quad<double><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
     count_launch();
-    k_rhs_pp<ff><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
-    count_launch();
-  } else {
-    k_rhs_gamma<double><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
-    count_launch();
-    k_rhs_quad<double><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
-    count_launch();
-    k_rhs_pp<double><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
+  }
+  if (stage == 0 || stage == 3) {
+    if (mixed)
+      k_rhs_pp<ff><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
+    else
+      k_rhs_pp<double><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
     count_launch();
   }
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
+}
+
+int pw_rhs(const cffyn_shell* sh, const double* u, const double* D, double* out, cudaStream_t st) {
+  return pw_rhs_part(sh, u, D, out, 0, st);
 }
 
 }  // namespace cffyn

@@ -197,7 +197,7 @@ def test_trace_and_profile_report_every_kernel_group(cf):
     ms, launches, steps = sh.get_trace()
     assert steps == 3
     assert all(v > 0 for v in ms.values())
-    assert launches["project"] == 16 and launches["d_r"] == 4 and launches["rhs"] == 12
+    assert launches["project"] == 16 and launches["d_r"] == 4 and launches["rhs_pp"] == 4
     assert sum(launches.values()) == 56
     # tracing does not change the result
     v = dev(u0)
