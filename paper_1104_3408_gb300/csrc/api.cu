@@ -26,9 +26,9 @@ void set_error(const char* fmt, ...) {
 
 // ops.cu
 int set_op_smem_limits();
-int op_deriv_r(const cffyn_shell*, const double*, double*, int, cudaStream_t);
-int op_deriv_theta(const cffyn_shell*, const double*, double*, int, cudaStream_t);
-int op_deriv_phi(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int op_deriv_r(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
+int op_deriv_theta(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
+int op_deriv_phi(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int op_dft_fwd(const cffyn_shell*, const double*, double*, int, cudaStream_t);
 int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t);
 int op_project(const cffyn_shell*, const double*, double*, const int*, int, const int* const[3],
@@ -38,14 +38,14 @@ int build_operators(cffyn_shell*);
 void free_sliced(SlicedOp&);
 // pointwise.cu
 int pw_rhs(const cffyn_shell*, const double*, const double*, double*, cudaStream_t);
-int pw_rhs_part(const cffyn_shell*, const double*, const double*, double*, int, cudaStream_t);
-int pw_decompose(const cffyn_shell*, const double*, double*, cudaStream_t);
+int pw_rhs_part(const cffyn_shell*, const double*, const double*, double*, int, bool, bool, cudaStream_t);
+int pw_decompose(const cffyn_shell*, const double*, double*, bool, cudaStream_t);
 int pw_reconstruct(const cffyn_shell*, const double*, double*, int, double*, double*, double*, double,
                    int*, cudaStream_t);
-int pw_cart(const cffyn_shell*, const double*, double*, int, cudaStream_t);
-int pw_gauge(const cffyn_shell*, const double*, double*, long long, cudaStream_t);
-int pw_constraints(const cffyn_shell*, const double*, const double*, const double*, long long, double*,
-                   cudaStream_t);
+int pw_cart(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
+int pw_gauge(const cffyn_shell*, const double*, double*, cudaStream_t);
+int pw_to_internal(const cffyn_shell*, const double*, double*, long long, cudaStream_t);
+int pw_constraints(const cffyn_shell*, const double*, const double*, const double*, double*, cudaStream_t);
 
 }  // namespace cffyn
 
@@ -72,12 +72,14 @@ int check_ptr(const void* p, const char* what) {
   return CFFYN_OK;
 }
 
-int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, cudaStream_t st) {
+// spherical derivatives of nf fields into D (internal storage); in_pairs: u is
+// a pair-stored internal buffer of the mixed path (else FP64)
+int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, bool in_pairs, cudaStream_t st) {
   const size_t P = sh->P;
   int rc;
-  if ((rc = op_deriv_r(sh, u, D, nf, st))) return rc;
-  if ((rc = op_deriv_theta(sh, u, D + (size_t)nf * P, nf, st))) return rc;
-  if ((rc = op_deriv_phi(sh, u, D + (size_t)2 * nf * P, nf, st))) return rc;
+  if ((rc = op_deriv_r(sh, u, D, nf, in_pairs, st))) return rc;
+  if ((rc = op_deriv_theta(sh, u, D + (size_t)nf * P, nf, in_pairs, st))) return rc;
+  if ((rc = op_deriv_phi(sh, u, D + (size_t)2 * nf * P, nf, in_pairs, st))) return rc;
   return CFFYN_OK;
 }
 
@@ -255,8 +257,9 @@ double cffyn_default_dt(const cffyn_shell* sh) { return sh ? sh->dt_default : 0.
 static int gauge_derivs(cffyn_shell* sh, cudaStream_t st) {
   // d_i H_a with the shell's operators: spherical derivatives into D, chain rule into dH
   int rc;
-  if ((rc = derivs_spherical(sh, sh->H, sh->D, 4, st))) return rc;
-  if ((rc = pw_cart(sh, sh->D, sh->dH, 4, st))) return rc;
+  const bool pairs = sh->d.precision == CFFYN_MIXED;
+  if ((rc = derivs_spherical(sh, sh->H, sh->D, 4, pairs, st))) return rc;
+  if ((rc = pw_cart(sh, sh->D, sh->dH, 4, true, st))) return rc;
   sh->gauge_set = true;
   return CFFYN_OK;
 }
@@ -266,7 +269,7 @@ int cffyn_set_gauge(cffyn_shell* sh, const double* H, void* stream) {
   int rc;
   if ((rc = check_ptr(H, "H"))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  CF_CUDA(cudaMemcpyAsync(sh->H, H, 4 * sh->P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if ((rc = pw_to_internal(sh, H, sh->H, 4 * (long long)sh->P, st))) return rc;
   return gauge_derivs(sh, st);
 }
 
@@ -275,7 +278,7 @@ int cffyn_init_gauge_from_state(cffyn_shell* sh, double* u, void* stream) {
   int rc;
   if ((rc = check_ptr(u, "u"))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = pw_gauge(sh, u, sh->H, (long long)sh->P, st))) return rc;
+  if ((rc = pw_gauge(sh, u, sh->H, st))) return rc;
   return gauge_derivs(sh, st);
 }
 
@@ -284,8 +287,8 @@ int cffyn_derivs(cffyn_shell* sh, const double* u, double* dxyz, void* stream) {
   int rc;
   if ((rc = check_ptr(u, "u")) || (rc = check_ptr(dxyz, "dxyz"))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, st))) return rc;
-  return pw_cart(sh, sh->D, dxyz, sh->nv, st);
+  if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, false, st))) return rc;
+  return pw_cart(sh, sh->D, dxyz, sh->nv, false, st);
 }
 
 int cffyn_rhs(cffyn_shell* sh, const double* u, double* dudt, void* stream) {
@@ -297,7 +300,7 @@ int cffyn_rhs(cffyn_shell* sh, const double* u, double* dudt, void* stream) {
     return CFFYN_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, st))) return rc;
+  if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, false, st))) return rc;
   return pw_rhs(sh, u, sh->D, dudt, st);
 }
 
@@ -306,7 +309,7 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
   int rc;
   if ((rc = check_ptr(u, "u")) || (rc = check_ptr(out, "out"))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = pw_decompose(sh, u, sh->S, st))) return rc;
+  if ((rc = pw_decompose(sh, u, sh->S, false, st))) return rc;
   if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
   return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
 }
@@ -343,14 +346,15 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
   for (int s = 0; s < 4; ++s) {
     const double* X = s == 0 ? u : sh->U;
     double* spin = sh->D + 2 * nvP;  // derivatives are dead after the rhs
-    if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, st); }))) return rc;
-    if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, st); }))) return rc;
-    if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, st); }))) return rc;
-    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, st); }))) return rc;
-    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, st); }))) return rc;
-    if ((rc = run(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, st); }))) return rc;
+    const bool xp = s > 0;  // stage states U are pair-stored on the mixed path
+    if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
+    if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) return rc;
+    if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) return rc;
+    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
+    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
+    if ((rc = run(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
     if (per_sub) {
-      if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, st); }))) return rc;
+      if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
       if ((rc = run(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return rc;
       if ((rc = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
         return rc;
@@ -367,7 +371,7 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
     }
   }
   if (!per_sub) {
-    if ((rc = run(6, [&] { return pw_decompose(sh, u, sh->S, st); }))) return rc;
+    if ((rc = run(6, [&] { return pw_decompose(sh, u, sh->S, false, st); }))) return rc;
     if ((rc = run(7, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); }))) return rc;
     if ((rc = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
       return rc;
@@ -475,12 +479,12 @@ int cffyn_constraint_norms(cffyn_shell* sh, const double* u, double out[2], void
   }
   cudaStream_t st = (cudaStream_t)stream;
   // derivatives of g_ab only (fields 0..9)
-  if ((rc = derivs_spherical(sh, u, sh->D, 10, st))) return rc;
-  double* dcart = sh->S;  // [3][10][P]
-  if ((rc = pw_cart(sh, sh->D, dcart, 10, st))) return rc;
+  if ((rc = derivs_spherical(sh, u, sh->D, 10, false, st))) return rc;
+  double* dcart = sh->S;  // [3][10][P], FP64
+  if ((rc = pw_cart(sh, sh->D, dcart, 10, false, st))) return rc;
   double* red = sh->red;
   CF_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
-  if ((rc = pw_constraints(sh, u, dcart, sh->H, (long long)sh->P, red, st))) return rc;
+  if ((rc = pw_constraints(sh, u, dcart, sh->H, red, st))) return rc;
   double h[2];
   CF_CUDA(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st));
   CF_CUDA(cudaStreamSynchronize(st));
@@ -557,14 +561,15 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
   for (int s = 0; s < 4 && !rc; ++s) {
     const double* X = s == 0 ? u : sh->U;
     double* spin = sh->D + 2 * nvP;
-    if ((rc = phase(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, st); }))) break;
-    if ((rc = phase(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, st); }))) break;
-    if ((rc = phase(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, st); }))) break;
-    if ((rc = phase(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, st); }))) break;
-    if ((rc = phase(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, st); }))) break;
-    if ((rc = phase(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, st); }))) break;
+    const bool xp = s > 0;
+    if ((rc = phase(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) break;
+    if ((rc = phase(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) break;
+    if ((rc = phase(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) break;
+    if ((rc = phase(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) break;
+    if ((rc = phase(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) break;
+    if ((rc = phase(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) break;
     if (per_sub) {
-      if ((rc = phase(6, [&] { return pw_decompose(sh, sh->S, spin, st); }))) break;
+      if ((rc = phase(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) break;
       if ((rc = phase(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) break;
       if ((rc = phase(8, [&] {
              return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
@@ -583,7 +588,7 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     }
   }
   if (!rc && !per_sub) {
-    rc = phase(6, [&] { return pw_decompose(sh, u, sh->S, st); });
+    rc = phase(6, [&] { return pw_decompose(sh, u, sh->S, false, st); });
     if (!rc) rc = phase(7, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); });
     if (!rc)
       rc = phase(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); });

@@ -23,6 +23,7 @@
 #include <cstdio>
 
 #include "common.cuh"
+#include "scalar.cuh"
 
 namespace cffyn {
 
@@ -148,6 +149,20 @@ __device__ __forceinline__ double load_elem(const OpArgs& a, const ColDesc& d, i
   return __longlong_as_double(__double_as_longlong(v) ^ ((long long)d.sgn1 << 63));
 }
 
+// Raw 64-bit element of a column for the split-precision core: an FP64 word
+// (FI = false) or a (hi, lo) float pair (FI = true), sign applied on the bits.
+template <bool FI>
+__device__ __forceinline__ long long load_raw(const OpArgs& a, const ColDesc& d, int k) {
+  if (!d.valid || k >= a.g.K) return 0;
+  const long long* in = reinterpret_cast<const long long*>(a.in);
+  if (k < a.g.K0) return __ldg(in + d.in0 + (long long)k * a.g.in_rs);
+  if (d.sgn1 == 2) return 0;
+  int kk = a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0);
+  const long long w = __ldg(in + d.in1 + (long long)kk * a.g.in_rs);
+  const long long m = FI ? (long long)0x8000000080000000ull : (long long)0x8000000000000000ull;
+  return d.sgn1 ? (w ^ m) : w;
+}
+
 __device__ __forceinline__ void store_elem(const OpArgs& a, const ColDesc& d, int p, double v) {
   if (!d.valid || p >= a.g.P) return;
   if (p < a.g.P0)
@@ -234,6 +249,30 @@ __device__ __forceinline__ int exp_field(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
 }
 
+// frexp exponent + 1022 of a raw element (0 for zero): FP64 word, or the
+// leading float of a pair (|hi + lo| < 2^frexp(hi) for a normalised pair)
+template <bool FI>
+__device__ __forceinline__ int raw_exp(long long w) {
+  if (FI) {
+    const int e = (int)(((unsigned int)w >> 23) & 0xff);
+    return e ? e - 126 + 1022 : 0;
+  }
+  return (int)((w >> 52) & 0x7ff);
+}
+
+// round(x 2^(47-E)) for one float, integer operations only
+__device__ __forceinline__ long long fixed47f(unsigned int u, int E) {
+  const int e = (int)((u >> 23) & 0xff);
+  if (e == 0) return 0;
+  const long long M = (long long)((u & 0x7fffff) | 0x800000);
+  const int sh = e - 103 - E;  // <= 23 because |x| < 2^E
+  long long Z;
+  if (sh >= 0) Z = M << sh;
+  else if (sh > -26) Z = (M + (1ll << (-sh - 1))) >> (-sh);
+  else Z = 0;
+  return (u >> 31) ? -Z : Z;
+}
+
 // 47-bit fixed point Z = round(x 2^(47-E)) of x relative to 2^E (|x| < 2^E),
 // integer operations only.
 __device__ __forceinline__ long long fixed47(double x, int E) {
@@ -247,6 +286,12 @@ __device__ __forceinline__ long long fixed47(double x, int E) {
     if (b >> 63) Z = -Z;
   }
   return Z;
+}
+
+template <bool FI>
+__device__ __forceinline__ long long raw_fixed47(long long w, int E) {
+  if (FI) return fixed47f((unsigned int)w, E) + fixed47f((unsigned int)((unsigned long long)w >> 32), E);
+  return fixed47(__longlong_as_double(w), E);
 }
 
 // Balanced base-256 digits of Z (|Z| <= 2^47): with Zb = Z + sum_{k<5} 128*256^k
@@ -312,6 +357,25 @@ __device__ __forceinline__ void ldmatrix_x4(unsigned int& r0, unsigned int& r1, 
                : "r"(a));
 }
 
+// T * 2^sc as a (hi, lo) float pair packed in 64 bits: hi exact leading 24
+// bits, lo the next 24 (truncated).
+__device__ __forceinline__ long long i64_scaled_to_pair(long long T, int sc) {
+  if (T == 0) return 0;
+  const bool neg = T < 0;
+  const unsigned long long v = neg ? (unsigned long long)(-T) : (unsigned long long)T;
+  const int nb = 64 - __clzll((long long)v);
+  float hi, lo = 0.0f;
+  if (nb <= 24) {
+    hi = u64_scaled_to_float(v, sc, neg);
+  } else {
+    const int sh = nb - 24;
+    const unsigned long long hm = v >> sh;
+    hi = u64_scaled_to_float(hm, sc + sh, neg);
+    lo = u64_scaled_to_float(v - (hm << sh), sc, neg);
+  }
+  return (long long)(((unsigned long long)__float_as_uint(lo) << 32) | __float_as_uint(hi));
+}
+
 __device__ __forceinline__ void mma_bf16(float c[4], const uint4& a, unsigned int b0, unsigned int b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
@@ -321,6 +385,7 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint4& a, unsigned in
 }
 
 // CTA: one warp per m-tile of W (mtiles warps), OZ_QT columns.
+template <bool FI, bool FO>
 __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
   extern __shared__ unsigned short smoz[];
   if (a.batched_m) {
@@ -349,17 +414,17 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
   const int nitems = KH * OZ_QT;
   // one pass over global memory: values stay in registers between the column
   // exponent reduction and the digit extraction
-  double v0[OZ_ITEMS], v1[OZ_ITEMS];
+  long long v0[OZ_ITEMS], v1[OZ_ITEMS];
 #pragma unroll
   for (int it = 0; it < OZ_ITEMS; ++it) {
     const int e = tid + it * nthr;
-    v0[it] = v1[it] = 0.0;
+    v0[it] = v1[it] = 0;
     if (e < nitems) {
       int kp, c;
       if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
-      v0[it] = load_elem(a, cols[c], 2 * kp);
-      v1[it] = load_elem(a, cols[c], 2 * kp + 1);
-      const int ex = max(exp_field(v0[it]), exp_field(v1[it]));  // 0 for zero
+      v0[it] = load_raw<FI>(a, cols[c], 2 * kp);
+      v1[it] = load_raw<FI>(a, cols[c], 2 * kp + 1);
+      const int ex = max(raw_exp<FI>(v0[it]), raw_exp<FI>(v1[it]));  // 0 for zero
       if (ex) atomicMax(&colE[c], ex - 1022);
     }
   }
@@ -372,8 +437,8 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
       if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
       const int E = colE[c];
       unsigned int d0[kSlices], d1[kSlices];
-      digits_bf16(fixed47(v0[it], E), d0);
-      digits_bf16(fixed47(v1[it], E), d1);
+      digits_bf16(raw_fixed47<FI>(v0[it], E), d0);
+      digits_bf16(raw_fixed47<FI>(v1[it], E), d1);
 #pragma unroll
       for (int s2 = 0; s2 < kSlices; ++s2) Bw[((size_t)s2 * OZ_QT + c) * KPW + kp] = d0[s2] | (d1[s2] << 16);
     }
@@ -429,22 +494,25 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
   for (int n = 0; n < OZ_NT; ++n) {
     const int cA = n * 8 + 2 * tg, cB = cA + 1;
     const int sA = colE[cA], sB = colE[cB];
-    const double v0 = i64_scaled_to_double(T[n][0], eA + sA - 54);
-    const double v1 = i64_scaled_to_double(T[n][1], eA + sB - 54);
-    const double v2 = i64_scaled_to_double(T[n][2], eB + sA - 54);
-    const double v3 = i64_scaled_to_double(T[n][3], eB + sB - 54);
-    store_elem(a, cols[cA], rowA, v0);
-    store_elem(a, cols[cB], rowA, v1);
-    store_elem(a, cols[cA], rowB, v2);
-    store_elem(a, cols[cB], rowB, v3);
+    auto put = [&](const ColDesc& d, int row, long long t, int sc) {
+      const long long w = FO ? i64_scaled_to_pair(t, sc)
+                             : __double_as_longlong(i64_scaled_to_double(t, sc));
+      store_elem(a, d, row, __longlong_as_double(w));
+    };
+    put(cols[cA], rowA, T[n][0], eA + sA - 54);
+    put(cols[cB], rowA, T[n][1], eA + sB - 54);
+    put(cols[cA], rowB, T[n][2], eB + sA - 54);
+    put(cols[cB], rowB, T[n][3], eB + sB - 54);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 
+// in_pairs / out_pairs: the mixed path's internal pair storage (ignored on
+// the FP64 path, whose buffers are all FP64)
 static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const SlicedOp* Ws,
-                  dim3 extra, cudaStream_t st) {
+                  dim3 extra, cudaStream_t st, bool in_pairs = true, bool out_pairs = true) {
   if (a.g.ncols <= 0) return CFFYN_OK;
   if (sh->d.precision == CFFYN_FP64 || Ws == nullptr) {
     unsigned gx = (unsigned)((a.g.ncols + F64_QT - 1) / F64_QT);
@@ -460,7 +528,15 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
     int KH = Ws->ksteps * 8;
     int warps = max(Ws->mtiles, (KH + OZ_ITEMS - 1) / OZ_ITEMS);
     int threads = warps * 32;
-    k_op_ozaki<<<dim3(gx, extra.y), threads, smem, st>>>(a, *Ws);
+    const dim3 grid(gx, extra.y);
+    if (in_pairs && out_pairs)
+      k_op_ozaki<true, true><<<grid, threads, smem, st>>>(a, *Ws);
+    else if (out_pairs)
+      k_op_ozaki<false, true><<<grid, threads, smem, st>>>(a, *Ws);
+    else if (in_pairs)
+      k_op_ozaki<true, false><<<grid, threads, smem, st>>>(a, *Ws);
+    else
+      k_op_ozaki<false, false><<<grid, threads, smem, st>>>(a, *Ws);
     count_launch();
   }
   CF_CUDA(cudaGetLastError());
@@ -469,7 +545,10 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
 
 int set_op_smem_limits() {
   CF_CUDA(cudaFuncSetAttribute(k_op_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   return CFFYN_OK;
 }
 
@@ -485,7 +564,8 @@ static OpArgs base_args(const cffyn_shell* sh) {
 }
 
 // d_r of nfields fields: in/out [nfields][P]
-int op_deriv_r(const cffyn_shell* sh, const double* in, double* out, int nfields, cudaStream_t st) {
+int op_deriv_r(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
+                 cudaStream_t st) {
   OpArgs a = base_args(sh);
   a.kind = OP_R;
   a.in = in;
@@ -493,10 +573,10 @@ int op_deriv_r(const cffyn_shell* sh, const double* in, double* out, int nfields
   a.g.K = a.g.K0 = a.g.P = a.g.P0 = sh->n_r;
   a.g.in_rs = a.g.out_rs = 1;
   a.g.ncols = (long long)nfields * sh->J * sh->N;
-  return launch(sh, a, sh->Dr, &sh->sDr, dim3(1, 1), st);
+  return launch(sh, a, sh->Dr, &sh->sDr, dim3(1, 1), st, in_pairs, true);
 }
 
-int op_deriv_theta(const cffyn_shell* sh, const double* in, double* out, int nfields,
+int op_deriv_theta(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
                    cudaStream_t st) {
   OpArgs a = base_args(sh);
   a.kind = OP_THETA;
@@ -507,12 +587,12 @@ int op_deriv_theta(const cffyn_shell* sh, const double* in, double* out, int nfi
   a.g.rev1 = 1;
   a.g.in_rs = a.g.out_rs = sh->n_r;
   a.g.ncols = (long long)nfields * (sh->J / 2) * sh->n_r;
-  return launch(sh, a, sh->Dth2, &sh->sDth2, dim3(1, 1), st);
+  return launch(sh, a, sh->Dth2, &sh->sDth2, dim3(1, 1), st, in_pairs, true);
 }
 
 static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb, int K, int P,
                    long long in_bs, long long out_bs, const double* W, const SlicedOp* Ws,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool in_pairs = true) {
   OpArgs a = base_args(sh);
   a.kind = OP_ROWS;
   a.in = in;
@@ -524,12 +604,13 @@ static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb,
   a.g.P = a.g.P0 = P;
   a.g.in_rs = a.g.out_rs = a.Q;
   a.g.ncols = (long long)nb * a.Q;
-  return launch(sh, a, W, Ws, dim3(1, 1), st);
+  return launch(sh, a, W, Ws, dim3(1, 1), st, in_pairs, true);
 }
 
-int op_deriv_phi(const cffyn_shell* sh, const double* in, double* out, int nfields, cudaStream_t st) {
+int op_deriv_phi(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
+                 cudaStream_t st) {
   long long bs = (long long)sh->P;
-  return op_rows(sh, in, out, nfields, sh->J, sh->J, bs, bs, sh->Dph, &sh->sDph, st);
+  return op_rows(sh, in, out, nfields, sh->J, sh->J, bs, bs, sh->Dph, &sh->sDph, st, in_pairs);
 }
 
 // phi analysis: S[f][j][i][k] -> C[f][row][i][k]

@@ -87,14 +87,17 @@ __device__ __forceinline__ void unrot_mat(const Triad<T>& t, const T O[3][3], T 
 #define SLOT_C2(q) (38 + 2 * (q))
 #define SLOT_C3 48
 
-template <class T>
+template <class T, bool F = false>
 __device__ __forceinline__ T ld(const double* a, long long P, long long p, int f) {
-  return S<T>::load(a + (long long)f * P + p);
+  return Store<T, F>::ld(a, (long long)f * P + p);
 }
-template <class T>
+template <bool F = false, class T>
 __device__ __forceinline__ void st(double* a, long long P, long long p, int f, T v) {
-  a[(long long)f * P + p] = S<T>::to_double(v);
+  Store<T, F>::st(a, (long long)f * P + p, v);
 }
+// internal buffers are pair-stored in the double-float path
+template <class T> constexpr bool kIn = false;
+template <> constexpr bool kIn<ff> = true;
 
 // Tensor groups handled by one thread each (blockIdx.y), so that a thread
 // holds at most the 18 components of Phi_ijk:
@@ -102,15 +105,15 @@ __device__ __forceinline__ void st(double* a, long long P, long long p, int f, T
 //   6: Phi_itj       7: Phi_ijk
 constexpr int kGroups = 8;
 
-template <class T>
+template <class T, bool FI>
 __device__ __forceinline__ void decompose_group(int grp, const double* __restrict__ in,
                                                 double* __restrict__ out, long long P, long long p,
                                                 const Triad<T>& t) {
   const T two = S<T>::c(2.0);
   switch (grp) {
     case 0:
-      st(out, P, p, SLOT_R0(0), ld<T>(in, P, p, SI(0, 0)));
-      st(out, P, p, SLOT_R0(1), ld<T>(in, P, p, 10 + SI(0, 0)));
+      st<kIn<T>>(out, P, p, SLOT_R0(0), ld<T, FI>(in, P, p, SI(0, 0)));
+      st<kIn<T>>(out, P, p, SLOT_R0(1), ld<T, FI>(in, P, p, 10 + SI(0, 0)));
       break;
     case 1:
     case 2:
@@ -120,11 +123,11 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
       const int st_ = gph == 2 ? 10 : 1;
       T v[3], o[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) v[a] = ld<T>(in, P, p, b0 + st_ * a);
+      for (int a = 0; a < 3; ++a) v[a] = ld<T, FI>(in, P, p, b0 + st_ * a);
       rot_vec(t, v, o);
-      st(out, P, p, SLOT_R0(2 + gph), o[0]);
-      st(out, P, p, SLOT_C1(gph), o[1]);
-      st(out, P, p, SLOT_C1(gph) + 1, o[2]);
+      st<kIn<T>>(out, P, p, SLOT_R0(2 + gph), o[0]);
+      st<kIn<T>>(out, P, p, SLOT_C1(gph), o[1]);
+      st<kIn<T>>(out, P, p, SLOT_C1(gph) + 1, o[2]);
       break;
     }
     case 4:
@@ -135,14 +138,14 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, b0 + SI(a + 1, b + 1));
+        for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T, FI>(in, P, p, b0 + SI(a + 1, b + 1));
       rot_mat(t, Tm, O);
-      st(out, P, p, SLOT_R0(5 + 2 * gph), O[0][0]);
-      st(out, P, p, SLOT_R0(6 + 2 * gph), O[1][1] + O[2][2]);
-      st(out, P, p, SLOT_C1(3 + gph), O[0][1]);
-      st(out, P, p, SLOT_C1(3 + gph) + 1, O[0][2]);
-      st(out, P, p, SLOT_C2(gph), O[1][1] - O[2][2]);
-      st(out, P, p, SLOT_C2(gph) + 1, two * O[1][2]);
+      st<kIn<T>>(out, P, p, SLOT_R0(5 + 2 * gph), O[0][0]);
+      st<kIn<T>>(out, P, p, SLOT_R0(6 + 2 * gph), O[1][1] + O[2][2]);
+      st<kIn<T>>(out, P, p, SLOT_C1(3 + gph), O[0][1]);
+      st<kIn<T>>(out, P, p, SLOT_C1(3 + gph) + 1, O[0][2]);
+      st<kIn<T>>(out, P, p, SLOT_C2(gph), O[1][1] - O[2][2]);
+      st<kIn<T>>(out, P, p, SLOT_C2(gph) + 1, two * O[1][2]);
       break;
     }
     case 6: {
@@ -150,17 +153,17 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T>(in, P, p, 20 + 10 * a + SI(0, b + 1));
+        for (int b = 0; b < 3; ++b) Tm[a][b] = ld<T, FI>(in, P, p, 20 + 10 * a + SI(0, b + 1));
       rot_mat(t, Tm, O);
-      st(out, P, p, SLOT_R0(9), O[0][0]);
-      st(out, P, p, SLOT_C1(5), O[0][1]);
-      st(out, P, p, SLOT_C1(5) + 1, O[0][2]);
-      st(out, P, p, SLOT_C1(6), O[1][0]);
-      st(out, P, p, SLOT_C1(6) + 1, O[2][0]);
-      st(out, P, p, SLOT_C2(2), O[1][1] - O[2][2]);
-      st(out, P, p, SLOT_C2(2) + 1, O[1][2] + O[2][1]);
-      st(out, P, p, SLOT_R0(12), O[1][1] + O[2][2]);
-      st(out, P, p, SLOT_R0(13), O[2][1] - O[1][2]);
+      st<kIn<T>>(out, P, p, SLOT_R0(9), O[0][0]);
+      st<kIn<T>>(out, P, p, SLOT_C1(5), O[0][1]);
+      st<kIn<T>>(out, P, p, SLOT_C1(5) + 1, O[0][2]);
+      st<kIn<T>>(out, P, p, SLOT_C1(6), O[1][0]);
+      st<kIn<T>>(out, P, p, SLOT_C1(6) + 1, O[2][0]);
+      st<kIn<T>>(out, P, p, SLOT_C2(2), O[1][1] - O[2][2]);
+      st<kIn<T>>(out, P, p, SLOT_C2(2) + 1, O[1][2] + O[2][1]);
+      st<kIn<T>>(out, P, p, SLOT_R0(12), O[1][1] + O[2][2]);
+      st<kIn<T>>(out, P, p, SLOT_R0(13), O[2][1] - O[1][2]);
       break;
     }
     default: {
@@ -172,7 +175,7 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) Tm[b][c] = ld<T>(in, P, p, 20 + 10 * a + SI(b + 1, c + 1));
+          for (int c = 0; c < 3; ++c) Tm[b][c] = ld<T, FI>(in, P, p, 20 + 10 * a + SI(b + 1, c + 1));
         rot_mat(t, Tm, Trot[a]);
       }
 #pragma unroll
@@ -190,28 +193,28 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
         Pmm[A][0] = O[1][1] - O[2][2];
         Pmm[A][1] = two * O[1][2];
       }
-      st(out, P, p, SLOT_R0(10), Pr[0]);
-      st(out, P, p, SLOT_R0(11), Pmb[0]);
-      st(out, P, p, SLOT_C1(7), Prm[0][0]);
-      st(out, P, p, SLOT_C1(7) + 1, Prm[0][1]);
-      st(out, P, p, SLOT_C2(3), Pmm[0][0]);
-      st(out, P, p, SLOT_C2(3) + 1, Pmm[0][1]);
-      st(out, P, p, SLOT_C1(8), Pr[1]);
-      st(out, P, p, SLOT_C1(8) + 1, Pr[2]);
-      st(out, P, p, SLOT_C1(9), Pmb[1]);
-      st(out, P, p, SLOT_C1(9) + 1, Pmb[2]);
+      st<kIn<T>>(out, P, p, SLOT_R0(10), Pr[0]);
+      st<kIn<T>>(out, P, p, SLOT_R0(11), Pmb[0]);
+      st<kIn<T>>(out, P, p, SLOT_C1(7), Prm[0][0]);
+      st<kIn<T>>(out, P, p, SLOT_C1(7) + 1, Prm[0][1]);
+      st<kIn<T>>(out, P, p, SLOT_C2(3), Pmm[0][0]);
+      st<kIn<T>>(out, P, p, SLOT_C2(3) + 1, Pmm[0][1]);
+      st<kIn<T>>(out, P, p, SLOT_C1(8), Pr[1]);
+      st<kIn<T>>(out, P, p, SLOT_C1(8) + 1, Pr[2]);
+      st<kIn<T>>(out, P, p, SLOT_C1(9), Pmb[1]);
+      st<kIn<T>>(out, P, p, SLOT_C1(9) + 1, Pmb[2]);
       // (mbar; mm) = P_mm^theta - i P_mm^phi
-      st(out, P, p, SLOT_C1(10), Pmm[1][0] + Pmm[2][1]);
-      st(out, P, p, SLOT_C1(10) + 1, Pmm[1][1] - Pmm[2][0]);
+      st<kIn<T>>(out, P, p, SLOT_C1(10), Pmm[1][0] + Pmm[2][1]);
+      st<kIn<T>>(out, P, p, SLOT_C1(10) + 1, Pmm[1][1] - Pmm[2][0]);
       // (m; rm) = P_rm^theta + i P_rm^phi
-      st(out, P, p, SLOT_C2(4), Prm[1][0] - Prm[2][1]);
-      st(out, P, p, SLOT_C2(4) + 1, Prm[1][1] + Prm[2][0]);
+      st<kIn<T>>(out, P, p, SLOT_C2(4), Prm[1][0] - Prm[2][1]);
+      st<kIn<T>>(out, P, p, SLOT_C2(4) + 1, Prm[1][1] + Prm[2][0]);
       // (m; r mbar) = conj(P_rm^theta) + i conj(P_rm^phi)   (spin 0)
-      st(out, P, p, SLOT_R0(14), Prm[1][0] + Prm[2][1]);
-      st(out, P, p, SLOT_R0(15), Prm[2][0] - Prm[1][1]);
+      st<kIn<T>>(out, P, p, SLOT_R0(14), Prm[1][0] + Prm[2][1]);
+      st<kIn<T>>(out, P, p, SLOT_R0(15), Prm[2][0] - Prm[1][1]);
       // (m; mm) = P_mm^theta + i P_mm^phi
-      st(out, P, p, SLOT_C3, Pmm[1][0] - Pmm[2][1]);
-      st(out, P, p, SLOT_C3 + 1, Pmm[1][1] + Pmm[2][0]);
+      st<kIn<T>>(out, P, p, SLOT_C3, Pmm[1][0] - Pmm[2][1]);
+      st<kIn<T>>(out, P, p, SLOT_C3 + 1, Pmm[1][1] + Pmm[2][0]);
     }
   }
 }
@@ -224,8 +227,8 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
   const T half = S<T>::c(0.5);
   switch (grp) {
     case 0:
-      emit(SI(0, 0), ld<T>(sp, P, p, SLOT_R0(0)));
-      emit(10 + SI(0, 0), ld<T>(sp, P, p, SLOT_R0(1)));
+      emit(SI(0, 0), ld<T, kIn<T>>(sp, P, p, SLOT_R0(0)));
+      emit(10 + SI(0, 0), ld<T, kIn<T>>(sp, P, p, SLOT_R0(1)));
       break;
     case 1:
     case 2:
@@ -233,8 +236,8 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
       const int gph = grp - 1;
       const int b0 = gph == 0 ? 1 : (gph == 1 ? 11 : 20);
       const int st_ = gph == 2 ? 10 : 1;
-      T o[3] = {ld<T>(sp, P, p, SLOT_R0(2 + gph)), ld<T>(sp, P, p, SLOT_C1(gph)),
-                ld<T>(sp, P, p, SLOT_C1(gph) + 1)};
+      T o[3] = {ld<T, kIn<T>>(sp, P, p, SLOT_R0(2 + gph)), ld<T, kIn<T>>(sp, P, p, SLOT_C1(gph)),
+                ld<T, kIn<T>>(sp, P, p, SLOT_C1(gph) + 1)};
       T v[3];
       unrot_vec(t, o, v);
 #pragma unroll
@@ -245,10 +248,10 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
     case 5: {
       const int gph = grp - 4;
       const int b0 = gph * 10;
-      const T rr = ld<T>(sp, P, p, SLOT_R0(5 + 2 * gph));
-      const T mmb = ld<T>(sp, P, p, SLOT_R0(6 + 2 * gph));
-      const T rmr = ld<T>(sp, P, p, SLOT_C1(3 + gph)), rmi = ld<T>(sp, P, p, SLOT_C1(3 + gph) + 1);
-      const T mmr = ld<T>(sp, P, p, SLOT_C2(gph)), mmi = ld<T>(sp, P, p, SLOT_C2(gph) + 1);
+      const T rr = ld<T, kIn<T>>(sp, P, p, SLOT_R0(5 + 2 * gph));
+      const T mmb = ld<T, kIn<T>>(sp, P, p, SLOT_R0(6 + 2 * gph));
+      const T rmr = ld<T, kIn<T>>(sp, P, p, SLOT_C1(3 + gph)), rmi = ld<T, kIn<T>>(sp, P, p, SLOT_C1(3 + gph) + 1);
+      const T mmr = ld<T, kIn<T>>(sp, P, p, SLOT_C2(gph)), mmi = ld<T, kIn<T>>(sp, P, p, SLOT_C2(gph) + 1);
       T O[3][3], Tm[3][3];
       O[0][0] = rr;
       O[0][1] = O[1][0] = rmr;
@@ -264,15 +267,15 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
       break;
     }
     case 6: {
-      const T s9 = ld<T>(sp, P, p, SLOT_R0(9));
-      const T s12 = ld<T>(sp, P, p, SLOT_R0(12)), s13 = ld<T>(sp, P, p, SLOT_R0(13));
-      const T s42 = ld<T>(sp, P, p, SLOT_C2(2)), s43 = ld<T>(sp, P, p, SLOT_C2(2) + 1);
+      const T s9 = ld<T, kIn<T>>(sp, P, p, SLOT_R0(9));
+      const T s12 = ld<T, kIn<T>>(sp, P, p, SLOT_R0(12)), s13 = ld<T, kIn<T>>(sp, P, p, SLOT_R0(13));
+      const T s42 = ld<T, kIn<T>>(sp, P, p, SLOT_C2(2)), s43 = ld<T, kIn<T>>(sp, P, p, SLOT_C2(2) + 1);
       T O[3][3], Tm[3][3];
       O[0][0] = s9;
-      O[0][1] = ld<T>(sp, P, p, SLOT_C1(5));
-      O[0][2] = ld<T>(sp, P, p, SLOT_C1(5) + 1);
-      O[1][0] = ld<T>(sp, P, p, SLOT_C1(6));
-      O[2][0] = ld<T>(sp, P, p, SLOT_C1(6) + 1);
+      O[0][1] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(5));
+      O[0][2] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(5) + 1);
+      O[1][0] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(6));
+      O[2][0] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(6) + 1);
       O[1][1] = half * (s42 + s12);
       O[2][2] = half * (s12 - s42);
       O[1][2] = half * (s43 - s13);
@@ -286,20 +289,20 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
     }
     default: {
       T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];
-      Pr[0] = ld<T>(sp, P, p, SLOT_R0(10));
-      Pmb[0] = ld<T>(sp, P, p, SLOT_R0(11));
-      Prm[0][0] = ld<T>(sp, P, p, SLOT_C1(7));
-      Prm[0][1] = ld<T>(sp, P, p, SLOT_C1(7) + 1);
-      Pmm[0][0] = ld<T>(sp, P, p, SLOT_C2(3));
-      Pmm[0][1] = ld<T>(sp, P, p, SLOT_C2(3) + 1);
-      Pr[1] = ld<T>(sp, P, p, SLOT_C1(8));
-      Pr[2] = ld<T>(sp, P, p, SLOT_C1(8) + 1);
-      Pmb[1] = ld<T>(sp, P, p, SLOT_C1(9));
-      Pmb[2] = ld<T>(sp, P, p, SLOT_C1(9) + 1);
+      Pr[0] = ld<T, kIn<T>>(sp, P, p, SLOT_R0(10));
+      Pmb[0] = ld<T, kIn<T>>(sp, P, p, SLOT_R0(11));
+      Prm[0][0] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(7));
+      Prm[0][1] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(7) + 1);
+      Pmm[0][0] = ld<T, kIn<T>>(sp, P, p, SLOT_C2(3));
+      Pmm[0][1] = ld<T, kIn<T>>(sp, P, p, SLOT_C2(3) + 1);
+      Pr[1] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(8));
+      Pr[2] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(8) + 1);
+      Pmb[1] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(9));
+      Pmb[2] = ld<T, kIn<T>>(sp, P, p, SLOT_C1(9) + 1);
       {
         // X = (m; rm) = P^th + i P^ph, Y = (m; r mbar) = conj(P^th) + i conj(P^ph)
-        const T xr = ld<T>(sp, P, p, SLOT_C2(4)), xi = ld<T>(sp, P, p, SLOT_C2(4) + 1);
-        const T yr = ld<T>(sp, P, p, SLOT_R0(14)), yi = ld<T>(sp, P, p, SLOT_R0(15));
+        const T xr = ld<T, kIn<T>>(sp, P, p, SLOT_C2(4)), xi = ld<T, kIn<T>>(sp, P, p, SLOT_C2(4) + 1);
+        const T yr = ld<T, kIn<T>>(sp, P, p, SLOT_R0(14)), yi = ld<T, kIn<T>>(sp, P, p, SLOT_R0(15));
         Prm[1][0] = half * (xr + yr);
         Prm[1][1] = half * (xi - yi);
         Prm[2][0] = half * (xi + yi);
@@ -307,8 +310,8 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
       }
       {
         // X = (m; mm) = P^th + i P^ph, Z = (mbar; mm) = P^th - i P^ph
-        const T xr = ld<T>(sp, P, p, SLOT_C3), xi = ld<T>(sp, P, p, SLOT_C3 + 1);
-        const T zr = ld<T>(sp, P, p, SLOT_C1(10)), zi = ld<T>(sp, P, p, SLOT_C1(10) + 1);
+        const T xr = ld<T, kIn<T>>(sp, P, p, SLOT_C3), xi = ld<T, kIn<T>>(sp, P, p, SLOT_C3 + 1);
+        const T zr = ld<T, kIn<T>>(sp, P, p, SLOT_C1(10)), zi = ld<T, kIn<T>>(sp, P, p, SLOT_C1(10) + 1);
         Pmm[1][0] = half * (xr + zr);
         Pmm[1][1] = half * (xi + zi);
         Pmm[2][0] = half * (xi - zi);
@@ -338,7 +341,7 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
   }
 }
 
-template <class T>
+template <class T, bool FI>
 __global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in, double* __restrict__ out,
                                                    Geo geo) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in
   const int i = (int)((p / geo.n_r) % geo.N);
   const int jj = (int)(p / ((long long)geo.n_r * geo.N));
   const Triad<T> t = triad_at<T>(geo, i, jj);
-  decompose_group<T>((int)blockIdx.y, in, out, geo.P, p, t);
+  decompose_group<T, FI>((int)blockIdx.y, in, out, geo.P, p, t);
 }
 
 // mode: 0 = write filtered tensor to `dst`;
@@ -355,11 +358,7 @@ __global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in
 // Stage updates: k_1: acc = k, U = u + dt/2 k; k_2: acc += 2k, U = u + dt/2 k;
 // k_3: acc += 2k, U = u + dt k; k_4: u = u + dt/6 (acc + k) (classical RK4).
 // The state sums are FP64 additions; the increments are formed in T.
-__device__ __forceinline__ bool nonfinite_bits(double x) {
-  return ((__double_as_longlong(x) >> 52) & 0x7ff) == 0x7ff;
-}
-
-template <class T>
+template <class T, bool FD>
 __global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
                                                      Geo geo, int mode, double* __restrict__ u,
                                                      double* __restrict__ U, double* __restrict__ kacc,
@@ -373,20 +372,21 @@ __global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ 
   const T wk = S<T>::c(stage == 0 ? 1.0 : 2.0);
   const T sixth = S<T>::c(dt / 6.0);
   bool bad = false;
+  using SI_ = Store<T, kIn<T>>;
   auto emit = [&](int f, T kf) {
     const long long o = (long long)f * P + p;
     if (mode == 0) {
-      dst[o] = S<T>::to_double(kf);
+      Store<T, FD>::st(dst, o, kf);
       return;
     }
-    const double kd = S<T>::to_double(kf);
-    bad |= nonfinite_bits(kd);
+    bad |= !finite_s(kf);
     const double uv = u[o];
     if (stage < 3) {
-      kacc[o] = stage == 0 ? kd : S<T>::to_double(S<T>::load(kacc + o) + wk * kf);
-      U[o] = uv + S<T>::to_double(cU * kf);
+      SI_::st(kacc, o, stage == 0 ? kf : SI_::ld(kacc, o) + wk * kf);
+      // stage state: FP64 sum on the FP64 path, double-float on the mixed path
+      SI_::st(U, o, S<T>::c(uv) + cU * kf);
     } else {
-      u[o] = uv + S<T>::to_double(sixth * (S<T>::load(kacc + o) + kf));
+      u[o] = uv + S<T>::to_double(sixth * (SI_::ld(kacc, o) + kf));
     }
   };
   if (mode == 0 || mode <= 4) {
@@ -397,12 +397,14 @@ __global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ 
   } else {
     // unfiltered stage: the group's Cartesian components straight from sp
     const int lo = grp * 7, hi = min(50, lo + 7);  // 8 blocks of fields
-    for (int f = lo; f < hi; ++f) emit(f, ld<T>(sp, P, p, f));
+    for (int f = lo; f < hi; ++f) emit(f, ld<T, kIn<T>>(sp, P, p, f));
   }
   if (bad) atomicOr(flag, 1);
 }
 
-// Spherical -> Cartesian derivatives: D[3][nf][P] -> out[3][nf][P]
+// Spherical -> Cartesian derivatives: D[3][nf][P] -> out[3][nf][P] (FP64
+// arithmetic; D and out in the given storages).  Setup and API paths only.
+template <bool FI, bool FO>
 __global__ void k_cart(const double* __restrict__ D, double* __restrict__ out, int nf, Geo geo) {
   const long long P = geo.P;
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -413,44 +415,62 @@ __global__ void k_cart(const double* __restrict__ D, double* __restrict__ out, i
   const int i = (int)((p / geo.n_r) % geo.N);
   const int jj = (int)(p / ((long long)geo.n_r * geo.N));
   const Jac<double> J = jacobian<double>(geo, k, i, jj);
-  double c3[3];
-  cart3(J, D, P, nf, mu, p, c3);
+  const double dr = Store<double, FI>::ld(D, (long long)mu * P + p);
+  const double dt = Store<double, FI>::ld(D, ((long long)nf + mu) * P + p);
+  const double dp = Store<double, FI>::ld(D, ((long long)2 * nf + mu) * P + p);
 #pragma unroll
-  for (int x = 0; x < 3; ++x) out[((long long)x * nf + mu) * P + p] = c3[x];
+  for (int x = 0; x < 3; ++x)
+    Store<double, FO>::st(out, ((long long)x * nf + mu) * P + p, J.j[x][0] * dr + J.j[x][1] * dt + J.j[x][2] * dp);
 }
 
-// H_a = -Gamma_a(u), pointwise (FP64)
-__global__ void k_gauge(const double* __restrict__ u, double* __restrict__ H, long long Hstride, Geo geo) {
+// H_a = -Gamma_a(u), pointwise (FP64); H in storage FO
+template <bool FO>
+__global__ void k_gauge(const double* __restrict__ u, double* __restrict__ H, Geo geo) {
   const long long P = geo.P;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
   double g[10], Pi[10], Ph[3][10];
+#pragma unroll
   for (int s = 0; s < 10; ++s) {
     g[s] = u[(long long)s * P + p];
     Pi[s] = u[(long long)(10 + s) * P + p];
+#pragma unroll
     for (int a = 0; a < 3; ++a) Ph[a][s] = u[(long long)(20 + 10 * a + s) * P + p];
   }
   Metric<double> M;
   metric_from(g, M);
   double dg4[4][10], Gam[4][10], Gc[4];
   christoffel(M, Pi, Ph, dg4, Gam, Gc);
-  for (int a = 0; a < 4; ++a) H[(long long)a * Hstride + p] = -Gc[a];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) Store<double, FO>::st(H, (long long)a * P + p, -Gc[a]);
+}
+
+// FP64 array -> storage FO (copies of caller arrays into internal buffers)
+template <bool FO>
+__global__ void k_to_store(const double* __restrict__ in, double* __restrict__ out, long long n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) Store<double, FO>::st(out, t, in[t]);
 }
 
 // sum over points of C_iab^2 (30 components) and C_a^2 (4) -> red[0], red[1]
+template <bool FH>
 __global__ void k_constraints(const double* __restrict__ u, const double* __restrict__ dcart /*[3][10][P]*/,
-                              const double* __restrict__ H, long long Hstride, Geo geo, double* red) {
+                              const double* __restrict__ H, Geo geo, double* red) {
   const long long P = geo.P;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double s3 = 0.0, s1 = 0.0;
   if (p < P) {
     double g[10], Pi[10], Ph[3][10];
+#pragma unroll
     for (int s = 0; s < 10; ++s) {
       g[s] = u[(long long)s * P + p];
       Pi[s] = u[(long long)(10 + s) * P + p];
+#pragma unroll
       for (int a = 0; a < 3; ++a) Ph[a][s] = u[(long long)(20 + 10 * a + s) * P + p];
     }
+#pragma unroll
     for (int x = 0; x < 3; ++x)
+#pragma unroll
       for (int s = 0; s < 10; ++s) {
         double c = dcart[((long long)x * 10 + s) * P + p] - Ph[x][s];
         s3 += c * c;
@@ -459,8 +479,9 @@ __global__ void k_constraints(const double* __restrict__ u, const double* __rest
     metric_from(g, M);
     double dg4[4][10], Gam[4][10], Gc[4];
     christoffel(M, Pi, Ph, dg4, Gam, Gc);
+#pragma unroll
     for (int a = 0; a < 4; ++a) {
-      double c = H[(long long)a * Hstride + p] + Gc[a];
+      double c = Store<double, FH>::ld(H, (long long)a * P + p) + Gc[a];
       s1 += c * c;
     }
   }
@@ -484,51 +505,81 @@ __global__ void k_constraints(const double* __restrict__ u, const double* __rest
 // ---------------------------------------------------------------------------
 // Host launchers
 
-int pw_decompose(const cffyn_shell* sh, const double* in, double* out, cudaStream_t st) {
+// in_pairs: the input is a pair-stored internal buffer (else an FP64 array)
+int pw_decompose(const cffyn_shell* sh, const double* in, double* out, bool in_pairs, cudaStream_t st) {
   Geo g = geo_of(sh);
-  if (sh->d.precision == CFFYN_MIXED)
-    k_decompose<ff><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(in, out, g);
+  const dim3 grid(blocks_for(g.P, 128), kGroups);
+  if (sh->d.precision != CFFYN_MIXED)
+    k_decompose<double, false><<<grid, 128, 0, st>>>(in, out, g);
+  else if (in_pairs)
+    k_decompose<ff, true><<<grid, 128, 0, st>>>(in, out, g);
   else
-    k_decompose<double><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(in, out, g);
+    k_decompose<ff, false><<<grid, 128, 0, st>>>(in, out, g);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }
 
+// dst (mode 0) is an FP64 array
 int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mode, double* u, double* U,
                    double* kacc, double dt, int* flag, cudaStream_t st) {
   Geo g = geo_of(sh);
+  const dim3 grid(blocks_for(g.P, 128), kGroups);
   if (sh->d.precision == CFFYN_MIXED)
-    k_reconstruct<ff><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(sp, dst, g, mode, u, U, kacc,
-                                                                             dt, flag);
+    k_reconstruct<ff, false><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, dt, flag);
   else
-    k_reconstruct<double><<<dim3(blocks_for(g.P, 128), kGroups), 128, 0, st>>>(sp, dst, g, mode, u, U,
-                                                                                 kacc, dt, flag);
+    k_reconstruct<double, false><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, dt, flag);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }
 
-int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, cudaStream_t st) {
+// D: internal storage; out_pairs: out is an internal buffer
+int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, bool out_pairs, cudaStream_t st) {
   Geo g = geo_of(sh);
-  k_cart<<<blocks_for(g.P * nf, 256), 256, 0, st>>>(D, out, nf, g);
+  const bool in_pairs = sh->d.precision == CFFYN_MIXED;
+  const unsigned nb = blocks_for(g.P * nf, 256);
+  if (in_pairs && out_pairs)
+    k_cart<true, true><<<nb, 256, 0, st>>>(D, out, nf, g);
+  else if (in_pairs)
+    k_cart<true, false><<<nb, 256, 0, st>>>(D, out, nf, g);
+  else
+    k_cart<false, false><<<nb, 256, 0, st>>>(D, out, nf, g);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }
 
-int pw_gauge(const cffyn_shell* sh, const double* u, double* H, long long Hstride, cudaStream_t st) {
+// H (internal storage) = -Gamma(u)
+int pw_gauge(const cffyn_shell* sh, const double* u, double* H, cudaStream_t st) {
   Geo g = geo_of(sh);
-  k_gauge<<<blocks_for(g.P, 128), 128, 0, st>>>(u, H, Hstride, g);
+  if (sh->d.precision == CFFYN_MIXED)
+    k_gauge<true><<<blocks_for(g.P, 128), 128, 0, st>>>(u, H, g);
+  else
+    k_gauge<false><<<blocks_for(g.P, 128), 128, 0, st>>>(u, H, g);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }
 
-int pw_constraints(const cffyn_shell* sh, const double* u, const double* dcart, const double* H,
-                   long long Hstride, double* red, cudaStream_t st) {
+// FP64 caller array -> internal storage
+int pw_to_internal(const cffyn_shell* sh, const double* in, double* out, long long n, cudaStream_t st) {
+  if (sh->d.precision == CFFYN_MIXED)
+    k_to_store<true><<<blocks_for(n, 256), 256, 0, st>>>(in, out, n);
+  else
+    k_to_store<false><<<blocks_for(n, 256), 256, 0, st>>>(in, out, n);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+int pw_constraints(const cffyn_shell* sh, const double* u, const double* dcart, const double* H, double* red,
+                   cudaStream_t st) {
   Geo g = geo_of(sh);
-  k_constraints<<<blocks_for(g.P, 128), 128, 0, st>>>(u, dcart, H, Hstride, g, red);
+  if (sh->d.precision == CFFYN_MIXED)
+    k_constraints<true><<<blocks_for(g.P, 128), 128, 0, st>>>(u, dcart, H, g, red);
+  else
+    k_constraints<false><<<blocks_for(g.P, 128), 128, 0, st>>>(u, dcart, H, g, red);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;

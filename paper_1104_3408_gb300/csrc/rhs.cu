@@ -23,16 +23,19 @@
 
 namespace cffyn {
 
-template <class T>
-__device__ __forceinline__ T ldT(const double* a, long long P, long long p, int f) {
-  return S<T>::load(a + (long long)f * P + p);
+template <class T, bool F>
+__device__ __forceinline__ T ldA(const double* a, long long P, long long p, int f) {
+  return Store<T, F>::ld(a, (long long)f * P + p);
 }
-template <class T>
-__device__ __forceinline__ void stT(double* a, long long P, long long p, int f, T v) {
-  a[(long long)f * P + p] = S<T>::to_double(v);
+template <class T, bool F>
+__device__ __forceinline__ void stA(double* a, long long P, long long p, int f, T v) {
+  Store<T, F>::st(a, (long long)f * P + p, v);
 }
+// internal buffers are pair-stored in the double-float path
+template <class T> constexpr bool kInt = false;
+template <> constexpr bool kInt<ff> = true;
 
-template <class T>
+template <class T, bool FU, bool FO>
 __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
                                                    const double* __restrict__ H,
                                                    const double* __restrict__ dH,
@@ -45,18 +48,18 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
 
   T g[10];
 #pragma unroll
-  for (int s = 0; s < 10; ++s) g[s] = ldT<T>(u, P, p, s);
+  for (int s = 0; s < 10; ++s) g[s] = ldA<T, FU>(u, P, p, s);
   Metric<T> M;
   metric_from(g, M);
-  stT(src, P, p, 40, M.alpha);
+  stA<T, kInt<T>>(src, P, p, 40, M.alpha);
 #pragma unroll
-  for (int x = 0; x < 3; ++x) stT(src, P, p, 41 + x, M.bu[x]);
-  stT(src, P, p, 44, M.gi[0][0]);
-  stT(src, P, p, 45, M.gi[0][1]);
-  stT(src, P, p, 46, M.gi[0][2]);
-  stT(src, P, p, 47, M.gi[1][1]);
-  stT(src, P, p, 48, M.gi[1][2]);
-  stT(src, P, p, 49, M.gi[2][2]);
+  for (int x = 0; x < 3; ++x) stA<T, kInt<T>>(src, P, p, 41 + x, M.bu[x]);
+  stA<T, kInt<T>>(src, P, p, 44, M.gi[0][0]);
+  stA<T, kInt<T>>(src, P, p, 45, M.gi[0][1]);
+  stA<T, kInt<T>>(src, P, p, 46, M.gi[0][2]);
+  stA<T, kInt<T>>(src, P, p, 47, M.gi[1][1]);
+  stA<T, kInt<T>>(src, P, p, 48, M.gi[1][2]);
+  stA<T, kInt<T>>(src, P, p, 49, M.gi[2][2]);
 
   // d_t g_ab (eq. gdot) and the Christoffel symbols
   T Gam[4][10];
@@ -65,13 +68,13 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
 #pragma unroll
     for (int s = 0; s < 10; ++s) {
 #pragma unroll
-      for (int x = 0; x < 3; ++x) Ph[x][s] = ldT<T>(u, P, p, 20 + 10 * x + s);
+      for (int x = 0; x < 3; ++x) Ph[x][s] = ldA<T, FU>(u, P, p, 20 + 10 * x + s);
       Acc<T> a;
 #pragma unroll
       for (int x = 0; x < 3; ++x) a.fma_(M.bu[x], Ph[x][s]);
-      a.fma_(-M.alpha, ldT<T>(u, P, p, 10 + s));
+      a.fma_(-M.alpha, ldA<T, FU>(u, P, p, 10 + s));
       dtg[s] = a.get();
-      stT(out, P, p, s, dtg[s]);
+      stA<T, FO>(out, P, p, s, dtg[s]);
     }
     auto dg4 = [&](int c, int s) -> T { return c == 0 ? dtg[s] : Ph[c - 1][s]; };
 #pragma unroll
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
   T nC;
   {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) Hd[a] = ldT<T>(H, P, p, a);
+    for (int a = 0; a < 4; ++a) Hd[a] = ldA<T, kInt<T>>(H, P, p, a);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       Acc<T> acc;
@@ -123,8 +126,8 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
 #pragma unroll
       for (int b = a; b < 4; ++b) {
         const int s = SI(a, b);
-        const T dHab = a == 0 ? zero : ldT<T>(dH, P, p, (a - 1) * 4 + b);
-        const T dHba = b == 0 ? zero : ldT<T>(dH, P, p, (b - 1) * 4 + a);
+        const T dHab = a == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (a - 1) * 4 + b);
+        const T dHba = b == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (b - 1) * 4 + a);
         Acc<T> acc;
         acc.fma_(half, dHab + dHba);
 #pragma unroll
@@ -182,10 +185,10 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
     }
   }
 #pragma unroll
-  for (int s = 0; s < 10; ++s) stT(src, P, p, s, SPi[s]);
+  for (int s = 0; s < 10; ++s) stA<T, kInt<T>>(src, P, p, s, SPi[s]);
 }
 
-template <class T>
+template <class T, bool FU>
 __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, double* __restrict__ src,
                                                   Geo geo) {
   const long long P = geo.P;
@@ -194,14 +197,14 @@ __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, 
   const T zero = S<T>::c(0.0), half = S<T>::c(0.5);
   T g[10], Pi[10], Ph[3][10];
 #pragma unroll
-  for (int s = 0; s < 10; ++s) g[s] = ldT<T>(u, P, p, s);
+  for (int s = 0; s < 10; ++s) g[s] = ldA<T, FU>(u, P, p, s);
   Metric<T> M;
   metric_from(g, M);
 #pragma unroll
   for (int s = 0; s < 10; ++s) {
-    Pi[s] = ldT<T>(u, P, p, 10 + s);
+    Pi[s] = ldA<T, FU>(u, P, p, 10 + s);
 #pragma unroll
-    for (int x = 0; x < 3; ++x) Ph[x][s] = ldT<T>(u, P, p, 20 + 10 * x + s);
+    for (int x = 0; x < 3; ++x) Ph[x][s] = ldA<T, FU>(u, P, p, 20 + 10 * x + s);
   }
   const T twoal = M.alpha + M.alpha;
   T Q[10];  // Q1 - Q2
@@ -295,12 +298,12 @@ __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, 
 #pragma unroll
   for (int s = 0; s < 10; ++s) {
     Acc<T> acc;
-    acc.add(ldT<T>(src, P, p, s));
+    acc.add(ldA<T, kInt<T>>(src, P, p, s));
     acc.fma_(twoal, Q[s]);
     acc.fma_(-(hal * nnPi), Pi[s]);
 #pragma unroll
     for (int x = 0; x < 3; ++x) acc.fma_(M.bu[x] - M.alpha * Vj[x], Ph[x][s]);
-    stT(src, P, p, s, acc.get());
+    stA<T, kInt<T>>(src, P, p, s, acc.get());
   }
   // algebraic terms of eq. Phidot
 #pragma unroll
@@ -340,13 +343,13 @@ __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, 
 #pragma unroll
       for (int z = 0; z < 3; ++z) acc.fma_(Mk[z], Ph[z][s]);
       acc.fma_(-M.alpha, Ph[x][s]);
-      stT(src, P, p, 10 + 10 * x + s, acc.get());
+      stA<T, kInt<T>>(src, P, p, 10 + 10 * x + s, acc.get());
     }
   }
   (void)zero;
 }
 
-template <class T>
+template <class T, bool FO>
 __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, const double* __restrict__ src,
                                                 double* __restrict__ out, Geo geo) {
   const long long P = geo.P;
@@ -358,16 +361,16 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
   const int nv = geo.nv;
   const T half = S<T>::c(0.5);
   const Jac<T> J = jacobian<T>(geo, k, i, jj);
-  const T alpha = ldT<T>(src, P, p, 40);
+  const T alpha = ldA<T, kInt<T>>(src, P, p, 40);
   T bu[3], gi[3][3];
 #pragma unroll
-  for (int x = 0; x < 3; ++x) bu[x] = ldT<T>(src, P, p, 41 + x);
-  gi[0][0] = ldT<T>(src, P, p, 44);
-  gi[0][1] = gi[1][0] = ldT<T>(src, P, p, 45);
-  gi[0][2] = gi[2][0] = ldT<T>(src, P, p, 46);
-  gi[1][1] = ldT<T>(src, P, p, 47);
-  gi[1][2] = gi[2][1] = ldT<T>(src, P, p, 48);
-  gi[2][2] = ldT<T>(src, P, p, 49);
+  for (int x = 0; x < 3; ++x) bu[x] = ldA<T, kInt<T>>(src, P, p, 41 + x);
+  gi[0][0] = ldA<T, kInt<T>>(src, P, p, 44);
+  gi[0][1] = gi[1][0] = ldA<T, kInt<T>>(src, P, p, 45);
+  gi[0][2] = gi[2][0] = ldA<T, kInt<T>>(src, P, p, 46);
+  gi[1][1] = ldA<T, kInt<T>>(src, P, p, 47);
+  gi[1][2] = gi[2][1] = ldA<T, kInt<T>>(src, P, p, 48);
+  gi[2][2] = ldA<T, kInt<T>>(src, P, p, 49);
   // beta^k d_k = sum_m b_m D_m; alpha gamma^ik d_k = sum_m G_im D_m; J_xm for d_x
   T b[3], G[3][3];
 #pragma unroll
@@ -417,14 +420,14 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const long long base = (long long)m * nv * P + p;
-      const T dg = S<T>::load(D + base + (long long)s * P);
-      const T dpi = S<T>::load(D + base + (long long)(10 + s) * P);
+      const T dg = Store<T, kInt<T>>::ld(D, base + (long long)s * P);
+      const T dpi = Store<T, kInt<T>>::ld(D, base + (long long)(10 + s) * P);
       Dd[m] = dg - dpi;
 #pragma unroll
-      for (int x = 0; x < 3; ++x) DPh[x][m] = S<T>::load(D + base + (long long)(20 + 10 * x + s) * P);
+      for (int x = 0; x < 3; ++x) DPh[x][m] = Store<T, kInt<T>>::ld(D, base + (long long)(20 + 10 * x + s) * P);
     }
     Acc<T> aPi;
-    aPi.add(ldT<T>(src, P, p, s));
+    aPi.add(ldA<T, kInt<T>>(src, P, p, s));
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       aPi.fma_(-b[m], Dd[m]);
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       Acc<T> a;
-      a.add(ldT<T>(src, P, p, 10 + 10 * x + s));
+      a.add(ldA<T, kInt<T>>(src, P, p, 10 + 10 * x + s));
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         a.fma_(b[m], DPh[x][m]);
@@ -445,7 +448,7 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
       rPh[x] = a.get();
     }
     if (outer) {
-      const T rg = ldT<T>(out, P, p, s);
+      const T rg = ldA<T, FO>(out, P, p, s);
       Acc<T> sd;
 #pragma unroll
       for (int x = 0; x < 3; ++x) sd.fma_(su[x], rPh[x]);
@@ -455,38 +458,48 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
 #pragma unroll
       for (int x = 0; x < 3; ++x) rPh[x] = sl[x] * w2;
     }
-    stT(out, P, p, 10 + s, rPi);
+    stA<T, FO>(out, P, p, 10 + s, rPi);
 #pragma unroll
-    for (int x = 0; x < 3; ++x) stT(out, P, p, 20 + 10 * x + s, rPh[x]);
+    for (int x = 0; x < 3; ++x) stA<T, FO>(out, P, p, 20 + 10 * x + s, rPh[x]);
   }
 }
 
 // stage = 0: all three kernels; 1: sources with Christoffels; 2: quadratic
-// sources; 3: principal parts + boundary.
+// sources; 3: principal parts + boundary.  u_pairs: the state is a pair-stored
+// internal buffer (the stage states of the mixed path); out_pairs: the output
+// is the internal rhs buffer (else an FP64 caller array).
 int pw_rhs_part(const cffyn_shell* sh, const double* u, const double* D, double* out, int stage,
-                cudaStream_t st) {
+                bool u_pairs, bool out_pairs, cudaStream_t st) {
   Geo g = geo_of(sh);
   const unsigned nb = blocks_for(g.P, 128);
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   if (stage == 0 || stage == 1) {
-    if (mixed)
-      k_rhs_gamma<ff><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+    if (!mixed)
+      k_rhs_gamma<double, false, false><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+    else if (u_pairs && out_pairs)
+      k_rhs_gamma<ff, true, true><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+    else if (out_pairs)
+      k_rhs_gamma<ff, false, true><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
     else
-      k_rhs_gamma<double><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+      k_rhs_gamma<ff, false, false><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
     count_launch();
   }
   if (stage == 0 || stage == 2) {
-    if (mixed)
-      k_rhs_quad<ff><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+    if (!mixed)
+      k_rhs_quad<double, false><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+    else if (u_pairs)
+      k_rhs_quad<ff, true><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
     else
-      k_rhs_quad<double><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+      k_rhs_quad<ff, false><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
     count_launch();
   }
   if (stage == 0 || stage == 3) {
-    if (mixed)
-      k_rhs_pp<ff><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
+    if (!mixed)
+      k_rhs_pp<double, false><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
+    else if (out_pairs)
+      k_rhs_pp<ff, true><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
     else
-      k_rhs_pp<double><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
+      k_rhs_pp<ff, false><<<nb, 128, 0, st>>>(D, sh->Rsrc, out, g);
     count_launch();
   }
   CF_CUDA(cudaGetLastError());
@@ -494,7 +507,7 @@ int pw_rhs_part(const cffyn_shell* sh, const double* u, const double* D, double*
 }
 
 int pw_rhs(const cffyn_shell* sh, const double* u, const double* D, double* out, cudaStream_t st) {
-  return pw_rhs_part(sh, u, D, out, 0, st);
+  return pw_rhs_part(sh, u, D, out, 0, false, false, st);
 }
 
 }  // namespace cffyn

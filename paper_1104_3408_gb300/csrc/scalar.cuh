@@ -197,6 +197,14 @@ template <> struct Acc<ff> {
   __device__ __forceinline__ ff get() const { return two_sum(s, c); }
 };
 
+// Finiteness from the bit patterns (no FP64 instruction).
+__device__ __forceinline__ bool finite_s(double x) {
+  return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ bool finite_s(ff x) {
+  return ((__float_as_uint(x.hi) >> 23) & 0xff) != 0xff;
+}
+
 // Uniform helpers so that templated code reads the same for both types.
 template <class T> struct S;
 template <> struct S<double> {
@@ -208,6 +216,39 @@ template <> struct S<ff> {
   static __device__ __forceinline__ ff c(double v) { return ff_from_double(v); }
   static __device__ __forceinline__ ff load(const double* p) { return ff_from_double(__ldg(p)); }
   static __device__ __forceinline__ double to_double(ff v) { return ff_to_double(v); }
+};
+
+// Storage of an array: FP64 words (FF = false) or double-float pairs stored
+// as float2 (FF = true); both are 8 bytes per value.  Internal buffers of the
+// mixed path use the pair form, so that its pointwise kernels load and store
+// without any conversion.
+template <class T, bool FF> struct Store;
+template <> struct Store<double, false> {
+  static __device__ __forceinline__ double ld(const double* b, long long i) { return b[i]; }
+  static __device__ __forceinline__ void st(double* b, long long i, double v) { b[i] = v; }
+};
+template <> struct Store<ff, false> {
+  static __device__ __forceinline__ ff ld(const double* b, long long i) { return ff_from_double(__ldg(b + i)); }
+  static __device__ __forceinline__ void st(double* b, long long i, ff v) { b[i] = ff_to_double(v); }
+};
+template <> struct Store<ff, true> {
+  static __device__ __forceinline__ ff ld(const double* b, long long i) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(b) + i);
+    return ff{v.x, v.y};
+  }
+  static __device__ __forceinline__ void st(double* b, long long i, ff v) {
+    reinterpret_cast<float2*>(b)[i] = make_float2(v.hi, v.lo);
+  }
+};
+template <> struct Store<double, true> {  // FP64 access to a pair-stored buffer (setup paths)
+  static __device__ __forceinline__ double ld(const double* b, long long i) {
+    const float2 v = reinterpret_cast<const float2*>(b)[i];
+    return ff_to_double(ff{v.x, v.y});
+  }
+  static __device__ __forceinline__ void st(double* b, long long i, double v) {
+    const ff f = ff_from_double(v);
+    reinterpret_cast<float2*>(b)[i] = make_float2(f.hi, f.lo);
+  }
 };
 
 }  // namespace cffyn
