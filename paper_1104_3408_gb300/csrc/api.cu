@@ -33,6 +33,7 @@ int op_dft_fwd(const cffyn_shell*, const double*, double*, int, cudaStream_t);
 int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t);
 int op_project(const cffyn_shell*, const double*, double*, const int*, int, const int* const[3],
                const int[3], cudaStream_t);
+int op_prepare(const cffyn_shell*, const double*, bool, int, long long, int, cudaStream_t);
 // setup.cu
 int build_operators(cffyn_shell*);
 void free_sliced(SlicedOp&);
@@ -77,6 +78,7 @@ int check_ptr(const void* p, const char* what) {
 int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, bool in_pairs, cudaStream_t st) {
   const size_t P = sh->P;
   int rc;
+  if ((rc = op_prepare(sh, u, in_pairs, nf, (long long)P, 0, st))) return rc;
   if ((rc = op_deriv_r(sh, u, D, nf, in_pairs, st))) return rc;
   if ((rc = op_deriv_theta(sh, u, D + (size_t)nf * P, nf, in_pairs, st))) return rc;
   if ((rc = op_deriv_phi(sh, u, D + (size_t)2 * nf * P, nf, in_pairs, st))) return rc;
@@ -90,9 +92,13 @@ int filter_spin_slots(cffyn_shell* sh, double* spin, cudaStream_t st) {
   int rc;
   double* C = sh->D;
   double* C2 = sh->D + nvP;
+  const long long lc = (long long)sh->R * sh->N * sh->n_r;  // coefficient values per function
+  if ((rc = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, 1, st))) return rc;
   if ((rc = op_dft_fwd(sh, spin, C, sh->nv, st))) return rc;
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  if ((rc = op_prepare(sh, C, true, sh->nv, lc, 1, st))) return rc;
   if ((rc = op_project(sh, C, C2, slots_r0(sh), kNR0, cl, kNC, st))) return rc;
+  if ((rc = op_prepare(sh, C2, true, sh->nv, lc, 1, st))) return rc;
   if ((rc = op_dft_inv(sh, C2, spin, sh->nv, st))) return rc;
   return CFFYN_OK;
 }
@@ -103,13 +109,14 @@ void free_shell(cffyn_shell* sh) {
   double** ptrs[] = {&sh->r,     &sh->sth,    &sh->cth,    &sh->sph, &sh->cph,  &sh->Dr,   &sh->Dth2,
                      &sh->Dph,   &sh->Fan,    &sh->Fsy,    &sh->Fraw, &sh->Fproj0, &sh->FprojC,
                      &sh->H,     &sh->dH,     &sh->U,      &sh->kacc, &sh->D,    &sh->S,
-                     &sh->Rsrc,  &sh->red};
+                     &sh->Rsrc,  &sh->red,    &sh->rec};
   for (double** p : ptrs)
     if (*p) cudaFree(*p);
   SlicedOp* so[] = {&sh->sDr, &sh->sDth2, &sh->sDph, &sh->sFan, &sh->sFsy, &sh->sF0,
                     &sh->sFC[0], &sh->sFC[1], &sh->sFC[2]};
   for (SlicedOp* s : so) free_sliced(*s);
   if (sh->slots) cudaFree(sh->slots);
+  if (sh->exps) cudaFree(sh->exps);
   if (sh->cap_stream) cudaStreamDestroy(sh->cap_stream);
   if (sh->flag_host) cudaFreeHost(sh->flag_host);
   if (sh->flag) cudaFree(sh->flag);
@@ -206,6 +213,10 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
       (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->Rsrc, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, 12 * sh->P)) ||
       (rc = alloc(&sh->red, 2)))
     return fail(rc);
+  if (d.precision == CFFYN_MIXED) {
+    if ((rc = alloc(&sh->rec, 2 * nvP))) return fail(rc);  // 16-byte records
+    if (cudaMalloc(&sh->exps, 64 * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
+  }
   {
     int host[33];
     for (int i = 0; i < 16; ++i) host[i] = i;
@@ -342,12 +353,17 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
     return mark(phase);
   };
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  const long long lc = (long long)sh->R * sh->N * sh->n_r;
   if ((rc = mark(-1))) return rc;
   for (int s = 0; s < 4; ++s) {
     const double* X = s == 0 ? u : sh->U;
     double* spin = sh->D + 2 * nvP;  // derivatives are dead after the rhs
     const bool xp = s > 0;  // stage states U are pair-stored on the mixed path
-    if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
+    if ((rc = run(0, [&] {
+           int r = op_prepare(sh, X, xp, sh->nv, (long long)sh->P, 0, st);
+           return r ? r : op_deriv_r(sh, X, sh->D, sh->nv, xp, st);
+         })))
+      return rc;
     if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) return rc;
     if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) return rc;
     if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
@@ -355,10 +371,21 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
     if ((rc = run(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
     if (per_sub) {
       if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
-      if ((rc = run(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return rc;
-      if ((rc = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+      if ((rc = run(7, [&] {
+             int r = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, 1, st);
+             return r ? r : op_dft_fwd(sh, spin, sh->D, sh->nv, st);
+           })))
         return rc;
-      if ((rc = run(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) return rc;
+      if ((rc = run(8, [&] {
+             int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
+             return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
+           })))
+        return rc;
+      if ((rc = run(9, [&] {
+             int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
+             return r ? r : op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st);
+           })))
+        return rc;
       if ((rc = run(10, [&] {
              return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
            })))
@@ -372,10 +399,21 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
   }
   if (!per_sub) {
     if ((rc = run(6, [&] { return pw_decompose(sh, u, sh->S, false, st); }))) return rc;
-    if ((rc = run(7, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); }))) return rc;
-    if ((rc = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+    if ((rc = run(7, [&] {
+           int r = op_prepare(sh, sh->S, true, sh->nv, (long long)sh->P, 1, st);
+           return r ? r : op_dft_fwd(sh, sh->S, sh->D, sh->nv, st);
+         })))
       return rc;
-    if ((rc = run(9, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); }))) return rc;
+    if ((rc = run(8, [&] {
+           int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
+           return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
+         })))
+      return rc;
+    if ((rc = run(9, [&] {
+           int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
+           return r ? r : op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st);
+         })))
+      return rc;
     if ((rc = run(10, [&] {
            return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
          })))
@@ -557,12 +595,17 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     return CFFYN_OK;
   };
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  const long long lc = (long long)sh->R * sh->N * sh->n_r;
   CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
   for (int s = 0; s < 4 && !rc; ++s) {
     const double* X = s == 0 ? u : sh->U;
     double* spin = sh->D + 2 * nvP;
     const bool xp = s > 0;
-    if ((rc = phase(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) break;
+    if ((rc = phase(0, [&] {
+           int r = op_prepare(sh, X, xp, sh->nv, (long long)sh->P, 0, st);
+           return r ? r : op_deriv_r(sh, X, sh->D, sh->nv, xp, st);
+         })))
+      break;
     if ((rc = phase(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) break;
     if ((rc = phase(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) break;
     if ((rc = phase(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) break;
@@ -570,12 +613,21 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     if ((rc = phase(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) break;
     if (per_sub) {
       if ((rc = phase(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) break;
-      if ((rc = phase(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) break;
-      if ((rc = phase(8, [&] {
-             return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
+      if ((rc = phase(7, [&] {
+             int r = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, 1, st);
+             return r ? r : op_dft_fwd(sh, spin, sh->D, sh->nv, st);
            })))
         break;
-      if ((rc = phase(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); }))) break;
+      if ((rc = phase(8, [&] {
+             int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
+             return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
+           })))
+        break;
+      if ((rc = phase(9, [&] {
+             int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
+             return r ? r : op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st);
+           })))
+        break;
       if ((rc = phase(10, [&] {
              return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
            })))
@@ -589,10 +641,21 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
   }
   if (!rc && !per_sub) {
     rc = phase(6, [&] { return pw_decompose(sh, u, sh->S, false, st); });
-    if (!rc) rc = phase(7, [&] { return op_dft_fwd(sh, sh->S, sh->D, sh->nv, st); });
     if (!rc)
-      rc = phase(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); });
-    if (!rc) rc = phase(9, [&] { return op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st); });
+      rc = phase(7, [&] {
+        int r = op_prepare(sh, sh->S, true, sh->nv, (long long)sh->P, 1, st);
+        return r ? r : op_dft_fwd(sh, sh->S, sh->D, sh->nv, st);
+      });
+    if (!rc)
+      rc = phase(8, [&] {
+        int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
+        return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
+      });
+    if (!rc)
+      rc = phase(9, [&] {
+        int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
+        return r ? r : op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st);
+      });
     if (!rc)
       rc = phase(10, [&] {
         return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);

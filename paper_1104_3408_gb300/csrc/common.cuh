@@ -100,6 +100,8 @@ struct cffyn_shell {
   double* D = nullptr;     // spherical derivatives [3][nv][P] (also DFT coefficients)
   double* S = nullptr;     // rhs / spin functions [nv][P]
   double* Rsrc = nullptr;  // right-hand-side source terms [nv][P]
+  double* rec = nullptr;   // split-precision digit records, 16 bytes per value [nv][P]
+  int* exps = nullptr;     // per-field exponents of the sliced array (64 entries)
   double* red = nullptr;   // device reduction words (2 doubles)
   int* flag = nullptr;     // device non-finite flag
   int* flag_host = nullptr;  // pinned host copy of the flag

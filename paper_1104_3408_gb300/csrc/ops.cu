@@ -20,6 +20,7 @@
 //          about 6 * 2^-48 of |W| |x| K).  The result is rebuilt as an FP64
 //          number with integer operations only (this part's FP64 and
 //          conversion pipes are narrow).
+#include <algorithm>
 #include <cstdio>
 
 #include "common.cuh"
@@ -34,6 +35,7 @@ struct ColDesc {
   long long in0, in1, out0, out1;  // base offsets of the two row segments
   int sgn1;                        // second input segment: 0 as is, 1 negated, 2 zero
   int valid;
+  int fld;                         // field (or function) whose exponent the column uses
 };
 
 struct OpGeom {
@@ -71,6 +73,7 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
   if (!d.valid) c = 0;
   switch (a.kind) {
     case OP_R: {
+      d.fld = (int)(c / ((long long)a.J * a.N));
       d.in0 = c * a.n_r;
       d.out0 = d.in0;
       d.in1 = d.out1 = 0;
@@ -78,6 +81,7 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
     }
     case OP_ROWS: {
       long long b = c / a.Q, q = c - b * a.Q;
+      d.fld = (int)b;
       d.in0 = b * a.in_bs + q;
       d.out0 = b * a.out_bs + q;
       d.in1 = d.out1 = 0;
@@ -89,6 +93,7 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
       int half = a.J / 2;
       long long mu = pb / half;
       int jp = (int)(pb - mu * half);
+      d.fld = (int)mu;
       d.in0 = ((mu * a.J + jp) * a.N) * a.n_r + kr;
       d.in1 = ((mu * a.J + jp + half) * a.N) * a.n_r + kr;
       d.out0 = d.in0;
@@ -104,6 +109,7 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
       int rem = (int)(c - fi * per);
       int part = rem / a.n_r, kr = rem - part * a.n_r;
       int f = a.slots[fi < a.nslots ? fi : 0];
+      d.fld = f;
       int row = part == 0 ? a.m : a.L + a.m;
       d.in0 = (((long long)f * a.R + row) * a.N) * a.n_r + kr;
       d.out0 = d.in0;
@@ -119,6 +125,7 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
       int rem = (int)(c - pi * per);
       int part = rem / a.n_r, kr = rem - part * a.n_r;
       int fre = a.slots[pi < a.nslots ? pi : 0], fim = fre + 1;
+      d.fld = fre;
       int ra = a.m, rb = a.L + a.m;
       auto base = [&](int f, int row) {
         return (((long long)f * a.R + row) * a.N) * a.n_r + kr;
@@ -243,7 +250,6 @@ constexpr int OZ_QT = 32;        // columns per CTA (4 n-tiles of 8)
 constexpr int OZ_NT = OZ_QT / 8;
 constexpr int OZ_MAXK = 192;
 constexpr int OZ_KCHUNK = 6;     // k-steps (of 16) per exact partial sum
-constexpr int OZ_ITEMS = 16;     // (k pair, column) items per thread in the prologue
 
 __device__ __forceinline__ int exp_field(double x) {
   return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
@@ -384,9 +390,65 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint4& a, unsigned in
       : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
 }
 
-// CTA: one warp per m-tile of W (mtiles warps), OZ_QT columns.
-template <bool FI, bool FO>
-__global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
+// ---------------------------------------------------------------------------
+// Slicing pass: per-field exponents and 16-byte digit records.
+//
+// exps[f] = max over the field of (frexp exponent + 1022), 0 for an all-zero
+// field.  With pairing, slots f >= kPairedFrom form (re, im) pairs (f, f^1)
+// that share one exponent (the projection of a complex function gathers
+// both).  A record holds the six balanced digits (slice 0 first) of the
+// 47-bit fixed point round(x 2^(47-E)), E = exps - 1022, as BF16 halves.
+
+constexpr int kPairedFrom = 16;
+
+template <bool FI>
+__global__ void k_field_exp(const long long* __restrict__ in, long long len, int* __restrict__ exps) {
+  const int f = blockIdx.y;
+  const long long* x = in + (long long)f * len;
+  int m = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
+       e += (long long)gridDim.x * blockDim.x)
+    m = max(m, raw_exp<FI>(__ldg(x + e)));
+  m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(exps + f, m);
+}
+
+template <bool FI>
+__global__ void k_slice(const long long* __restrict__ in, long long len, long long n,
+                        const int* __restrict__ exps, int pairing, uint4* __restrict__ rec) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int f = (int)(e / len);
+  int ex = exps[f];
+  if (pairing && f >= kPairedFrom) ex = max(ex, exps[f ^ 1]);
+  unsigned int d[kSlices];
+  digits_bf16(raw_fixed47<FI>(__ldg(in + e), ex - 1022), d);
+  rec[e] = make_uint4(d[0] | (d[1] << 16), d[2] | (d[3] << 16), d[4] | (d[5] << 16), 0u);
+}
+
+// Digit record of one column element (zero record outside K or for the empty
+// second segment; negation flips the sign bit of every BF16 digit).
+__device__ __forceinline__ uint4 load_rec(const OpArgs& a, const uint4* __restrict__ rec, const ColDesc& d,
+                                          int k) {
+  if (!d.valid || k >= a.g.K) return make_uint4(0u, 0u, 0u, 0u);
+  if (k < a.g.K0) return __ldg(rec + d.in0 + (long long)k * a.g.in_rs);
+  if (d.sgn1 == 2) return make_uint4(0u, 0u, 0u, 0u);
+  const int kk = a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0);
+  uint4 r = __ldg(rec + d.in1 + (long long)kk * a.g.in_rs);
+  if (d.sgn1) {
+    r.x ^= 0x80008000u;
+    r.y ^= 0x80008000u;
+    r.z ^= 0x80008000u;
+  }
+  return r;
+}
+
+// CTA: one warp per m-tile of W (mtiles warps), OZ_QT columns.  The input is
+// given as digit records (see k_slice); the prologue only copies them into
+// the slice-major shared-memory tile.
+template <bool FO>
+__global__ void __launch_bounds__(384) k_op_rec(OpArgs a, SlicedOp W, const uint4* __restrict__ rec,
+                                              const int* __restrict__ exps, int pairing) {
   extern __shared__ unsigned short smoz[];
   if (a.batched_m) {
     a.m = blockIdx.y;
@@ -401,10 +463,7 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
   __shared__ int colE[OZ_QT];
   const long long c0 = (long long)blockIdx.x * OZ_QT;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  if (tid < OZ_QT) {
-    cols[tid] = make_col(a, c0 + tid);
-    colE[tid] = -100000;
-  }
+  if (tid < OZ_QT) cols[tid] = make_col(a, c0 + tid);
   __syncthreads();
   const bool kfast = a.kind == OP_R;
   const int Kp = ksteps * 16;
@@ -412,36 +471,26 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
   const int KPW = KP / 2;                // row pitch in 32-bit words
   unsigned int* Bw = reinterpret_cast<unsigned int*>(Bs);
   const int nitems = KH * OZ_QT;
-  // one pass over global memory: values stay in registers between the column
-  // exponent reduction and the digit extraction
-  long long v0[OZ_ITEMS], v1[OZ_ITEMS];
-#pragma unroll
-  for (int it = 0; it < OZ_ITEMS; ++it) {
-    const int e = tid + it * nthr;
-    v0[it] = v1[it] = 0;
-    if (e < nitems) {
-      int kp, c;
-      if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
-      v0[it] = load_raw<FI>(a, cols[c], 2 * kp);
-      v1[it] = load_raw<FI>(a, cols[c], 2 * kp + 1);
-      const int ex = max(raw_exp<FI>(v0[it]), raw_exp<FI>(v1[it]));  // 0 for zero
-      if (ex) atomicMax(&colE[c], ex - 1022);
-    }
+  if (tid < OZ_QT) {
+    const int f = cols[tid].fld;
+    int e = exps[f];
+    if (pairing && f >= kPairedFrom) e = max(e, exps[f ^ 1]);
+    colE[tid] = e - 1022;
   }
-  __syncthreads();
-#pragma unroll
-  for (int it = 0; it < OZ_ITEMS; ++it) {
-    const int e = tid + it * nthr;
-    if (e < nitems) {
-      int kp, c;
-      if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
-      const int E = colE[c];
-      unsigned int d0[kSlices], d1[kSlices];
-      digits_bf16(raw_fixed47<FI>(v0[it], E), d0);
-      digits_bf16(raw_fixed47<FI>(v1[it], E), d1);
-#pragma unroll
-      for (int s2 = 0; s2 < kSlices; ++s2) Bw[((size_t)s2 * OZ_QT + c) * KPW + kp] = d0[s2] | (d1[s2] << 16);
-    }
+  // copy the digit records of the tile: two k values of one column per item
+  for (int e = tid; e < nitems; e += nthr) {
+    int kp, c;
+    if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
+    const uint4 r0 = load_rec(a, rec, cols[c], 2 * kp);
+    const uint4 r1 = load_rec(a, rec, cols[c], 2 * kp + 1);
+    unsigned int* dst = Bw + (size_t)c * KPW + kp;
+    const size_t sstride = (size_t)OZ_QT * KPW;
+    dst[0] = __byte_perm(r0.x, r1.x, 0x5410);
+    dst[sstride] = __byte_perm(r0.x, r1.x, 0x7632);
+    dst[2 * sstride] = __byte_perm(r0.y, r1.y, 0x5410);
+    dst[3 * sstride] = __byte_perm(r0.y, r1.y, 0x7632);
+    dst[4 * sstride] = __byte_perm(r0.z, r1.z, 0x5410);
+    dst[5 * sstride] = __byte_perm(r0.z, r1.z, 0x7632);
   }
   __syncthreads();
 
@@ -455,37 +504,48 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) T[n][q] = 0;
 
-  for (int d = 0; d < kSlices; ++d) {
-    for (int kc = 0; kc < ksteps; kc += OZ_KCHUNK) {
-      const int kend = min(ksteps, kc + OZ_KCHUNK);
-      float acc[OZ_NT][4];
+  // k-step outer: the six operator digit fragments A_i(ks) are loaded once per
+  // k-step, each data slice B_j(ks) once per k-step, and every pair (i, j)
+  // accumulates into the digit-sum accumulator d = i + j (exact FP32 integers
+  // per K chunk, folded into T with weight 256^(5-d)).
+  const unsigned short* Bl = Bs + (size_t)(((lane >> 4) * 8) + (lane & 7)) * KP + ((lane >> 3) & 1) * 8;
+  const uint4* Am = W.frag + ((size_t)mt * ksteps) * 32 + lane;
+  const size_t aslice = (size_t)W.mtiles * ksteps * 32;
+  for (int kc = 0; kc < ksteps; kc += OZ_KCHUNK) {
+    const int kend = min(ksteps, kc + OZ_KCHUNK);
+    float acc[kSlices][OZ_NT][4];
+#pragma unroll
+    for (int d = 0; d < kSlices; ++d)
 #pragma unroll
       for (int n = 0; n < OZ_NT; ++n)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[n][q] = 0.0f;
-      for (int i = 0; i <= d; ++i) {
-        const int j = d - i;
-        const uint4* Af = W.frag + ((size_t)(i * W.mtiles + mt) * ksteps) * 32 + lane;
-        // ldmatrix row addresses: tile q = lane/8 is (n-tile q/2, k half q%2)
-        const unsigned short* Bj = Bs + (size_t)j * OZ_QT * KP +
-                                   (size_t)(((lane >> 4) * 8) + (lane & 7)) * KP + ((lane >> 3) & 1) * 8;
-        for (int ks = kc; ks < kend; ++ks) {
-          const uint4 af = __ldg(Af + (size_t)ks * 32);
+        for (int q = 0; q < 4; ++q) acc[d][n][q] = 0.0f;
+    for (int ks = kc; ks < kend; ++ks) {
+      uint4 af[kSlices];
 #pragma unroll
-          for (int n = 0; n < OZ_NT; n += 2) {
-            unsigned int b00, b01, b10, b11;
-            ldmatrix_x4(b00, b01, b10, b11, Bj + (size_t)n * 8 * KP + ks * 16);
-            mma_bf16(acc[n], af, b00, b01);
-            mma_bf16(acc[n + 1], af, b10, b11);
+      for (int i = 0; i < kSlices; ++i) af[i] = __ldg(Am + i * aslice + (size_t)ks * 32);
+#pragma unroll
+      for (int j = 0; j < kSlices; ++j) {
+        const unsigned short* Bj = Bl + (size_t)j * OZ_QT * KP + ks * 16;
+#pragma unroll
+        for (int n = 0; n < OZ_NT; n += 2) {
+          unsigned int b00, b01, b10, b11;
+          ldmatrix_x4(b00, b01, b10, b11, Bj + (size_t)n * 8 * KP);
+#pragma unroll
+          for (int i = 0; i < kSlices - j; ++i) {
+            mma_bf16(acc[i + j][n], af[i], b00, b01);
+            mma_bf16(acc[i + j][n + 1], af[i], b10, b11);
           }
         }
       }
-      const int shift = 8 * (kSlices - 1 - d);
+    }
+#pragma unroll
+    for (int d = 0; d < kSlices; ++d)
 #pragma unroll
       for (int n = 0; n < OZ_NT; ++n)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) T[n][q] += ((long long)f32_int_exact(acc[n][q])) << shift;
-    }
+        for (int q = 0; q < 4; ++q)
+          T[n][q] += ((long long)__float2int_rz(acc[d][n][q])) << (8 * (kSlices - 1 - d));
   }
   // epilogue: rows mt*16 + g (+8), columns n*8 + 2tg (+1)
   const int rowA = mt * 16 + g, rowB = rowA + 8;
@@ -509,10 +569,10 @@ __global__ void __launch_bounds__(384) k_op_ozaki(OpArgs a, SlicedOp W) {
 // ---------------------------------------------------------------------------
 // Host side
 
-// in_pairs / out_pairs: the mixed path's internal pair storage (ignored on
-// the FP64 path, whose buffers are all FP64)
+// Mixed path: the operator input must have been sliced by op_prepare into
+// sh->rec / sh->exps (pairing as given there); outputs are pair-stored.
 static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const SlicedOp* Ws,
-                  dim3 extra, cudaStream_t st, bool in_pairs = true, bool out_pairs = true) {
+                  dim3 extra, cudaStream_t st, int pairing = 0) {
   if (a.g.ncols <= 0) return CFFYN_OK;
   if (sh->d.precision == CFFYN_FP64 || Ws == nullptr) {
     unsigned gx = (unsigned)((a.g.ncols + F64_QT - 1) / F64_QT);
@@ -524,19 +584,9 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
     unsigned gx = (unsigned)((a.g.ncols + OZ_QT - 1) / OZ_QT);
     int KP = Ws->ksteps * 16 + 8;
     size_t smem = (size_t)kSlices * OZ_QT * KP * sizeof(unsigned short);
-    // one warp per m-tile, and enough threads that the prologue's items fit
-    int KH = Ws->ksteps * 8;
-    int warps = max(Ws->mtiles, (KH + OZ_ITEMS - 1) / OZ_ITEMS);
-    int threads = warps * 32;
-    const dim3 grid(gx, extra.y);
-    if (in_pairs && out_pairs)
-      k_op_ozaki<true, true><<<grid, threads, smem, st>>>(a, *Ws);
-    else if (out_pairs)
-      k_op_ozaki<false, true><<<grid, threads, smem, st>>>(a, *Ws);
-    else if (in_pairs)
-      k_op_ozaki<true, false><<<grid, threads, smem, st>>>(a, *Ws);
-    else
-      k_op_ozaki<false, false><<<grid, threads, smem, st>>>(a, *Ws);
+    int threads = Ws->mtiles * 32;  // one warp per m-tile
+    k_op_rec<true><<<dim3(gx, extra.y), threads, smem, st>>>(a, *Ws, reinterpret_cast<const uint4*>(sh->rec),
+                                                           sh->exps, pairing);
     count_launch();
   }
   CF_CUDA(cudaGetLastError());
@@ -545,10 +595,33 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
 
 int set_op_smem_limits() {
   CF_CUDA(cudaFuncSetAttribute(k_op_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CF_CUDA(cudaFuncSetAttribute(k_op_ozaki<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CF_CUDA(cudaFuncSetAttribute(k_op_rec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  return CFFYN_OK;
+}
+
+// Slicing pass of the mixed path (no-op on the FP64 path): per-field
+// exponents of nf fields of len values each, then one digit record per value
+// into sh->rec.  in_pairs: the input is pair-stored.
+int op_prepare(const cffyn_shell* sh, const double* in, bool in_pairs, int nf, long long len, int pairing,
+               cudaStream_t st) {
+  if (sh->d.precision != CFFYN_MIXED) return CFFYN_OK;
+  CF_CUDA(cudaMemsetAsync(sh->exps, 0, sizeof(int) * 64, st));
+  const long long* x = reinterpret_cast<const long long*>(in);
+  const int bx = (int)std::min<long long>((len + 255) / 256, 64);
+  if (in_pairs)
+    k_field_exp<true><<<dim3(bx, nf), 256, 0, st>>>(x, len, sh->exps);
+  else
+    k_field_exp<false><<<dim3(bx, nf), 256, 0, st>>>(x, len, sh->exps);
+  count_launch();
+  const long long n = (long long)nf * len;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  uint4* rec = reinterpret_cast<uint4*>(sh->rec);
+  if (in_pairs)
+    k_slice<true><<<nb, 256, 0, st>>>(x, len, n, sh->exps, pairing, rec);
+  else
+    k_slice<false><<<nb, 256, 0, st>>>(x, len, n, sh->exps, pairing, rec);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }
 
@@ -573,7 +646,8 @@ int op_deriv_r(const cffyn_shell* sh, const double* in, double* out, int nfields
   a.g.K = a.g.K0 = a.g.P = a.g.P0 = sh->n_r;
   a.g.in_rs = a.g.out_rs = 1;
   a.g.ncols = (long long)nfields * sh->J * sh->N;
-  return launch(sh, a, sh->Dr, &sh->sDr, dim3(1, 1), st, in_pairs, true);
+  (void)in_pairs;
+  return launch(sh, a, sh->Dr, &sh->sDr, dim3(1, 1), st, 0);
 }
 
 int op_deriv_theta(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
@@ -587,12 +661,13 @@ int op_deriv_theta(const cffyn_shell* sh, const double* in, double* out, int nfi
   a.g.rev1 = 1;
   a.g.in_rs = a.g.out_rs = sh->n_r;
   a.g.ncols = (long long)nfields * (sh->J / 2) * sh->n_r;
-  return launch(sh, a, sh->Dth2, &sh->sDth2, dim3(1, 1), st, in_pairs, true);
+  (void)in_pairs;
+  return launch(sh, a, sh->Dth2, &sh->sDth2, dim3(1, 1), st, 0);
 }
 
 static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb, int K, int P,
                    long long in_bs, long long out_bs, const double* W, const SlicedOp* Ws,
-                   cudaStream_t st, bool in_pairs = true) {
+                   cudaStream_t st, int pairing) {
   OpArgs a = base_args(sh);
   a.kind = OP_ROWS;
   a.in = in;
@@ -604,26 +679,27 @@ static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb,
   a.g.P = a.g.P0 = P;
   a.g.in_rs = a.g.out_rs = a.Q;
   a.g.ncols = (long long)nb * a.Q;
-  return launch(sh, a, W, Ws, dim3(1, 1), st, in_pairs, true);
+  return launch(sh, a, W, Ws, dim3(1, 1), st, pairing);
 }
 
 int op_deriv_phi(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
                  cudaStream_t st) {
   long long bs = (long long)sh->P;
-  return op_rows(sh, in, out, nfields, sh->J, sh->J, bs, bs, sh->Dph, &sh->sDph, st, in_pairs);
+  (void)in_pairs;
+  return op_rows(sh, in, out, nfields, sh->J, sh->J, bs, bs, sh->Dph, &sh->sDph, st, 0);
 }
 
 // phi analysis: S[f][j][i][k] -> C[f][row][i][k]
 int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
   long long Q = (long long)sh->N * sh->n_r;
   return op_rows(sh, in, out, nf, sh->J, sh->R, (long long)sh->J * Q, (long long)sh->R * Q, sh->Fan,
-                 &sh->sFan, st);
+                 &sh->sFan, st, 1);
 }
 
 int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
   long long Q = (long long)sh->N * sh->n_r;
   return op_rows(sh, in, out, nf, sh->R, sh->J, (long long)sh->R * Q, (long long)sh->J * Q, sh->Fsy,
-                 &sh->sFsy, st);
+                 &sh->sFsy, st, 1);
 }
 
 // Projection of all spin classes, coefficients C -> C2 (same layout); one
@@ -644,7 +720,7 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     a.g.K = a.g.K0 = a.g.P = a.g.P0 = N;
     a.g.in_rs = a.g.out_rs = sh->n_r;
     a.g.ncols = (long long)n_r0 * 2 * sh->n_r;
-    int rc = launch(sh, a, sh->Fproj0, &sh->sF0, dim3(1, nm), st);
+    int rc = launch(sh, a, sh->Fproj0, &sh->sF0, dim3(1, nm), st, 1);
     if (rc) return rc;
   }
   for (int s = 0; s < 3; ++s) {
@@ -662,7 +738,7 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     b.g.P = b.g.P0 = N;
     b.g.in_rs = b.g.out_rs = sh->n_r;
     b.g.ncols = (long long)n_c[s] * 4 * sh->n_r;
-    int rc = launch(sh, b, sh->FprojC + (size_t)s * nm * N * 2 * N, &sh->sFC[s], dim3(1, nm), st);
+    int rc = launch(sh, b, sh->FprojC + (size_t)s * nm * N * 2 * N, &sh->sFC[s], dim3(1, nm), st, 1);
     if (rc) return rc;
   }
   return CFFYN_OK;
