@@ -184,6 +184,59 @@ CFFYN_API int cffyn_set_trace(cffyn_shell* sh, int on);
 CFFYN_API int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launches_out,
                               long long* steps);
 
+/* Allocation-free Cartesian derivatives.  A library facility: the paper has
+ * no counterpart (it is a variant of cffyn_derivs, Secs. 2.3-2.4, eq. dvdx).
+ * Computes what cffyn_derivs computes, for the first n_f fields of u only:
+ *     dxyz[d][mu][n_phi][n_theta][n_r], d = x, y, z, mu < n_f (3 * n_f arrays).
+ * Every intermediate (the spherical derivatives and, on the CFFYN_MIXED
+ * path, the digit records and per-field exponents) lives in one fixed array
+ * of CFFYN_STATIC_SCRATCH_BYTES of the library's own device memory, which
+ * exists on each device once the library's device code is loaded there.  The
+ * call allocates nothing (no cudaMalloc, no library allocator) and neither
+ * reads nor writes the shell's workspace: it reads only the shell's constant
+ * grid and operators.
+ *
+ * Who it is for: callers that cannot get device memory at the point of the
+ * call, or must not cause an allocation there: code running with the
+ * device's memory fully reserved by another allocator (a new allocation would
+ * fail), code that must not take the device-wide synchronisation of
+ * cudaMalloc / cudaFree in its loop, and code that differentiates a few
+ * auxiliary or diagnostic fields without disturbing work of the same shell
+ * enqueued on other streams (cffyn_derivs / cffyn_rhs / cffyn_filter write the
+ * shell's workspace; this call does not).
+ *
+ * Size limit: with P = n_r * n_theta * n_phi the call needs
+ * round256(24 * n_f * P) bytes (CFFYN_FP64) or round256(24 * n_f * P) +
+ * round256(16 * n_f * P) + 256 bytes (CFFYN_MIXED), round256 rounding up to
+ * a multiple of 256.  More than CFFYN_STATIC_SCRATCH_BYTES (8 MiB) returns
+ * CFFYN_EINVAL, with the bytes needed in cffyn_last_error(), and launches
+ * nothing.  Examples: 9 x 12 x 24, all 50 fields on either path; 33 x 32 x 64,
+ * 3 fields (mixed) or 5 (FP64).
+ *
+ * Zeroing: the 64 per-field exponent words of the mixed path are maxima
+ * accumulated with atomics and must start at zero on every call; the call
+ * zeroes them itself on `stream` (cudaMemsetAsync, no allocation).  The
+ * caller clears nothing; every other byte is written before it is read.
+ *
+ * Races: there is one array per device, shared by every call on that device
+ * for every shell.  Calls whose device work can overlap (other streams,
+ * other threads, other shells on the same device) race on it and give wrong
+ * results: order them (one stream, or events).  The array is free for the
+ * next call once `stream` has passed the end of this one.
+ *
+ * Set-up: the first call on each device looks up the array's address with
+ * cudaGetSymbolAddress (the shell's device current), which may load the
+ * library's device code there; make that first call before any stream
+ * capture begins on the calling thread.  Later calls only reuse the address.
+ *
+ * Errors: CFFYN_EINVAL for a NULL shell, NULL or unaligned u / dxyz, n_f
+ * outside [1, n_fields], the size limit, or a current device other than the
+ * shell's; CFFYN_ECUDA if the address lookup or a launch fails.  Asynchronous
+ * like cffyn_derivs. */
+#define CFFYN_STATIC_SCRATCH_BYTES (8u * 1024u * 1024u)
+CFFYN_API int cffyn_derivs_static(const cffyn_shell* sh, const double* u, int n_f, double* dxyz,
+                                  void* stream);
+
 /* Message of the last failing call on this thread (never NULL). */
 CFFYN_API const char* cffyn_last_error(void);
 

@@ -16,13 +16,14 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcffyn.so")
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
 FILTER_SUBSTEP, FILTER_STEP = 0, 1
+STATIC_SCRATCH_BYTES = 8 * 1024 * 1024   # CFFYN_STATIC_SCRATCH_BYTES
 
 EXPORTED = [
     "cffyn_create_shell", "cffyn_create_shell_ex", "cffyn_destroy", "cffyn_device_bytes",
     "cffyn_default_dt", "cffyn_set_gauge", "cffyn_init_gauge_from_state", "cffyn_derivs",
     "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_constraint_norms",
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
-    "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace",
+    "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
 ]
 PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
                   "dft_fwd", "project", "dft_inv", "reconstruct"]
@@ -65,6 +66,7 @@ def load(path=LIB_PATH):
         "cffyn_set_gauge": ([vp, dp, vp], i),
         "cffyn_init_gauge_from_state": ([vp, dp, vp], i),
         "cffyn_derivs": ([vp, dp, dp, vp], i),
+        "cffyn_derivs_static": ([vp, dp, i, dp, vp], i),
         "cffyn_rhs": ([vp, dp, dp, vp], i),
         "cffyn_filter": ([vp, dp, dp, vp], i),
         "cffyn_rk4_step": ([vp, dp, d, i, vp], i),
@@ -152,6 +154,14 @@ class Shell:
 
     def derivs(self, u, out, stream=None):
         _check(load().cffyn_derivs(self.h, _ptr(u, "u"), _ptr(out, "dxyz"), _stream(stream)))
+        return out
+
+    def derivs_static(self, u, n_f, out, stream=None):
+        """Cartesian derivatives of the first n_f fields of u into out
+        ([3][n_f][P]) with no allocation: intermediates in the library's
+        fixed STATIC_SCRATCH_BYTES device array (see cffyn_derivs_static)."""
+        _check(load().cffyn_derivs_static(self.h, _ptr(u, "u"), int(n_f), _ptr(out, "dxyz"),
+                                          _stream(stream)))
         return out
 
     def rhs(self, u, out, stream=None):

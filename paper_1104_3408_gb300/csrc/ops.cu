@@ -744,4 +744,61 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
   return CFFYN_OK;
 }
 
+// Spherical derivatives of nf fields (FP64 input) into D = [3][nf][P], with the
+// mixed path's digit records (16 bytes per value, nf * P of them) and field
+// exponents (64 ints) at the given device addresses instead of the shell's
+// workspace.  exps is zeroed here on st: its words are atomicMax targets.  The
+// FP64 path uses neither.  Same kernels and arithmetic as op_prepare followed
+// by op_deriv_r / op_deriv_theta / op_deriv_phi.
+int op_derivs_at(const cffyn_shell* sh, const double* u, double* D, int nf, uint4* rec, int* exps,
+                 cudaStream_t st) {
+  const long long P = (long long)sh->P;
+  if (sh->d.precision != CFFYN_MIXED) {
+    int rc;
+    if ((rc = op_deriv_r(sh, u, D, nf, false, st))) return rc;
+    if ((rc = op_deriv_theta(sh, u, D + nf * P, nf, false, st))) return rc;
+    return op_deriv_phi(sh, u, D + 2 * nf * P, nf, false, st);
+  }
+  CF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * 64, st));
+  const long long* x = reinterpret_cast<const long long*>(u);
+  const int bx = (int)std::min<long long>((P + 255) / 256, 64);
+  k_field_exp<false><<<dim3(bx, nf), 256, 0, st>>>(x, P, exps);
+  count_launch();
+  const long long n = (long long)nf * P;
+  k_slice<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, P, n, exps, 0, rec);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+
+  OpArgs a[3] = {base_args(sh), base_args(sh), base_args(sh)};
+  const SlicedOp* W[3] = {&sh->sDr, &sh->sDth2, &sh->sDph};
+  a[0].kind = OP_R;                                    // as op_deriv_r
+  a[0].g.K = a[0].g.K0 = a[0].g.P = a[0].g.P0 = sh->n_r;
+  a[0].g.in_rs = a[0].g.out_rs = 1;
+  a[0].g.ncols = (long long)nf * sh->J * sh->N;
+  a[1].kind = OP_THETA;                                // as op_deriv_theta
+  a[1].g.K = a[1].g.P = 2 * sh->N;
+  a[1].g.K0 = a[1].g.P0 = sh->N;
+  a[1].g.rev1 = 1;
+  a[1].g.in_rs = a[1].g.out_rs = sh->n_r;
+  a[1].g.ncols = (long long)nf * (sh->J / 2) * sh->n_r;
+  a[2].kind = OP_ROWS;                                 // as op_deriv_phi
+  a[2].Q = sh->N * sh->n_r;
+  a[2].in_bs = a[2].out_bs = P;
+  a[2].g.K = a[2].g.K0 = a[2].g.P = a[2].g.P0 = sh->J;
+  a[2].g.in_rs = a[2].g.out_rs = a[2].Q;
+  a[2].g.ncols = (long long)nf * a[2].Q;
+  for (int i = 0; i < 3; ++i) {
+    a[i].in = u;
+    a[i].out = D + i * nf * P;
+    if (a[i].g.ncols <= 0) continue;
+    const unsigned gx = (unsigned)((a[i].g.ncols + OZ_QT - 1) / OZ_QT);
+    const int KP = W[i]->ksteps * 16 + 8;
+    const size_t smem = (size_t)kSlices * OZ_QT * KP * sizeof(unsigned short);
+    k_op_rec<true><<<dim3(gx, 1), W[i]->mtiles * 32, smem, st>>>(a[i], *W[i], rec, exps, 0);
+    count_launch();
+    CF_CUDA(cudaGetLastError());
+  }
+  return CFFYN_OK;
+}
+
 }  // namespace cffyn

@@ -65,3 +65,11 @@ def test_null_handles_are_rejected(lib):
     assert lib.cffyn_filter(None, None, None, None) == cffyn.EINVAL
     assert lib.cffyn_rk4_step(None, None, 0.1, 1, None) == cffyn.EINVAL
     assert lib.cffyn_create_shell_ex(None, None) == cffyn.EINVAL
+
+
+def test_static_scratch_limit_and_null_shell(lib):
+    with open(os.path.join(ROOT, "include", "cffyn.h")) as fh:
+        m = re.search(r"#define CFFYN_STATIC_SCRATCH_BYTES \((\d+)u \* (\d+)u \* (\d+)u\)", fh.read())
+    assert m and int(m[1]) * int(m[2]) * int(m[3]) == cffyn.STATIC_SCRATCH_BYTES
+    assert lib.cffyn_derivs_static(None, None, 1, None, None) == cffyn.EINVAL
+    assert b"NULL" in lib.cffyn_last_error()
