@@ -139,7 +139,9 @@ CFFYN_API int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* 
  * call captures one step in a CUDA graph (so it must not itself be made during
  * a stream capture); later calls with the same u and dt replay it.  The call
  * synchronises `stream` at its end to read the fused finiteness flag and
- * returns CFFYN_ENONFINITE if a stage right-hand side was not finite. */
+ * returns CFFYN_ENONFINITE if a stage right-hand side was not finite, or
+ * CFFYN_ETIMEOUT if a bounded wait of a tensor-core operator kernel gave up
+ * (the results are then invalid; the context stays usable). */
 CFFYN_API int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream);
 
 /* RMS over all points of C_iab = d_i g_ab - Phi_iab (30 components, numerical
@@ -189,7 +191,7 @@ CFFYN_API int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launch
  * Computes what cffyn_derivs computes, for the first n_f fields of u only:
  *     dxyz[d][mu][n_phi][n_theta][n_r], d = x, y, z, mu < n_f (3 * n_f arrays).
  * Every intermediate (the spherical derivatives and, on the CFFYN_MIXED
- * path, the digit records and per-field exponents) lives in one fixed array
+ * path, the per-field exponents) lives in one fixed array
  * of CFFYN_STATIC_SCRATCH_BYTES of the library's own device memory, which
  * exists on each device once the library's device code is loaded there.  The
  * call allocates nothing (no cudaMalloc, no library allocator) and neither
@@ -206,12 +208,11 @@ CFFYN_API int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launch
  * shell's workspace; this call does not).
  *
  * Size limit: with P = n_r * n_theta * n_phi the call needs
- * round256(24 * n_f * P) bytes (CFFYN_FP64) or round256(24 * n_f * P) +
- * round256(16 * n_f * P) + 256 bytes (CFFYN_MIXED), round256 rounding up to
- * a multiple of 256.  More than CFFYN_STATIC_SCRATCH_BYTES (8 MiB) returns
- * CFFYN_EINVAL, with the bytes needed in cffyn_last_error(), and launches
- * nothing.  Examples: 9 x 12 x 24, all 50 fields on either path; 33 x 32 x 64,
- * 3 fields (mixed) or 5 (FP64).
+ * round256(24 * n_f * P) bytes, plus 256 on the CFFYN_MIXED path (round256
+ * rounds up to a multiple of 256).  More than CFFYN_STATIC_SCRATCH_BYTES
+ * (8 MiB) returns CFFYN_EINVAL, with the bytes needed in cffyn_last_error(),
+ * and launches nothing.  Examples: 9 x 12 x 24, all 50 fields; 33 x 32 x 64,
+ * 5 fields.
  *
  * Zeroing: the 64 per-field exponent words of the mixed path are maxima
  * accumulated with atomics and must start at zero on every call; the call

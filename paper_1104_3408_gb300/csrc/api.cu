@@ -36,7 +36,7 @@ int op_project(const cffyn_shell*, const double*, double*, const int*, int, cons
 int op_prepare(const cffyn_shell*, const double*, bool, int, long long, int, cudaStream_t);
 // setup.cu
 int build_operators(cffyn_shell*);
-void free_sliced(SlicedOp&);
+void free_tc(TcOp&);
 // pointwise.cu
 int pw_rhs(const cffyn_shell*, const double*, const double*, double*, cudaStream_t);
 int pw_rhs_part(const cffyn_shell*, const double*, const double*, double*, int, bool, bool, cudaStream_t);
@@ -109,12 +109,12 @@ void free_shell(cffyn_shell* sh) {
   double** ptrs[] = {&sh->r,     &sh->sth,    &sh->cth,    &sh->sph, &sh->cph,  &sh->Dr,   &sh->Dth2,
                      &sh->Dph,   &sh->Fan,    &sh->Fsy,    &sh->Fraw, &sh->Fproj0, &sh->FprojC,
                      &sh->H,     &sh->dH,     &sh->U,      &sh->kacc, &sh->D,    &sh->S,
-                     &sh->Rsrc,  &sh->red,    &sh->rec};
+                     &sh->Rsrc,  &sh->red};
   for (double** p : ptrs)
     if (*p) cudaFree(*p);
-  SlicedOp* so[] = {&sh->sDr, &sh->sDth2, &sh->sDph, &sh->sFan, &sh->sFsy, &sh->sF0,
-                    &sh->sFC[0], &sh->sFC[1], &sh->sFC[2]};
-  for (SlicedOp* s : so) free_sliced(*s);
+  TcOp* to[] = {&sh->tDr, &sh->tDth2, &sh->tDph, &sh->tFan, &sh->tFsy, &sh->tF0,
+                &sh->tFC[0], &sh->tFC[1], &sh->tFC[2]};
+  for (TcOp* t : to) free_tc(*t);
   if (sh->slots) cudaFree(sh->slots);
   if (sh->exps) cudaFree(sh->exps);
   if (sh->cap_stream) cudaStreamDestroy(sh->cap_stream);
@@ -213,10 +213,8 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
       (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->Rsrc, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, 12 * sh->P)) ||
       (rc = alloc(&sh->red, 2)))
     return fail(rc);
-  if (d.precision == CFFYN_MIXED) {
-    if ((rc = alloc(&sh->rec, 2 * nvP))) return fail(rc);  // 16-byte records
+  if (d.precision == CFFYN_MIXED)
     if (cudaMalloc(&sh->exps, 64 * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
-  }
   {
     int host[33];
     for (int i = 0; i < 16; ++i) host[i] = i;
@@ -477,6 +475,10 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
       if (sh->mark_phase[i] >= 0) sh->trace_ms[sh->mark_phase[i]] += (double)ms * n_steps;
     }
     sh->trace_steps += n_steps;
+  }
+  if (*sh->flag_host & 2) {
+    set_error("a bounded tensor-core wait gave up (operator results are invalid)");
+    return CFFYN_ETIMEOUT;
   }
   if (*sh->flag_host) {
     set_error("non-finite value in a stage right-hand side");

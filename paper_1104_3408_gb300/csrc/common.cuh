@@ -48,13 +48,20 @@ struct SpinLayout {
 };
 
 // --------------------------------------------------------------------------
-// Split-precision (Ozaki-style) operator: digits of every row in the
-// mma.m16n8k16 A-fragment order, plus per-row binary exponents.
-struct SlicedOp {
-  uint4* frag = nullptr;  // [batch][slice][mtile][kstep][lane] -> 4 x bf16x2
-  int* rowexp = nullptr;  // [batch][P_pad]
-  int P = 0, K = 0, mtiles = 0, ksteps = 0, nbatch = 1;
-  size_t frag_stride = 0, rowexp_stride = 0;  // per batch
+// Split-precision operator for the tcgen05 core: W cut into row groups of
+// `rows` = 48 (P <= 48) or 96 rows and k-steps of 16 columns; per (group,
+// k-step) eleven BF16 digit slices of rows x 16 in the K-major no-swizzle
+// core-matrix order (core matrix = 8 rows x 8 columns, 128 contiguous bytes;
+// the two core matrices of an 8-row group adjacent, groups 256 bytes apart).
+// Slices 0..4 are digits 0..4 of W; slices 5..10 are digits 0..5 scaled by
+// 2^-8 (they carry the digit-sum-5 products into the digit-sum-4
+// accumulator).
+constexpr int kTcWSlices = 11;
+struct TcOp {
+  unsigned short* w = nullptr;  // [batch][group][kstep][slice][rows x 16]
+  int* rowexp = nullptr;        // [batch][groups * rows]
+  int P = 0, K = 0, rows = 0, ngroups = 0, ksteps = 0, nbatch = 1;
+  size_t w_stride = 0, rowexp_stride = 0;  // per batch (elements)
 };
 
 struct cffyn_shell_impl;
@@ -82,10 +89,9 @@ struct cffyn_shell {
   double* Fproj0 = nullptr; // [L+1] N x N : F^0_m
   double* FprojC = nullptr; // [3][L+1] N x 2N : [F_s | F_d] for spin 1..3
 
-  // split-precision operators
-  cffyn::SlicedOp sDr, sDth2, sDph, sFan, sFsy;
-  cffyn::SlicedOp sF0;       // batched over m = 0..L
-  cffyn::SlicedOp sFC[3];    // per spin 1..3, batched over m
+  // split-precision operators (tcgen05 core); tF0 and tFC are batched over
+  // m = 0..L, tFC per spin 1..3
+  cffyn::TcOp tDr, tDth2, tDph, tFan, tFsy, tF0, tFC[3];
 
   cffyn::SpinLayout spin;
 
@@ -100,8 +106,7 @@ struct cffyn_shell {
   double* D = nullptr;     // spherical derivatives [3][nv][P] (also DFT coefficients)
   double* S = nullptr;     // rhs / spin functions [nv][P]
   double* Rsrc = nullptr;  // right-hand-side source terms [nv][P]
-  double* rec = nullptr;   // split-precision digit records, 16 bytes per value [nv][P]
-  int* exps = nullptr;     // per-field exponents of the sliced array (64 entries)
+  int* exps = nullptr;     // per-field exponents of the next operator input (64 entries)
   double* red = nullptr;   // device reduction words (2 doubles)
   int* flag = nullptr;     // device non-finite flag
   int* flag_host = nullptr;  // pinned host copy of the flag

@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "scalar.cuh"
+#include "tc.cuh"
 
 namespace cffyn {
 
@@ -246,15 +247,6 @@ __global__ void __launch_bounds__(256) k_op_fp64(OpArgs a, const double* __restr
 // ---------------------------------------------------------------------------
 // Split-precision core.
 
-constexpr int OZ_QT = 32;        // columns per CTA (4 n-tiles of 8)
-constexpr int OZ_NT = OZ_QT / 8;
-constexpr int OZ_MAXK = 192;
-constexpr int OZ_KCHUNK = 6;     // k-steps (of 16) per exact partial sum
-
-__device__ __forceinline__ int exp_field(double x) {
-  return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-}
-
 // frexp exponent + 1022 of a raw element (0 for zero): FP64 word, or the
 // leading float of a pair (|hi + lo| < 2^frexp(hi) for a normalised pair)
 template <bool FI>
@@ -320,16 +312,6 @@ __device__ __forceinline__ void digits_bf16(long long Z, unsigned int out[kSlice
   out[0] = __float_as_uint(__int_as_float(0x4B400000 + top) - 12582912.0f) >> 16;
 }
 
-// FP32 value holding an exact integer |v| < 2^24 -> int, integer ops only.
-__device__ __forceinline__ int f32_int_exact(float v) {
-  const unsigned int u = __float_as_uint(v);
-  const int e = (int)((u >> 23) & 0xff);
-  const int m = (int)((u & 0x7fffff) | 0x800000);
-  const int sh = 150 - e;
-  int r = (sh < 32 && e != 0) ? (m >> sh) : 0;
-  return (u >> 31) ? -r : r;
-}
-
 // T * 2^sc as a double (round to nearest), integer ops only.
 __device__ __forceinline__ double i64_scaled_to_double(long long T, int sc) {
   if (T == 0) return 0.0;
@@ -353,16 +335,6 @@ __device__ __forceinline__ double i64_scaled_to_double(long long T, int sc) {
   return __longlong_as_double((long long)bits);
 }
 
-// Four 8x8 BF16 tiles from shared memory; lane l addresses row (l % 8) of tile
-// (l / 8) and receives, per tile, the pair at row lane/4, columns 2*(lane%4).
-__device__ __forceinline__ void ldmatrix_x4(unsigned int& r0, unsigned int& r1, unsigned int& r2,
-                                            unsigned int& r3, const void* p) {
-  const unsigned int a = (unsigned int)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(a));
-}
-
 // T * 2^sc as a (hi, lo) float pair packed in 64 bits: hi exact leading 24
 // bits, lo the next 24 (truncated).
 __device__ __forceinline__ long long i64_scaled_to_pair(long long T, int sc) {
@@ -382,22 +354,14 @@ __device__ __forceinline__ long long i64_scaled_to_pair(long long T, int sc) {
   return (long long)(((unsigned long long)__float_as_uint(lo) << 32) | __float_as_uint(hi));
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], const uint4& a, unsigned int b0, unsigned int b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
-
 // ---------------------------------------------------------------------------
-// Slicing pass: per-field exponents and 16-byte digit records.
+// Per-field exponents of the mixed path's operator inputs.
 //
 // exps[f] = max over the field of (frexp exponent + 1022), 0 for an all-zero
 // field.  With pairing, slots f >= kPairedFrom form (re, im) pairs (f, f^1)
 // that share one exponent (the projection of a complex function gathers
-// both).  A record holds the six balanced digits (slice 0 first) of the
-// 47-bit fixed point round(x 2^(47-E)), E = exps - 1022, as BF16 halves.
+// both).  Column values are cut into 47-bit fixed point round(x 2^(47-E)),
+// E = exps - 1022, inside the operator kernel.
 
 constexpr int kPairedFrom = 16;
 
@@ -413,216 +377,330 @@ __global__ void k_field_exp(const long long* __restrict__ in, long long len, int
   if ((threadIdx.x & 31) == 0 && m) atomicMax(exps + f, m);
 }
 
-template <bool FI>
-__global__ void k_slice(const long long* __restrict__ in, long long len, long long n,
-                        const int* __restrict__ exps, int pairing, uint4* __restrict__ rec) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const int f = (int)(e / len);
-  int ex = exps[f];
-  if (pairing && f >= kPairedFrom) ex = max(ex, exps[f ^ 1]);
-  unsigned int d[kSlices];
-  digits_bf16(raw_fixed47<FI>(__ldg(in + e), ex - 1022), d);
-  rec[e] = make_uint4(d[0] | (d[1] << 16), d[2] | (d[3] << 16), d[4] | (d[5] << 16), 0u);
-}
+// ---------------------------------------------------------------------------
+// Split-precision core on the fifth-generation tensor cores (tcgen05).
+//
+// CTA: 128 data columns (the MMA's M: one TMEM lane each) x one row group of
+// W (N = 48 or 96 rows), all of K in k-steps of 16 through a ring of
+// shared-memory stages.  Warp-specialised:
+//   producer warps (256 or 512 threads; one column and KQ = 8 or 4
+//     consecutive k of every k-step each): write the six BF16 digit slices of
+//     their values (47-bit fixed point relative to the field's exponent, input
+//     words prefetched one k-step ahead) into the stage, then arrive on its
+//     `xfull` barrier; after the last k-step they run the epilogue;
+//   one MMA warp: bulk-copies (TMA) the operator's eleven slices of each
+//     k-step (see TcOp) a stage ahead and, once a stage is full, issues the 21
+//     digit-pair MMAs into five FP32 accumulators in TMEM and commits them to
+//     the stage's `empty` barrier:
+//   acc_d = sum_{i+j=d} W_i X_j                            d = 0..3
+//   acc_4 = sum_{i+j=4} W_i X_j + 2^-8 sum_{i+j=5} W_i X_j
+// acc_0..acc_3 are exact integers (below 4 * 192 * 2^14 < 2^24).  acc_4 is
+// not exact; its rounding is below 2^-24 of a term of weight 256^-4 relative
+// to the leading one, about 2^-56 of the result's scale, under the truncation
+// of the dropped pairs i + j > 5 (about 6 * 2^-48).  The epilogue sums
+// (acc_0 + acc_1 2^-8 + ... + acc_4 2^-32) 2^(E_row + E_col - 14) as a
+// float pair with error-free FP32 transformations.
 
-// Digit record of one column element (zero record outside K or for the empty
-// second segment; negation flips the sign bit of every BF16 digit).
-__device__ __forceinline__ uint4 load_rec(const OpArgs& a, const uint4* __restrict__ rec, const ColDesc& d,
-                                          int k) {
-  if (!d.valid || k >= a.g.K) return make_uint4(0u, 0u, 0u, 0u);
-  if (k < a.g.K0) return __ldg(rec + d.in0 + (long long)k * a.g.in_rs);
-  if (d.sgn1 == 2) return make_uint4(0u, 0u, 0u, 0u);
-  const int kk = a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0);
-  uint4 r = __ldg(rec + d.in1 + (long long)kk * a.g.in_rs);
-  if (d.sgn1) {
-    r.x ^= 0x80008000u;
-    r.y ^= 0x80008000u;
-    r.z ^= 0x80008000u;
+constexpr int kTcCols = 128;
+constexpr int kTcXSlice = kTcCols * 16 * 2;                 // bytes of one data slice per k-step
+constexpr int kTcXBytes = kSlices * kTcXSlice;               // 24576
+constexpr unsigned long long kTcWaitNs = 1000000000ull;      // bounded waits: 1 s
+
+template <int ROWS>
+struct TcCfg {
+  static constexpr int kProd = ROWS == 48 ? 256 : 512;                 // producer threads
+  static constexpr int kThreads = kProd + 32;                          // + the MMA warp
+  static constexpr int kKQ = 16 * kTcCols / kProd;                     // k per producer per k-step
+  static constexpr int kWSlice = ROWS * 16 * 2;                        // bytes of one operator slice
+  static constexpr int kWBytes = kTcWSlices * kWSlice;                 // 16896 | 33792
+  static constexpr int kStage = kTcXBytes + kWBytes;                   // 41472 | 58368
+  static constexpr int kStages = ROWS == 48 ? 2 : 3;                   // 2 CTAs / 1 CTA per SM
+  static constexpr int kSmem = kStages * kStage;                       // 82944 | 175104
+  static constexpr uint32_t kTmemCols = ROWS == 48 ? 256 : 512;        // 5 accumulators x ROWS
+};
+
+// Raw 64-bit words of N consecutive k of one column (zero outside K or in an
+// empty second segment; the sign of a negated segment applied on the bits).
+// Branch-free so that the loads issue together.
+template <bool FI, int N>
+__device__ __forceinline__ void gather(const OpArgs& a, const ColDesc& d, int k0, long long (&w)[N]) {
+  const long long* in = reinterpret_cast<const long long*>(a.in);
+  const long long m = FI ? (long long)0x8000000080000000ull : (long long)0x8000000000000000ull;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int k = k0 + i;
+    const bool seg1 = k >= a.g.K0;
+    const int kk = seg1 ? (a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0)) : k;
+    const long long base = seg1 ? d.in1 : d.in0;
+    const bool live = d.valid && k < a.g.K && !(seg1 && d.sgn1 == 2);
+    const long long v = live ? __ldg(in + base + (long long)kk * a.g.in_rs) : 0ll;
+    w[i] = (seg1 && d.sgn1 == 1) ? (v ^ m) : v;
   }
-  return r;
 }
 
-// CTA: one warp per m-tile of W (mtiles warps), OZ_QT columns.  The input is
-// given as digit records (see k_slice); the prologue only copies them into
-// the slice-major shared-memory tile.
-template <bool FO>
-__global__ void __launch_bounds__(384) k_op_rec(OpArgs a, SlicedOp W, const uint4* __restrict__ rec,
-                                              const int* __restrict__ exps, int pairing) {
-  extern __shared__ unsigned short smoz[];
+// (hi, lo) float pair, packed like the mixed path's internal storage, of
+// (a0 + a1 2^-8 + a2 2^-16 + a3 2^-24 + a4 2^-32) 2^k.
+__device__ __forceinline__ long long fold_pair(float a0, float a1, float a2, float a3, float a4, int k) {
+  ff r = two_sum(a0, fm(a1, 0.00390625f));
+  float e = r.lo;
+  r = two_sum(r.hi, fm(a2, 1.52587890625e-05f));
+  e = fa(e, r.lo);
+  r = two_sum(r.hi, fm(a3, 5.9604644775390625e-08f));
+  e = fa(e, r.lo);
+  r = two_sum(r.hi, fm(a4, 2.3283064365386963e-10f));
+  e = fa(e, r.lo);
+  r = fast_two_sum(r.hi, e);
+  // 2^k as one or two exact float factors (k below -126 only for results
+  // under the float range)
+  const int k1 = max(-126, min(127, k));
+  const int k2 = max(-126, min(127, k - k1));
+  const float f1 = __int_as_float((k1 + 127) << 23), f2 = __int_as_float((k2 + 127) << 23);
+  const float hi = fm(fm(r.hi, f1), f2), lo = fm(fm(r.lo, f1), f2);
+  return (long long)(((unsigned long long)__float_as_uint(lo) << 32) | __float_as_uint(hi));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(b)) : "memory");
+}
+
+template <bool FI, int ROWS>
+__global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp W, const int* __restrict__ exps,
+                                                                 int pairing, int* __restrict__ flag) {
+  using C = TcCfg<ROWS>;
+  constexpr int S = C::kStages, KQ = C::kKQ;
+  extern __shared__ __align__(128) unsigned char smtc[];
+  __shared__ uint64_t xfull[S], wfull[S], empty[S], accf;
+  __shared__ uint32_t tmem_base;
+  __shared__ int rowE[ROWS];
+  const int tid = threadIdx.x;
+  const bool producer = tid < C::kProd;
+  const long long tile = blockIdx.x / W.ngroups;
+  const int grp = (int)(blockIdx.x - tile * W.ngroups);
   if (a.batched_m) {
     a.m = blockIdx.y;
-    W.frag += (size_t)a.m * W.frag_stride;
+    W.w += (size_t)a.m * W.w_stride;
     W.rowexp += (size_t)a.m * W.rowexp_stride;
   }
-  const int K = a.g.K;
+  const int ctile = tid & (kTcCols - 1);        // column within the tile (producers)
+  const int kq = (tid >> 7) * KQ;               // first k of this producer within a k-step
+  const ColDesc col = make_col(a, tile * kTcCols + ctile);
+  int ce = exps[col.fld];
+  if (pairing && col.fld >= kPairedFrom) ce = max(ce, exps[col.fld ^ 1]);
+  const int E = ce - 1022;
+  if (tid < ROWS) rowE[tid] = W.rowexp[grp * ROWS + tid];
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::bar_init(&xfull[s], C::kProd);
+      tc::bar_init(&wfull[s], 1);
+      tc::bar_init(&empty[s], 1);
+    }
+    tc::bar_init(&accf, 1);
+  }
+  if (tid >= C::kProd) tc::alloc(&tmem_base, C::kTmemCols);  // the MMA warp
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tmem_base;
   const int ksteps = W.ksteps;
-  const int KP = ksteps * 16 + 8;                    // row pitch (halfwords), odd multiple of 8
-  unsigned short* Bs = smoz;                         // [kSlices][OZ_QT][KP]
-  __shared__ ColDesc cols[OZ_QT];
-  __shared__ int colE[OZ_QT];
-  const long long c0 = (long long)blockIdx.x * OZ_QT;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  if (tid < OZ_QT) cols[tid] = make_col(a, c0 + tid);
-  __syncthreads();
-  const bool kfast = a.kind == OP_R;
-  const int Kp = ksteps * 16;
-  const int KH = Kp / 2;                 // k pairs per column
-  const int KPW = KP / 2;                // row pitch in 32-bit words
-  unsigned int* Bw = reinterpret_cast<unsigned int*>(Bs);
-  const int nitems = KH * OZ_QT;
-  if (tid < OZ_QT) {
-    const int f = cols[tid].fld;
-    int e = exps[f];
-    if (pairing && f >= kPairedFrom) e = max(e, exps[f ^ 1]);
-    colE[tid] = e - 1022;
-  }
-  // copy the digit records of the tile: two k values of one column per item
-  for (int e = tid; e < nitems; e += nthr) {
-    int kp, c;
-    if (kfast) { kp = e % KH; c = e / KH; } else { c = e % OZ_QT; kp = e / OZ_QT; }
-    const uint4 r0 = load_rec(a, rec, cols[c], 2 * kp);
-    const uint4 r1 = load_rec(a, rec, cols[c], 2 * kp + 1);
-    unsigned int* dst = Bw + (size_t)c * KPW + kp;
-    const size_t sstride = (size_t)OZ_QT * KPW;
-    dst[0] = __byte_perm(r0.x, r1.x, 0x5410);
-    dst[sstride] = __byte_perm(r0.x, r1.x, 0x7632);
-    dst[2 * sstride] = __byte_perm(r0.y, r1.y, 0x5410);
-    dst[3 * sstride] = __byte_perm(r0.y, r1.y, 0x7632);
-    dst[4 * sstride] = __byte_perm(r0.z, r1.z, 0x5410);
-    dst[5 * sstride] = __byte_perm(r0.z, r1.z, 0x7632);
-  }
-  __syncthreads();
+  bool ok = true;
 
-  const int warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, tg = lane & 3;
-  const int mt = warp;
-  if (mt >= W.mtiles) return;
-  long long T[OZ_NT][4];
+  if (producer) {
+    // byte offset of this thread's row piece (column ctile, k kq..kq+KQ-1)
+    const int xoff = (ctile >> 3) * 256 + (kq >> 3) * 128 + (ctile & 7) * 16 + (kq & 7) * 2;
+    long long nxt[KQ];
+    gather<FI, KQ>(a, col, kq, nxt);
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int s = ks % S;
+      long long cur[KQ];
 #pragma unroll
-  for (int n = 0; n < OZ_NT; ++n)
+      for (int i = 0; i < KQ; ++i) cur[i] = nxt[i];
+      if (ks + 1 < ksteps) gather<FI, KQ>(a, col, (ks + 1) * 16 + kq, nxt);
+      if (ks >= S && ok) ok = tc::bar_wait(&empty[s], ((ks - S) / S) & 1, kTcWaitNs);
+      unsigned char* xs = smtc + s * C::kStage + xoff;
+      uint32_t wd[kSlices][KQ / 2];
+      if (ks * 16 + kq < a.g.K) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) T[n][q] = 0;
-
-  // k-step outer: the six operator digit fragments A_i(ks) are loaded once per
-  // k-step, each data slice B_j(ks) once per k-step, and every pair (i, j)
-  // accumulates into the digit-sum accumulator d = i + j (exact FP32 integers
-  // per K chunk, folded into T with weight 256^(5-d)).
-  const unsigned short* Bl = Bs + (size_t)(((lane >> 4) * 8) + (lane & 7)) * KP + ((lane >> 3) & 1) * 8;
-  const uint4* Am = W.frag + ((size_t)mt * ksteps) * 32 + lane;
-  const size_t aslice = (size_t)W.mtiles * ksteps * 32;
-  for (int kc = 0; kc < ksteps; kc += OZ_KCHUNK) {
-    const int kend = min(ksteps, kc + OZ_KCHUNK);
-    float acc[kSlices][OZ_NT][4];
+        for (int i = 0; i < KQ; i += 2) {
+          unsigned int d0[kSlices], d1[kSlices];
+          digits_bf16(raw_fixed47<FI>(cur[i], E), d0);
+          digits_bf16(raw_fixed47<FI>(cur[i + 1], E), d1);
 #pragma unroll
-    for (int d = 0; d < kSlices; ++d)
+          for (int j = 0; j < kSlices; ++j) wd[j][i >> 1] = d0[j] | (d1[j] << 16);
+        }
+      } else {
 #pragma unroll
-      for (int n = 0; n < OZ_NT; ++n)
+        for (int j = 0; j < kSlices; ++j)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[d][n][q] = 0.0f;
-    for (int ks = kc; ks < kend; ++ks) {
-      uint4 af[kSlices];
-#pragma unroll
-      for (int i = 0; i < kSlices; ++i) af[i] = __ldg(Am + i * aslice + (size_t)ks * 32);
+          for (int i = 0; i < KQ / 2; ++i) wd[j][i] = 0u;
+      }
 #pragma unroll
       for (int j = 0; j < kSlices; ++j) {
-        const unsigned short* Bj = Bl + (size_t)j * OZ_QT * KP + ks * 16;
+        if (KQ == 8)
+          *reinterpret_cast<uint4*>(xs + j * kTcXSlice) = make_uint4(wd[j][0], wd[j][1], wd[j][2], wd[j][3]);
+        else
+          *reinterpret_cast<uint2*>(xs + j * kTcXSlice) = make_uint2(wd[j][0], wd[j][1]);
+      }
+      tc::fence_proxy_async();
+      bar_arrive(&xfull[s]);
+    }
+    if (ok) ok = tc::bar_wait(&accf, 0, kTcWaitNs);
+  } else if (tid == C::kProd) {
+    // MMA thread
+    const unsigned char* wsrc =
+        reinterpret_cast<const unsigned char*>(W.w) + (size_t)grp * ksteps * C::kWBytes;
+    const uint32_t sbase = tc::smem_addr(smtc);
+    for (int ks = 0; ks < S && ks < ksteps; ++ks) {
+      tc::bar_expect_tx(&wfull[ks], C::kWBytes);
+      tc::bulk_g2s(smtc + ks * C::kStage + kTcXBytes, wsrc + (size_t)ks * C::kWBytes, C::kWBytes, &wfull[ks]);
+    }
+    int copied = S < ksteps ? S : ksteps;  // operator k-steps whose copy has been issued
+    for (int ks = 0; ks < ksteps && ok; ++ks) {
+      const int s = ks % S;
+      ok = tc::bar_wait(&wfull[s], (ks / S) & 1, kTcWaitNs) && tc::bar_wait(&xfull[s], (ks / S) & 1, kTcWaitNs);
+      if (!ok) break;
+      tc::fence_after();
+      const uint32_t xa = sbase + s * C::kStage;
+      const uint64_t dx = tc::desc_kmajor(xa, 128, 256);
+      const uint64_t dw = tc::desc_kmajor(xa + kTcXBytes, 128, 256);
+      constexpr uint32_t ID = tc::idesc_bf16_f32(kTcCols, ROWS);
+      constexpr uint64_t XS = kTcXSlice >> 4, WS = C::kWSlice >> 4;  // slice strides, descriptor units
 #pragma unroll
-        for (int n = 0; n < OZ_NT; n += 2) {
-          unsigned int b00, b01, b10, b11;
-          ldmatrix_x4(b00, b01, b10, b11, Bj + (size_t)n * 8 * KP);
+      for (int d = 0; d < 5; ++d)
 #pragma unroll
-          for (int i = 0; i < kSlices - j; ++i) {
-            mma_bf16(acc[i + j][n], af[i], b00, b01);
-            mma_bf16(acc[i + j][n + 1], af[i], b10, b11);
-          }
+        for (int i = 0; i <= d; ++i)
+          tc::mma(tm + d * ROWS, dx + (d - i) * XS, dw + i * WS, ID, (ks > 0 || i > 0) ? 1u : 0u);
+#pragma unroll
+      for (int i = 0; i < 6; ++i) tc::mma(tm + 4 * ROWS, dx + (5 - i) * XS, dw + (5 + i) * WS, ID, 1u);
+      tc::commit(&empty[s]);
+      // refill the stage of k-step ks - 1 with the operator of k-step ks - 1 + S
+      if (ks >= 1 && copied < ksteps) {
+        const int sp = (ks - 1) % S;
+        ok = tc::bar_wait(&empty[sp], ((ks - 1) / S) & 1, kTcWaitNs);
+        if (!ok) break;
+        tc::bar_expect_tx(&wfull[sp], C::kWBytes);
+        tc::bulk_g2s(smtc + sp * C::kStage + kTcXBytes, wsrc + (size_t)copied * C::kWBytes, C::kWBytes,
+                     &wfull[sp]);
+        ++copied;
+      }
+    }
+    if (ok) tc::commit(&accf);
+    if (!ok) {
+      // let operator copies still in flight land before the CTA's memory goes
+      for (int c = (copied > S ? copied - S : 0); c < copied; ++c) tc::bar_wait(&wfull[c % S], (c / S) & 1, kTcWaitNs);
+    }
+  }
+  ok = __syncthreads_and(ok);
+  if (!ok && tid == 0) atomicOr(flag, 2);
+  if (!ok && tid == C::kProd) {
+    // MMAs possibly still in flight: one more bounded wait on the last commit
+    tc::bar_wait(&empty[(ksteps - 1) % S], ((ksteps - 1) / S) & 1, kTcWaitNs);
+  }
+  tc::fence_after();
+  if (ok && producer) {
+    // producer warp w reads TMEM lanes 32 (w % 4) .. + 31 (its columns) and
+    // rows [g R, (g + 1) R) of every accumulator, g = w / 4, R = ROWS / (warps / 4)
+    constexpr int R = ROWS / (C::kProd / 128);
+    const int g = tid >> 7;
+    const int prow = a.g.P - grp * ROWS;  // valid rows of this group
+    const uint32_t lane = tm + ((uint32_t)(((tid >> 5) & 3) * 32) << 16);
+#pragma unroll 1
+    for (int p0 = g * R; p0 < (g + 1) * R && p0 < prow; p0 += 8) {
+      uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
+      tc::ld8(lane + 0 * ROWS + p0, v0);
+      tc::ld8(lane + 1 * ROWS + p0, v1);
+      tc::ld8(lane + 2 * ROWS + p0, v2);
+      tc::ld8(lane + 3 * ROWS + p0, v3);
+      tc::ld8(lane + 4 * ROWS + p0, v4);
+      tc::ld_wait(v0);
+      tc::tie(v1);
+      tc::tie(v2);
+      tc::tie(v3);
+      tc::tie(v4);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (p0 + j < prow) {
+          const long long w =
+              fold_pair(__uint_as_float(v0[j]), __uint_as_float(v1[j]), __uint_as_float(v2[j]),
+                        __uint_as_float(v3[j]), __uint_as_float(v4[j]), rowE[p0 + j] + E - 14);
+          store_elem(a, col, grp * ROWS + p0 + j, __longlong_as_double(w));
         }
       }
     }
-#pragma unroll
-    for (int d = 0; d < kSlices; ++d)
-#pragma unroll
-      for (int n = 0; n < OZ_NT; ++n)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          T[n][q] += ((long long)__float2int_rz(acc[d][n][q])) << (8 * (kSlices - 1 - d));
   }
-  // epilogue: rows mt*16 + g (+8), columns n*8 + 2tg (+1)
-  const int rowA = mt * 16 + g, rowB = rowA + 8;
-  const int eA = W.rowexp[rowA], eB = W.rowexp[rowB];
-#pragma unroll
-  for (int n = 0; n < OZ_NT; ++n) {
-    const int cA = n * 8 + 2 * tg, cB = cA + 1;
-    const int sA = colE[cA], sB = colE[cB];
-    auto put = [&](const ColDesc& d, int row, long long t, int sc) {
-      const long long w = FO ? i64_scaled_to_pair(t, sc)
-                             : __double_as_longlong(i64_scaled_to_double(t, sc));
-      store_elem(a, d, row, __longlong_as_double(w));
-    };
-    put(cols[cA], rowA, T[n][0], eA + sA - 54);
-    put(cols[cB], rowA, T[n][1], eA + sB - 54);
-    put(cols[cA], rowB, T[n][2], eB + sA - 54);
-    put(cols[cB], rowB, T[n][3], eB + sB - 54);
+  tc::fence_before();
+  __syncthreads();
+  if (tid >= C::kProd) {
+    tc::fence_after();
+    tc::dealloc(tm, C::kTmemCols);
   }
 }
 
 // ---------------------------------------------------------------------------
 // Host side
 
-// Mixed path: the operator input must have been sliced by op_prepare into
-// sh->rec / sh->exps (pairing as given there); outputs are pair-stored.
-static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const SlicedOp* Ws,
-                  dim3 extra, cudaStream_t st, int pairing = 0) {
+// FP64 core, or on the mixed path the tcgen05 core with the per-field
+// exponents of the input at exps (op_prepare fills sh->exps); in_pairs: the
+// input is pair-stored.  Mixed-path outputs are pair-stored.
+static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const TcOp* Wt, dim3 extra,
+                  cudaStream_t st, int pairing, bool in_pairs, const int* exps = nullptr) {
   if (a.g.ncols <= 0) return CFFYN_OK;
-  if (sh->d.precision == CFFYN_FP64 || Ws == nullptr) {
+  if (sh->d.precision == CFFYN_FP64 || Wt == nullptr) {
     unsigned gx = (unsigned)((a.g.ncols + F64_QT - 1) / F64_QT);
     unsigned gy = (unsigned)((a.g.P + F64_PT - 1) / F64_PT);
     size_t smem = (size_t)(F64_PT * a.g.K + a.g.K * F64_QT) * sizeof(double);
     k_op_fp64<<<dim3(gx, gy, extra.y), 256, smem, st>>>(a, W64);
-    count_launch();
   } else {
-    unsigned gx = (unsigned)((a.g.ncols + OZ_QT - 1) / OZ_QT);
-    int KP = Ws->ksteps * 16 + 8;
-    size_t smem = (size_t)kSlices * OZ_QT * KP * sizeof(unsigned short);
-    int threads = Ws->mtiles * 32;  // one warp per m-tile
-    k_op_rec<true><<<dim3(gx, extra.y), threads, smem, st>>>(a, *Ws, reinterpret_cast<const uint4*>(sh->rec),
-                                                           sh->exps, pairing);
-    count_launch();
+    const long long tiles = (a.g.ncols + kTcCols - 1) / kTcCols;
+    const dim3 grid((unsigned)(tiles * Wt->ngroups), extra.y);
+    const int* ex = exps ? exps : sh->exps;
+    if (Wt->rows == 48) {
+      if (in_pairs)
+        k_op_tc<true, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
+      else
+        k_op_tc<false, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
+    } else {
+      if (in_pairs)
+        k_op_tc<true, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
+      else
+        k_op_tc<false, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
+    }
   }
+  count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }
 
 int set_op_smem_limits() {
   CF_CUDA(cudaFuncSetAttribute(k_op_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CF_CUDA(cudaFuncSetAttribute(k_op_rec<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<true, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<48>::kSmem));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<false, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<48>::kSmem));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<true, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<96>::kSmem));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<false, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<96>::kSmem));
   return CFFYN_OK;
 }
 
-// Slicing pass of the mixed path (no-op on the FP64 path): per-field
-// exponents of nf fields of len values each, then one digit record per value
-// into sh->rec.  in_pairs: the input is pair-stored.
-int op_prepare(const cffyn_shell* sh, const double* in, bool in_pairs, int nf, long long len, int pairing,
-               cudaStream_t st) {
-  if (sh->d.precision != CFFYN_MIXED) return CFFYN_OK;
-  CF_CUDA(cudaMemsetAsync(sh->exps, 0, sizeof(int) * 64, st));
+// Per-field exponents of nf fields of len values each into exps (64 words,
+// zeroed here: they are atomicMax targets); in_pairs: pair-stored input.
+static int field_exps(const double* in, bool in_pairs, int nf, long long len, int* exps, cudaStream_t st) {
+  CF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * 64, st));
   const long long* x = reinterpret_cast<const long long*>(in);
   const int bx = (int)std::min<long long>((len + 255) / 256, 64);
   if (in_pairs)
-    k_field_exp<true><<<dim3(bx, nf), 256, 0, st>>>(x, len, sh->exps);
+    k_field_exp<true><<<dim3(bx, nf), 256, 0, st>>>(x, len, exps);
   else
-    k_field_exp<false><<<dim3(bx, nf), 256, 0, st>>>(x, len, sh->exps);
-  count_launch();
-  const long long n = (long long)nf * len;
-  const unsigned nb = (unsigned)((n + 255) / 256);
-  uint4* rec = reinterpret_cast<uint4*>(sh->rec);
-  if (in_pairs)
-    k_slice<true><<<nb, 256, 0, st>>>(x, len, n, sh->exps, pairing, rec);
-  else
-    k_slice<false><<<nb, 256, 0, st>>>(x, len, n, sh->exps, pairing, rec);
+    k_field_exp<false><<<dim3(bx, nf), 256, 0, st>>>(x, len, exps);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
+}
+
+// Mixed path (no-op on the FP64 path): the per-field exponents of the next
+// operator input into sh->exps.
+int op_prepare(const cffyn_shell* sh, const double* in, bool in_pairs, int nf, long long len, int pairing,
+               cudaStream_t st) {
+  (void)pairing;  // pairing is applied by the operator kernel
+  if (sh->d.precision != CFFYN_MIXED) return CFFYN_OK;
+  return field_exps(in, in_pairs, nf, len, sh->exps, st);
 }
 
 static OpArgs base_args(const cffyn_shell* sh) {
@@ -636,38 +714,53 @@ static OpArgs base_args(const cffyn_shell* sh) {
   return a;
 }
 
-// d_r of nfields fields: in/out [nfields][P]
-int op_deriv_r(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
-                 cudaStream_t st) {
+// d_r (which = 0), d_theta over the double cover (1), d_phi (2) of nf fields:
+// in/out [nf][P]
+static OpArgs deriv_args(const cffyn_shell* sh, int which, const double* in, double* out, int nf) {
   OpArgs a = base_args(sh);
-  a.kind = OP_R;
   a.in = in;
   a.out = out;
-  a.g.K = a.g.K0 = a.g.P = a.g.P0 = sh->n_r;
-  a.g.in_rs = a.g.out_rs = 1;
-  a.g.ncols = (long long)nfields * sh->J * sh->N;
-  (void)in_pairs;
-  return launch(sh, a, sh->Dr, &sh->sDr, dim3(1, 1), st, 0);
+  if (which == 0) {
+    a.kind = OP_R;
+    a.g.K = a.g.K0 = a.g.P = a.g.P0 = sh->n_r;
+    a.g.in_rs = a.g.out_rs = 1;
+    a.g.ncols = (long long)nf * sh->J * sh->N;
+  } else if (which == 1) {
+    a.kind = OP_THETA;
+    a.g.K = a.g.P = 2 * sh->N;
+    a.g.K0 = a.g.P0 = sh->N;
+    a.g.rev1 = 1;
+    a.g.in_rs = a.g.out_rs = sh->n_r;
+    a.g.ncols = (long long)nf * (sh->J / 2) * sh->n_r;
+  } else {
+    a.kind = OP_ROWS;
+    a.Q = sh->N * sh->n_r;
+    a.in_bs = a.out_bs = (long long)sh->P;
+    a.g.K = a.g.K0 = a.g.P = a.g.P0 = sh->J;
+    a.g.in_rs = a.g.out_rs = a.Q;
+    a.g.ncols = (long long)nf * a.Q;
+  }
+  return a;
+}
+
+int op_deriv_r(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
+               cudaStream_t st) {
+  return launch(sh, deriv_args(sh, 0, in, out, nfields), sh->Dr, &sh->tDr, dim3(1, 1), st, 0, in_pairs);
 }
 
 int op_deriv_theta(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
                    cudaStream_t st) {
-  OpArgs a = base_args(sh);
-  a.kind = OP_THETA;
-  a.in = in;
-  a.out = out;
-  a.g.K = a.g.P = 2 * sh->N;
-  a.g.K0 = a.g.P0 = sh->N;
-  a.g.rev1 = 1;
-  a.g.in_rs = a.g.out_rs = sh->n_r;
-  a.g.ncols = (long long)nfields * (sh->J / 2) * sh->n_r;
-  (void)in_pairs;
-  return launch(sh, a, sh->Dth2, &sh->sDth2, dim3(1, 1), st, 0);
+  return launch(sh, deriv_args(sh, 1, in, out, nfields), sh->Dth2, &sh->tDth2, dim3(1, 1), st, 0, in_pairs);
+}
+
+int op_deriv_phi(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
+                 cudaStream_t st) {
+  return launch(sh, deriv_args(sh, 2, in, out, nfields), sh->Dph, &sh->tDph, dim3(1, 1), st, 0, in_pairs);
 }
 
 static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb, int K, int P,
-                   long long in_bs, long long out_bs, const double* W, const SlicedOp* Ws,
-                   cudaStream_t st, int pairing) {
+                   long long in_bs, long long out_bs, const double* W, const TcOp* Wt, cudaStream_t st,
+                   int pairing) {
   OpArgs a = base_args(sh);
   a.kind = OP_ROWS;
   a.in = in;
@@ -679,27 +772,20 @@ static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb,
   a.g.P = a.g.P0 = P;
   a.g.in_rs = a.g.out_rs = a.Q;
   a.g.ncols = (long long)nb * a.Q;
-  return launch(sh, a, W, Ws, dim3(1, 1), st, pairing);
+  return launch(sh, a, W, Wt, dim3(1, 1), st, pairing, true);
 }
 
-int op_deriv_phi(const cffyn_shell* sh, const double* in, double* out, int nfields, bool in_pairs,
-                 cudaStream_t st) {
-  long long bs = (long long)sh->P;
-  (void)in_pairs;
-  return op_rows(sh, in, out, nfields, sh->J, sh->J, bs, bs, sh->Dph, &sh->sDph, st, 0);
-}
-
-// phi analysis: S[f][j][i][k] -> C[f][row][i][k]
+// phi analysis: S[f][j][i][k] -> C[f][row][i][k] (pair-stored input on the mixed path)
 int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
   long long Q = (long long)sh->N * sh->n_r;
   return op_rows(sh, in, out, nf, sh->J, sh->R, (long long)sh->J * Q, (long long)sh->R * Q, sh->Fan,
-                 &sh->sFan, st, 1);
+                 &sh->tFan, st, 1);
 }
 
 int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
   long long Q = (long long)sh->N * sh->n_r;
   return op_rows(sh, in, out, nf, sh->R, sh->J, (long long)sh->R * Q, (long long)sh->J * Q, sh->Fsy,
-                 &sh->sFsy, st, 1);
+                 &sh->tFsy, st, 1);
 }
 
 // Projection of all spin classes, coefficients C -> C2 (same layout); one
@@ -720,7 +806,7 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     a.g.K = a.g.K0 = a.g.P = a.g.P0 = N;
     a.g.in_rs = a.g.out_rs = sh->n_r;
     a.g.ncols = (long long)n_r0 * 2 * sh->n_r;
-    int rc = launch(sh, a, sh->Fproj0, &sh->sF0, dim3(1, nm), st, 1);
+    int rc = launch(sh, a, sh->Fproj0, &sh->tF0, dim3(1, nm), st, 1, true);
     if (rc) return rc;
   }
   for (int s = 0; s < 3; ++s) {
@@ -738,66 +824,28 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     b.g.P = b.g.P0 = N;
     b.g.in_rs = b.g.out_rs = sh->n_r;
     b.g.ncols = (long long)n_c[s] * 4 * sh->n_r;
-    int rc = launch(sh, b, sh->FprojC + (size_t)s * nm * N * 2 * N, &sh->sFC[s], dim3(1, nm), st, 1);
+    int rc = launch(sh, b, sh->FprojC + (size_t)s * nm * N * 2 * N, &sh->tFC[s], dim3(1, nm), st, 1, true);
     if (rc) return rc;
   }
   return CFFYN_OK;
 }
 
 // Spherical derivatives of nf fields (FP64 input) into D = [3][nf][P], with the
-// mixed path's digit records (16 bytes per value, nf * P of them) and field
-// exponents (64 ints) at the given device addresses instead of the shell's
-// workspace.  exps is zeroed here on st: its words are atomicMax targets.  The
-// FP64 path uses neither.  Same kernels and arithmetic as op_prepare followed
-// by op_deriv_r / op_deriv_theta / op_deriv_phi.
-int op_derivs_at(const cffyn_shell* sh, const double* u, double* D, int nf, uint4* rec, int* exps,
-                 cudaStream_t st) {
+// mixed path's per-field exponents (64 ints) at exps instead of the shell's
+// workspace; exps is zeroed here on st (its words are atomicMax targets).  The
+// FP64 path does not use it.  Same kernels and arithmetic as op_prepare
+// followed by op_deriv_r / op_deriv_theta / op_deriv_phi.
+int op_derivs_at(const cffyn_shell* sh, const double* u, double* D, int nf, int* exps, cudaStream_t st) {
   const long long P = (long long)sh->P;
-  if (sh->d.precision != CFFYN_MIXED) {
-    int rc;
-    if ((rc = op_deriv_r(sh, u, D, nf, false, st))) return rc;
-    if ((rc = op_deriv_theta(sh, u, D + nf * P, nf, false, st))) return rc;
-    return op_deriv_phi(sh, u, D + 2 * nf * P, nf, false, st);
-  }
-  CF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * 64, st));
-  const long long* x = reinterpret_cast<const long long*>(u);
-  const int bx = (int)std::min<long long>((P + 255) / 256, 64);
-  k_field_exp<false><<<dim3(bx, nf), 256, 0, st>>>(x, P, exps);
-  count_launch();
-  const long long n = (long long)nf * P;
-  k_slice<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, P, n, exps, 0, rec);
-  count_launch();
-  CF_CUDA(cudaGetLastError());
-
-  OpArgs a[3] = {base_args(sh), base_args(sh), base_args(sh)};
-  const SlicedOp* W[3] = {&sh->sDr, &sh->sDth2, &sh->sDph};
-  a[0].kind = OP_R;                                    // as op_deriv_r
-  a[0].g.K = a[0].g.K0 = a[0].g.P = a[0].g.P0 = sh->n_r;
-  a[0].g.in_rs = a[0].g.out_rs = 1;
-  a[0].g.ncols = (long long)nf * sh->J * sh->N;
-  a[1].kind = OP_THETA;                                // as op_deriv_theta
-  a[1].g.K = a[1].g.P = 2 * sh->N;
-  a[1].g.K0 = a[1].g.P0 = sh->N;
-  a[1].g.rev1 = 1;
-  a[1].g.in_rs = a[1].g.out_rs = sh->n_r;
-  a[1].g.ncols = (long long)nf * (sh->J / 2) * sh->n_r;
-  a[2].kind = OP_ROWS;                                 // as op_deriv_phi
-  a[2].Q = sh->N * sh->n_r;
-  a[2].in_bs = a[2].out_bs = P;
-  a[2].g.K = a[2].g.K0 = a[2].g.P = a[2].g.P0 = sh->J;
-  a[2].g.in_rs = a[2].g.out_rs = a[2].Q;
-  a[2].g.ncols = (long long)nf * a[2].Q;
-  for (int i = 0; i < 3; ++i) {
-    a[i].in = u;
-    a[i].out = D + i * nf * P;
-    if (a[i].g.ncols <= 0) continue;
-    const unsigned gx = (unsigned)((a[i].g.ncols + OZ_QT - 1) / OZ_QT);
-    const int KP = W[i]->ksteps * 16 + 8;
-    const size_t smem = (size_t)kSlices * OZ_QT * KP * sizeof(unsigned short);
-    k_op_rec<true><<<dim3(gx, 1), W[i]->mtiles * 32, smem, st>>>(a[i], *W[i], rec, exps, 0);
-    count_launch();
-    CF_CUDA(cudaGetLastError());
-  }
+  const bool mixed = sh->d.precision == CFFYN_MIXED;
+  int rc;
+  if (mixed && (rc = field_exps(u, false, nf, P, exps, st))) return rc;
+  const double* W64[3] = {sh->Dr, sh->Dth2, sh->Dph};
+  const TcOp* Wt[3] = {&sh->tDr, &sh->tDth2, &sh->tDph};
+  for (int i = 0; i < 3; ++i)
+    if ((rc = launch(sh, deriv_args(sh, i, u, D + i * nf * P, nf), W64[i], Wt[i], dim3(1, 1), st, 0, false,
+                     exps)))
+      return rc;
   return CFFYN_OK;
 }
 

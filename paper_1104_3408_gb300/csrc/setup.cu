@@ -337,81 +337,67 @@ __global__ void k_slice_rows(const double* A, int P, int K, int ld, int* rowexp)
   rowexp[p] = (E == -2000) ? 0 : E;
 }
 
-__device__ __forceinline__ unsigned short bf16_of_small_int(int d) {
-  float f = (float)d;  // exact, |d| <= 128 (create time only)
-  return (unsigned short)(__float_as_uint(f) >> 16);
-}
-
-__global__ void k_slice_frag(const double* A, int P, int K, int ld, const int* rowexp, uint4* frag,
-                             int mtiles, int ksteps) {
-  // one thread per (slice, mtile, kstep, lane)
-  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  size_t total = (size_t)kSlices * mtiles * ksteps * 32;
+// One thread per BF16 value of the tcgen05 operator layout (see TcOp).
+__global__ void k_tc_pack(const double* A, int P, int K, int ld, const int* rowexp, unsigned short* w,
+                          int rows, int ksteps, size_t total) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= total) return;
-  int lane = (int)(t % 32);
-  size_t r = t / 32;
-  int ks = (int)(r % ksteps);
-  r /= ksteps;
-  int mt = (int)(r % mtiles);
-  int sl = (int)(r / mtiles);
-  int g = lane >> 2, tg = lane & 3;
-  auto digit = [&](int row, int col) -> unsigned short {
-    if (row >= P || col >= K) return 0;
-    double v = A[(size_t)row * ld + col];
-    int E = rowexp[row];
-    double z = rint(ldexp(v, 47 - E));
-    long long Z = (long long)z;
-    int d[kSlices];
-    for (int i = kSlices - 1; i >= 1; --i) {
-      long long lo = ((Z % 256) + 256) % 256;  // 0..255
-      if (lo >= 128) lo -= 256;
-      d[i] = (int)lo;
-      Z = (Z - lo) / 256;
-    }
-    d[0] = (int)Z;
-    return bf16_of_small_int(d[sl]);
-  };
-  int r0 = mt * 16 + g, c0 = ks * 16 + 2 * tg;
-  auto pack = [&](int row, int col) -> unsigned int {
-    return (unsigned int)digit(row, col) | ((unsigned int)digit(row, col + 1) << 16);
-  };
-  uint4 q;
-  q.x = pack(r0, c0);
-  q.y = pack(r0 + 8, c0);
-  q.z = pack(r0, c0 + 8);
-  q.w = pack(r0 + 8, c0 + 8);
-  frag[t] = q;
+  const int blk = (int)(t % (rows * 16));
+  size_t r = t / (rows * 16);
+  const int q = (int)(r % kTcWSlices);
+  r /= kTcWSlices;
+  const int ks = (int)(r % ksteps);
+  const int grp = (int)(r / ksteps);
+  const int core = blk >> 6, rg = core >> 1, kh = core & 1, rr = (blk >> 3) & 7, kk = blk & 7;
+  const int row = grp * rows + rg * 8 + rr, col = ks * 16 + kh * 8 + kk;
+  if (row >= P || col >= K) {
+    w[t] = 0;
+    return;
+  }
+  const double v = A[(size_t)row * ld + col];
+  long long Z = (long long)rint(ldexp(v, 47 - rowexp[row]));
+  int d[kSlices];
+  for (int i = kSlices - 1; i >= 1; --i) {
+    long long lo = ((Z % 256) + 256) % 256;
+    if (lo >= 128) lo -= 256;
+    d[i] = (int)lo;
+    Z = (Z - lo) / 256;
+  }
+  d[0] = (int)Z;
+  float f = (float)(q < 5 ? d[q] : d[q - 5]);  // exact, |d| <= 128
+  if (q >= 5) f *= 0.00390625f;                 // 2^-8, exact
+  w[t] = (unsigned short)(__float_as_uint(f) >> 16);
 }
 
-// Digits of nbatch operators A + b * a_stride (each P x K, leading dim ld).
-int build_sliced(SlicedOp& s, const double* A, int P, int K, int ld, size_t& bytes, int nbatch = 1,
-                 size_t a_stride = 0) {
+int build_tc(TcOp& s, const double* A, int P, int K, int ld, size_t& bytes, int nbatch = 1,
+             size_t a_stride = 0) {
   s.P = P;
   s.K = K;
-  s.mtiles = (P + 15) / 16;
+  s.rows = P <= 48 ? 48 : 96;
+  s.ngroups = (P + s.rows - 1) / s.rows;
   s.ksteps = (K + 15) / 16;
   s.nbatch = nbatch;
-  s.frag_stride = (size_t)kSlices * s.mtiles * s.ksteps * 32;
-  s.rowexp_stride = (size_t)s.mtiles * 16;
-  CF_CUDA(cudaMalloc(&s.frag, s.frag_stride * nbatch * sizeof(uint4)));
+  s.w_stride = (size_t)s.ngroups * s.ksteps * kTcWSlices * s.rows * 16;
+  s.rowexp_stride = (size_t)s.ngroups * s.rows;
+  CF_CUDA(cudaMalloc(&s.w, s.w_stride * nbatch * sizeof(unsigned short)));
   CF_CUDA(cudaMalloc(&s.rowexp, s.rowexp_stride * nbatch * sizeof(int)));
-  bytes += s.frag_stride * nbatch * sizeof(uint4) + s.rowexp_stride * nbatch * sizeof(int);
+  CF_CUDA(cudaMemset(s.rowexp, 0, s.rowexp_stride * nbatch * sizeof(int)));
+  bytes += s.w_stride * nbatch * sizeof(unsigned short) + s.rowexp_stride * nbatch * sizeof(int);
   for (int b = 0; b < nbatch; ++b) {
     const double* Ab = A + (size_t)b * a_stride;
     int* re = s.rowexp + (size_t)b * s.rowexp_stride;
-    uint4* fr = s.frag + (size_t)b * s.frag_stride;
-    k_slice_rows<<<(s.mtiles * 16 + 127) / 128, 128>>>(Ab, P, K, ld, re);
-    k_slice_frag<<<(unsigned)((s.frag_stride + 255) / 256), 256>>>(Ab, P, K, ld, re, fr, s.mtiles,
-                                                                   s.ksteps);
+    k_slice_rows<<<(unsigned)((s.rowexp_stride + 127) / 128), 128>>>(Ab, P, K, ld, re);
+    k_tc_pack<<<(unsigned)((s.w_stride + 255) / 256), 256>>>(Ab, P, K, ld, re, s.w + (size_t)b * s.w_stride,
+                                                             s.rows, s.ksteps, s.w_stride);
   }
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }
 
-void free_sliced(SlicedOp& s) {
-  if (s.frag) cudaFree(s.frag);
+void free_tc(TcOp& s) {
+  if (s.w) cudaFree(s.w);
   if (s.rowexp) cudaFree(s.rowexp);
-  s.frag = nullptr;
+  s.w = nullptr;
   s.rowexp = nullptr;
 }
 
@@ -461,15 +447,15 @@ int build_operators(cffyn_shell* sh) {
 
   // split-precision digits of every operator (used by the mixed path)
   if (sh->d.precision == CFFYN_MIXED) {
-    if ((rc = build_sliced(sh->sDr, sh->Dr, n_r, n_r, n_r, B))) return rc;
-    if ((rc = build_sliced(sh->sDth2, sh->Dth2, 2 * N, 2 * N, 2 * N, B))) return rc;
-    if ((rc = build_sliced(sh->sDph, sh->Dph, J, J, J, B))) return rc;
-    if ((rc = build_sliced(sh->sFan, sh->Fan, R, J, J, B))) return rc;
-    if ((rc = build_sliced(sh->sFsy, sh->Fsy, J, R, R, B))) return rc;
-    if ((rc = build_sliced(sh->sF0, sh->Fproj0, N, N, N, B, nm, (size_t)N * N))) return rc;
+    if ((rc = build_tc(sh->tDr, sh->Dr, n_r, n_r, n_r, B))) return rc;
+    if ((rc = build_tc(sh->tDth2, sh->Dth2, 2 * N, 2 * N, 2 * N, B))) return rc;
+    if ((rc = build_tc(sh->tDph, sh->Dph, J, J, J, B))) return rc;
+    if ((rc = build_tc(sh->tFan, sh->Fan, R, J, J, B))) return rc;
+    if ((rc = build_tc(sh->tFsy, sh->Fsy, J, R, R, B))) return rc;
+    if ((rc = build_tc(sh->tF0, sh->Fproj0, N, N, N, B, nm, (size_t)N * N))) return rc;
     for (int s = 0; s < 3; ++s)
-      if ((rc = build_sliced(sh->sFC[s], sh->FprojC + (size_t)s * nm * N * 2 * N, N, 2 * N, 2 * N, B,
-                             nm, (size_t)N * 2 * N)))
+      if ((rc = build_tc(sh->tFC[s], sh->FprojC + (size_t)s * nm * N * 2 * N, N, 2 * N, 2 * N, B, nm,
+                         (size_t)N * 2 * N)))
         return rc;
     CF_CUDA(cudaDeviceSynchronize());
   }

@@ -10,7 +10,7 @@
 
 namespace cffyn {
 // ops.cu
-int op_derivs_at(const cffyn_shell*, const double*, double*, int, uint4*, int*, cudaStream_t);
+int op_derivs_at(const cffyn_shell*, const double*, double*, int, int*, cudaStream_t);
 // pointwise.cu
 int pw_cart(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 }  // namespace cffyn
@@ -21,8 +21,8 @@ namespace {
 
 // One array per device, reserved when the module's device code is loaded
 // there.  Layout of one call: spherical derivatives [3][n_f][P] (8 bytes per
-// value on both paths), then on the mixed path the digit records (16 bytes per
-// value) and the 64 per-field exponent words, each part 256-byte aligned.
+// value on both paths), then on the mixed path the 64 per-field exponent
+// words, 256-byte aligned.
 __device__ __align__(256) unsigned char g_static_scratch[CFFYN_STATIC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -72,8 +72,7 @@ extern "C" int cffyn_derivs_static(const cffyn_shell* sh, const double* u, int n
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   const size_t vals = (size_t)n_f * sh->P;
   const size_t d_bytes = round256(3 * vals * sizeof(double));
-  const size_t rec_bytes = mixed ? round256(16 * vals) : 0;
-  const size_t need = d_bytes + rec_bytes + (mixed ? 256 : 0);
+  const size_t need = d_bytes + (mixed ? 256 : 0);
   if (need > (size_t)CFFYN_STATIC_SCRATCH_BYTES) {
     set_error("cffyn_derivs_static: %d fields of %zu points need %zu bytes of static scratch; "
               "the limit is %zu bytes",
@@ -91,9 +90,8 @@ extern "C" int cffyn_derivs_static(const cffyn_shell* sh, const double* u, int n
   int rc;
   if ((rc = scratch_address(dev, &base))) return rc;
   double* D = reinterpret_cast<double*>(base);
-  uint4* rec = mixed ? reinterpret_cast<uint4*>(base + d_bytes) : nullptr;
-  int* exps = mixed ? reinterpret_cast<int*>(base + d_bytes + rec_bytes) : nullptr;
+  int* exps = mixed ? reinterpret_cast<int*>(base + d_bytes) : nullptr;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = op_derivs_at(sh, u, D, n_f, rec, exps, st))) return rc;
+  if ((rc = op_derivs_at(sh, u, D, n_f, exps, st))) return rc;
   return pw_cart(sh, D, dxyz, n_f, false, st);
 }

@@ -37,7 +37,7 @@ def rel(got, ref):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("n_r,N,J,L,n_f", [(9, 12, 24, 10, 50), (13, 9, 18, 6, 7), (33, 32, 64, 30, 3)])
+@pytest.mark.parametrize("n_r,N,J,L,n_f", [(9, 12, 24, 10, 50), (13, 9, 18, 6, 7), (33, 32, 64, 30, 5)])
 def test_static_derivs_match_derivs_on_two_calls(cf, prec, n_r, N, J, L, n_f):
     sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec)
     P = n_r * N * J
@@ -61,7 +61,7 @@ def test_static_derivs_match_derivs_on_two_calls(cf, prec, n_r, N, J, L, n_f):
     sh.destroy()
 
 
-@pytest.mark.parametrize("prec,n_ok", [(0, 5), (1, 3)])
+@pytest.mark.parametrize("prec,n_ok", [(0, 5), (1, 5)])
 def test_static_derivs_reject_requests_above_the_limit(cf, prec, n_ok):
     n_r, N, J, L = 33, 32, 64, 30
     sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec)
