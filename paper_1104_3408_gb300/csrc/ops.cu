@@ -459,6 +459,46 @@ __device__ __forceinline__ long long fold_pair(float a0, float a1, float a2, flo
   return (long long)(((unsigned long long)__float_as_uint(lo) << 32) | __float_as_uint(hi));
 }
 
+// Digit slices of a float pair x = hi + lo (|lo| < ulp(hi), |x| < 2^E) on the
+// FMA pipe.  Digit j has weight 2^(E - 7 - 8j) (the balanced base-256 digits
+// of round(x 2^(47 - E))).  For a float v and each j the exact steps
+//   d = rint(v / w_j) (one FFMA against 1.5 * 2^23),  v -= d w_j  (exact FFMA)
+// give balanced digits |d| <= 128 of v; the last digit rounds like the
+// fixed-point conversion.  lo contributes to digits 3..5 only (|lo| / w_2 < 1/2),
+// so digit j is d_j(hi) + d_j(lo), |.| <= 256, an exact BF16 value; it is the
+// same integer sum of weights as the rounded fixed point of hi plus that of lo.
+// Requires -78 <= E <= 126 (every weight and inverse weight a normal float).
+struct DigitScale {
+  float w[kSlices], inv[kSlices];
+};
+
+__device__ __forceinline__ DigitScale digit_scale(int E) {
+  DigitScale c;
+#pragma unroll
+  for (int j = 0; j < kSlices; ++j) {
+    c.w[j] = __int_as_float((E - 7 - 8 * j + 127) << 23);
+    c.inv[j] = __int_as_float((7 + 8 * j - E + 127) << 23);
+  }
+  return c;
+}
+
+__device__ __forceinline__ void digits_pair_f32(long long wbits, const DigitScale& c, float (&d)[kSlices]) {
+  constexpr float M = 12582912.0f;  // 1.5 * 2^23
+  float v = __int_as_float((int)(unsigned int)wbits);
+  float u = __int_as_float((int)(unsigned int)((unsigned long long)wbits >> 32));
+#pragma unroll
+  for (int j = 0; j < kSlices; ++j) {
+    d[j] = __fsub_rn(__fmaf_rn(v, c.inv[j], M), M);
+    if (j < kSlices - 1) v = __fmaf_rn(-d[j], c.w[j], v);
+  }
+#pragma unroll
+  for (int j = 3; j < kSlices; ++j) {
+    const float e = __fsub_rn(__fmaf_rn(u, c.inv[j], M), M);
+    if (j < kSlices - 1) u = __fmaf_rn(-e, c.w[j], u);
+    d[j] = __fadd_rn(d[j], e);
+  }
+}
+
 __device__ __forceinline__ void bar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(b)) : "memory");
 }
@@ -507,6 +547,8 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
   if (producer) {
     // byte offset of this thread's row piece (column ctile, k kq..kq+KQ-1)
     const int xoff = (ctile >> 3) * 256 + (kq >> 3) * 128 + (ctile & 7) * 16 + (kq & 7) * 2;
+    const bool fscale = E >= -78 && E <= 126;  // FMA-pipe slicing of float pairs
+    const DigitScale dsc = digit_scale(fscale ? E : 0);
     long long nxt[KQ];
     gather<FI, KQ>(a, col, kq, nxt);
     for (int ks = 0; ks < ksteps; ++ks) {
@@ -518,7 +560,18 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
       if (ks >= S && ok) ok = tc::bar_wait(&empty[s], ((ks - S) / S) & 1, kTcWaitNs);
       unsigned char* xs = smtc + s * C::kStage + xoff;
       uint32_t wd[kSlices][KQ / 2];
-      if (ks * 16 + kq < a.g.K) {
+      if (FI && fscale && ks * 16 + kq < a.g.K) {
+#pragma unroll
+        for (int i = 0; i < KQ; i += 2) {
+          float f0[kSlices], f1[kSlices];
+          digits_pair_f32(cur[i], dsc, f0);
+          digits_pair_f32(cur[i + 1], dsc, f1);
+          // BF16 of an 8-bit integer float: its upper half
+#pragma unroll
+          for (int j = 0; j < kSlices; ++j)
+            wd[j][i >> 1] = __byte_perm(__float_as_uint(f0[j]), __float_as_uint(f1[j]), 0x7632);
+        }
+      } else if (ks * 16 + kq < a.g.K) {
 #pragma unroll
         for (int i = 0; i < KQ; i += 2) {
           unsigned int d0[kSlices], d1[kSlices];
