@@ -35,22 +35,44 @@ __device__ __forceinline__ void stA(double* a, long long P, long long p, int f, 
 template <class T> constexpr bool kInt = false;
 template <> constexpr bool kInt<ff> = true;
 
+// Per-thread working tensors that rolled loops index at run time live in
+// shared memory as [slot][thread] (consecutive threads, consecutive words: no
+// bank conflicts); the outer contraction loops stay rolled so that the code
+// of a kernel fits the instruction caches, the inner ones unrolled so that
+// independent accumulations overlap.
+template <class T, int NB>
+struct Slots {
+  T* s;
+  __device__ __forceinline__ T& operator()(int v) const { return s[v * NB + (int)threadIdx.x]; }
+};
+
+constexpr int kRhsBlock = 64;
+constexpr int kGamSlots = 64;   // Gamma_cab (c*10 + s) | S_Pi 40..49 | g_ab 50..59 | C_a 60..63
+constexpr int kQuadSlots = 50;  // Pi 0..9 | Phi_iab 10 + 10 i + s | Q 40..49
+
 template <class T, bool FU, bool FO>
-__global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
-                                                   const double* __restrict__ H,
-                                                   const double* __restrict__ dH,
-                                                   double* __restrict__ src, double* __restrict__ out,
-                                                   Geo geo) {
+__global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restrict__ u,
+                                                         const double* __restrict__ H,
+                                                         const double* __restrict__ dH,
+                                                         double* __restrict__ src, double* __restrict__ out,
+                                                         Geo geo) {
+  __shared__ T sm[kGamSlots * kRhsBlock];
+  const Slots<T, kRhsBlock> V{sm};
   const long long P = geo.P;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
   const T zero = S<T>::c(0.0), half = S<T>::c(0.5);
 
-  T g[10];
-#pragma unroll
-  for (int s = 0; s < 10; ++s) g[s] = ldA<T, FU>(u, P, p, s);
   Metric<T> M;
-  metric_from(g, M);
+  {
+    T g[10];
+#pragma unroll
+    for (int s = 0; s < 10; ++s) {
+      g[s] = ldA<T, FU>(u, P, p, s);
+      V(50 + s) = g[s];
+    }
+    metric_from(g, M);
+  }
   stA<T, kInt<T>>(src, P, p, 40, M.alpha);
 #pragma unroll
   for (int x = 0; x < 3; ++x) stA<T, kInt<T>>(src, P, p, 41 + x, M.bu[x]);
@@ -61,8 +83,7 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
   stA<T, kInt<T>>(src, P, p, 48, M.gi[1][2]);
   stA<T, kInt<T>>(src, P, p, 49, M.gi[2][2]);
 
-  // d_t g_ab (eq. gdot) and the Christoffel symbols
-  T Gam[4][10];
+  // d_t g_ab (eq. gdot) and the Christoffel symbols Gamma_cab
   {
     T dtg[10], Ph[3][10];
 #pragma unroll
@@ -83,15 +104,17 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = a; b < 4; ++b)
-          Gam[c][SI(a, b)] = half * (dg4(a, SI(b, c)) + dg4(b, SI(a, c)) - dg4(c, SI(a, b)));
+          V(c * 10 + SI(a, b)) = half * (dg4(a, SI(b, c)) + dg4(b, SI(a, c)) - dg4(c, SI(a, b)));
   }
-  // Gamma_c = g^ab Gamma_cab (symmetric pairs counted twice off the diagonal)
-  T C[4], Hup[4], Hd[4];
-  T nC;
+  // Gamma_c = g^ab Gamma_cab (symmetric pairs counted twice off the diagonal);
+  // gauge constraint C_c = H_c + Gamma_c, H^c, n^c C_c
+  T Hup[4], nC;
   {
+    T Hd[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) Hd[a] = ldA<T, kInt<T>>(H, P, p, a);
-#pragma unroll
+    Acc<T> an;
+#pragma unroll 1
     for (int c = 0; c < 4; ++c) {
       Acc<T> acc;
 #pragma unroll
@@ -99,10 +122,11 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
 #pragma unroll
         for (int b = a; b < 4; ++b) {
           const T w = (a == b) ? M.gi4[SI(a, b)] : M.gi4[SI(a, b)] + M.gi4[SI(a, b)];
-          acc.fma_(w, Gam[c][SI(a, b)]);
+          acc.fma_(w, V(c * 10 + SI(a, b)));
         }
-      acc.add(Hd[c]);
-      C[c] = acc.get();
+      const T hc = c == 0 ? Hd[0] : (c == 1 ? Hd[1] : (c == 2 ? Hd[2] : Hd[3]));
+      acc.add(hc);
+      V(60 + c) = acc.get();
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -110,130 +134,145 @@ __global__ void __launch_bounds__(128) k_rhs_gamma(const double* __restrict__ u,
 #pragma unroll
       for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Hd[d]);
       Hup[c] = acc.get();
+      an.fma_(M.nu[c], V(60 + c));
     }
-    Acc<T> acc;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc.fma_(M.nu[c], C[c]);
-    nC = acc.get();
+    nC = an.get();
   }
-  // -2 alpha nabla_(a H_b) + alpha (n_b C_a + n_a C_b - g_ab n^c C_c)
-  T SPi[10];
+  // S_Pi = -2 alpha nabla_(a H_b) + alpha (n_b C_a + n_a C_b - g_ab n^c C_c)
   {
     const T twoal = M.alpha + M.alpha;
-    const T nlo0 = -M.alpha;
+    const T aa = M.alpha * (-M.alpha);  // alpha n_0, n_a = (-alpha, 0, 0, 0)
+    const T anC = M.alpha * nC;
+#pragma unroll 1
+    for (int s = 0; s < 10; ++s) {
+      const int a = s < 4 ? 0 : (s < 7 ? 1 : (s < 9 ? 2 : 3));
+      const int b = s - (a == 0 ? 0 : (a == 1 ? 3 : (a == 2 ? 5 : 6)));
+      const T dHab = a == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (a - 1) * 4 + b);
+      const T dHba = b == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (b - 1) * 4 + a);
+      Acc<T> acc;
+      acc.fma_(half, dHab + dHba);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b) {
-        const int s = SI(a, b);
-        const T dHab = a == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (a - 1) * 4 + b);
-        const T dHba = b == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (b - 1) * 4 + a);
-        Acc<T> acc;
-        acc.fma_(half, dHab + dHba);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc.fma_(-Gam[c][s], Hup[c]);
-        const T DH = acc.get();
-        Acc<T> v;
-        v.fma_(-twoal, DH);
-        v.fma_(-M.alpha * g[s], nC);
-        if (a == 0) v.fma_(M.alpha * nlo0, C[b]);
-        if (b == 0) v.fma_(M.alpha * nlo0, C[a]);
-        SPi[s] = v.get();
-      }
+      for (int c = 0; c < 4; ++c) acc.fma_(-V(c * 10 + s), Hup[c]);
+      const T DH = acc.get();
+      Acc<T> v;
+      v.fma_(-twoal, DH);
+      v.fma_(-(anC), V(50 + s));
+      if (a == 0) v.fma_(aa, V(60 + b));
+      if (b == 0) v.fma_(aa, V(60 + a));
+      V(40 + s) = v.get();
+    }
   }
   // -2 alpha g^cd g^ef Gamma_ace Gamma_bdf
   {
     const T m2al = -(M.alpha + M.alpha);
-#pragma unroll
+#pragma unroll 1
     for (int b = 0; b < 4; ++b) {
-      T Gcf[4][4];  // Gamma_b^c_f = g^cd Gamma_bdf
+      T Gce[10];  // Gamma_b^{ce}, symmetric, off-diagonal weight 2
+      {
+        T Gcf[4][4];  // Gamma_b^c_f = g^cd Gamma_bdf
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          Acc<T> acc;
+          for (int f = 0; f < 4; ++f) {
+            Acc<T> acc;
 #pragma unroll
-          for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Gam[b][SI(d, f)]);
-          Gcf[c][f] = acc.get();
-        }
-      T Gce[10];  // Gamma_b^{ce}, symmetric
+            for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], V(b * 10 + SI(d, f)));
+            Gcf[c][f] = acc.get();
+          }
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int e = c; e < 4; ++e) {
-          Acc<T> acc;
+          for (int e = c; e < 4; ++e) {
+            Acc<T> acc;
 #pragma unroll
-          for (int f = 0; f < 4; ++f) acc.fma_(M.gi4[SI(e, f)], Gcf[c][f]);
-          Gce[SI(c, e)] = (c == e) ? acc.get() : acc.get() + acc.get();  // off-diagonal weight 2
-        }
-#pragma unroll
+            for (int f = 0; f < 4; ++f) acc.fma_(M.gi4[SI(e, f)], Gcf[c][f]);
+            Gce[SI(c, e)] = (c == e) ? acc.get() : acc.get() + acc.get();
+          }
+      }
+#pragma unroll 1
       for (int a = 0; a <= b; ++a) {
+        Acc<T> qa;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int e = c; e < 4; ++e) qa.fma_(V(a * 10 + SI(c, e)), Gce[SI(c, e)]);
         Acc<T> acc;
-        acc.add(SPi[SI(a, b)]);
-        T q = zero;
-        {
-          Acc<T> qa;
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int e = c; e < 4; ++e) qa.fma_(Gam[a][SI(c, e)], Gce[SI(c, e)]);
-          q = qa.get();
-        }
-        acc.fma_(m2al, q);
-        SPi[SI(a, b)] = acc.get();
+        acc.add(V(40 + SI(a, b)));
+        acc.fma_(m2al, qa.get());
+        V(40 + SI(a, b)) = acc.get();
       }
     }
   }
 #pragma unroll
-  for (int s = 0; s < 10; ++s) stA<T, kInt<T>>(src, P, p, s, SPi[s]);
+  for (int s = 0; s < 10; ++s) stA<T, kInt<T>>(src, P, p, s, V(40 + s));
 }
 
+// The Phi-Phi and Pi-Pi terms of eq. Pidot and the remaining algebraic terms
+// of eqs. Pidot and Phidot; alpha, beta^i, gamma^ij come from k_rhs_gamma.
 template <class T, bool FU>
-__global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, double* __restrict__ src,
-                                                  Geo geo) {
+__global__ void __launch_bounds__(kRhsBlock) k_rhs_quad(const double* __restrict__ u, double* __restrict__ src,
+                                                        Geo geo) {
+  __shared__ T sm[kQuadSlots * kRhsBlock];
+  const Slots<T, kRhsBlock> V{sm};
   const long long P = geo.P;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const T zero = S<T>::c(0.0), half = S<T>::c(0.5);
-  T g[10], Pi[10], Ph[3][10];
+  const T half = S<T>::c(0.5);
+  // 3+1 quantities (eqs. normal, abgfromgab) as k_rhs_gamma derived them
+  const T alpha = ldA<T, kInt<T>>(src, P, p, 40);
+  T bu[3], gi[3][3];
 #pragma unroll
-  for (int s = 0; s < 10; ++s) g[s] = ldA<T, FU>(u, P, p, s);
-  Metric<T> M;
-  metric_from(g, M);
+  for (int x = 0; x < 3; ++x) bu[x] = ldA<T, kInt<T>>(src, P, p, 41 + x);
+  gi[0][0] = ldA<T, kInt<T>>(src, P, p, 44);
+  gi[0][1] = gi[1][0] = ldA<T, kInt<T>>(src, P, p, 45);
+  gi[0][2] = gi[2][0] = ldA<T, kInt<T>>(src, P, p, 46);
+  gi[1][1] = ldA<T, kInt<T>>(src, P, p, 47);
+  gi[1][2] = gi[2][1] = ldA<T, kInt<T>>(src, P, p, 48);
+  gi[2][2] = ldA<T, kInt<T>>(src, P, p, 49);
+  const T ialpha = S<T>::c(1.0) / alpha;
+  const T ia2 = ialpha * ialpha;
+  T nu[4], gi4[10];
+  nu[0] = ialpha;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) nu[i + 1] = -(bu[i] * ialpha);
+  gi4[0] = -ia2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) gi4[SI(0, i + 1)] = bu[i] * ia2;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) gi4[SI(i + 1, j + 1)] = gi[i][j] - bu[i] * bu[j] * ia2;
+
 #pragma unroll
   for (int s = 0; s < 10; ++s) {
-    Pi[s] = ldA<T, FU>(u, P, p, 10 + s);
+    V(s) = ldA<T, FU>(u, P, p, 10 + s);
 #pragma unroll
-    for (int x = 0; x < 3; ++x) Ph[x][s] = ldA<T, FU>(u, P, p, 20 + 10 * x + s);
+    for (int x = 0; x < 3; ++x) V(10 + 10 * x + s) = ldA<T, FU>(u, P, p, 20 + 10 * x + s);
   }
-  const T twoal = M.alpha + M.alpha;
-  T Q[10];  // Q1 - Q2
-  // Q2_ab = Pi_ac g^cd Pi_db
-  {
-    T Piu[4][4];
+  const T twoal = alpha + alpha;
+  // Q = Q1 - Q2 into slots 40..49; Q2_ab = Pi_ac g^cd Pi_db
+#pragma unroll 1
+  for (int b = 0; b < 4; ++b) {
+    T Piu[4];
 #pragma unroll
-    for (int b = 0; b < 4; ++b)
+    for (int c = 0; c < 4; ++c) {
+      Acc<T> acc;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        Acc<T> acc;
+      for (int d = 0; d < 4; ++d) acc.fma_(gi4[SI(c, d)], V(SI(b, d)));
+      Piu[c] = acc.get();
+    }
+#pragma unroll 1
+    for (int a = 0; a <= b; ++a) {
+      Acc<T> acc;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Pi[SI(b, d)]);
-        Piu[b][c] = acc.get();
-      }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = a; b < 4; ++b) {
-        Acc<T> acc;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc.fma_(-Pi[SI(a, c)], Piu[b][c]);
-        Q[SI(a, b)] = acc.get();
-      }
+      for (int c = 0; c < 4; ++c) acc.fma_(-V(SI(a, c)), Piu[c]);
+      V(40 + SI(a, b)) = acc.get();
+    }
   }
   // Q1_ab = gamma^ij g^cd Phi_iac Phi_jbd
-#pragma unroll
+#pragma unroll 1
   for (int b = 0; b < 4; ++b) {
-    T V[3][4];
+    T W[3][4];
     {
       T Y[3][4];
 #pragma unroll
@@ -242,7 +281,7 @@ __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, 
         for (int c = 0; c < 4; ++c) {
           Acc<T> acc;
 #pragma unroll
-          for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Ph[x][SI(b, d)]);
+          for (int d = 0; d < 4; ++d) acc.fma_(gi4[SI(c, d)], V(10 + 10 * x + SI(b, d)));
           Y[x][c] = acc.get();
         }
 #pragma unroll
@@ -251,19 +290,19 @@ __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, 
         for (int c = 0; c < 4; ++c) {
           Acc<T> acc;
 #pragma unroll
-          for (int y = 0; y < 3; ++y) acc.fma_(M.gi[x][y], Y[y][c]);
-          V[x][c] = acc.get();
+          for (int y = 0; y < 3; ++y) acc.fma_(gi[x][y], Y[y][c]);
+          W[x][c] = acc.get();
         }
     }
-#pragma unroll
+#pragma unroll 1
     for (int a = 0; a <= b; ++a) {
       Acc<T> acc;
-      acc.add(Q[SI(a, b)]);
+      acc.add(V(40 + SI(a, b)));
 #pragma unroll
       for (int x = 0; x < 3; ++x)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc.fma_(Ph[x][SI(a, c)], V[x][c]);
-      Q[SI(a, b)] = acc.get();
+        for (int c = 0; c < 4; ++c) acc.fma_(V(10 + 10 * x + SI(a, c)), W[x][c]);
+      V(40 + SI(a, b)) = acc.get();
     }
   }
   // remaining algebraic terms of eq. Pidot
@@ -273,40 +312,41 @@ __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, 
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int d = 0; d < 4; ++d) acc.fma_(M.nu[c] * M.nu[d], Pi[SI(c, d)]);
+      for (int d = 0; d < 4; ++d) acc.fma_(nu[c] * nu[d], V(SI(c, d)));
     nnPi = acc.get();
   }
-  T Vj[3];  // n^c Pi_ci gamma^ij
+  T cPh[3];  // beta^j - alpha n^c Pi_ci gamma^ij
   {
     T nPi[3];
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
       Acc<T> acc;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc.fma_(M.nu[c], Pi[SI(c, x + 1)]);
+      for (int c = 0; c < 4; ++c) acc.fma_(nu[c], V(SI(c, x + 1)));
       nPi[x] = acc.get();
     }
 #pragma unroll
     for (int y = 0; y < 3; ++y) {
       Acc<T> acc;
 #pragma unroll
-      for (int x = 0; x < 3; ++x) acc.fma_(nPi[x], M.gi[x][y]);
-      Vj[y] = acc.get();
+      for (int x = 0; x < 3; ++x) acc.fma_(nPi[x], gi[x][y]);
+      cPh[y] = bu[y] - alpha * acc.get();
     }
   }
-  const T hal = half * M.alpha;
-#pragma unroll
+  const T hal = half * alpha;
+  const T cPi = -(hal * nnPi);
+#pragma unroll 1
   for (int s = 0; s < 10; ++s) {
     Acc<T> acc;
     acc.add(ldA<T, kInt<T>>(src, P, p, s));
-    acc.fma_(twoal, Q[s]);
-    acc.fma_(-(hal * nnPi), Pi[s]);
+    acc.fma_(twoal, V(40 + s));
+    acc.fma_(cPi, V(s));
 #pragma unroll
-    for (int x = 0; x < 3; ++x) acc.fma_(M.bu[x] - M.alpha * Vj[x], Ph[x][s]);
+    for (int x = 0; x < 3; ++x) acc.fma_(cPh[x], V(10 + 10 * x + s));
     stA<T, kInt<T>>(src, P, p, s, acc.get());
   }
   // algebraic terms of eq. Phidot
-#pragma unroll
+#pragma unroll 1
   for (int x = 0; x < 3; ++x) {
     T nnPhi;
     {
@@ -314,39 +354,38 @@ __global__ void __launch_bounds__(128) k_rhs_quad(const double* __restrict__ u, 
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int d = 0; d < 4; ++d) acc.fma_(M.nu[c] * M.nu[d], Ph[x][SI(c, d)]);
+        for (int d = 0; d < 4; ++d) acc.fma_(nu[c] * nu[d], V(10 + 10 * x + SI(c, d)));
       nnPhi = acc.get();
     }
-    T Mk[3];  // gamma^jk n^c Phi_x,j,c
+    T Mk[3];  // alpha gamma^jk n^c Phi_x,j,c
     {
       T nP[3];
 #pragma unroll
       for (int y = 0; y < 3; ++y) {
         Acc<T> acc;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc.fma_(M.nu[c], Ph[x][SI(y + 1, c)]);
+        for (int c = 0; c < 4; ++c) acc.fma_(nu[c], V(10 + 10 * x + SI(y + 1, c)));
         nP[y] = acc.get();
       }
 #pragma unroll
       for (int z = 0; z < 3; ++z) {
         Acc<T> acc;
 #pragma unroll
-        for (int y = 0; y < 3; ++y) acc.fma_(nP[y], M.gi[y][z]);
-        Mk[z] = M.alpha * acc.get();
+        for (int y = 0; y < 3; ++y) acc.fma_(nP[y], gi[y][z]);
+        Mk[z] = alpha * acc.get();
       }
     }
     const T hnn = hal * nnPhi;
-#pragma unroll
+#pragma unroll 2
     for (int s = 0; s < 10; ++s) {
       Acc<T> acc;
-      acc.fma_(hnn, Pi[s]);
+      acc.fma_(hnn, V(s));
 #pragma unroll
-      for (int z = 0; z < 3; ++z) acc.fma_(Mk[z], Ph[z][s]);
-      acc.fma_(-M.alpha, Ph[x][s]);
+      for (int z = 0; z < 3; ++z) acc.fma_(Mk[z], V(10 + 10 * z + s));
+      acc.fma_(-alpha, V(10 + 10 * x + s));
       stA<T, kInt<T>>(src, P, p, 10 + 10 * x + s, acc.get());
     }
   }
-  (void)zero;
 }
 
 template <class T, bool FO>
@@ -471,26 +510,26 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
 int pw_rhs_part(const cffyn_shell* sh, const double* u, const double* D, double* out, int stage,
                 bool u_pairs, bool out_pairs, cudaStream_t st) {
   Geo g = geo_of(sh);
-  const unsigned nb = blocks_for(g.P, 128);
+  const unsigned nb = blocks_for(g.P, 128), nbr = blocks_for(g.P, kRhsBlock);
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   if (stage == 0 || stage == 1) {
     if (!mixed)
-      k_rhs_gamma<double, false, false><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+      k_rhs_gamma<double, false, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
     else if (u_pairs && out_pairs)
-      k_rhs_gamma<ff, true, true><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+      k_rhs_gamma<ff, true, true><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
     else if (out_pairs)
-      k_rhs_gamma<ff, false, true><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+      k_rhs_gamma<ff, false, true><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
     else
-      k_rhs_gamma<ff, false, false><<<nb, 128, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+      k_rhs_gamma<ff, false, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
     count_launch();
   }
   if (stage == 0 || stage == 2) {
     if (!mixed)
-      k_rhs_quad<double, false><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+      k_rhs_quad<double, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->Rsrc, g);
     else if (u_pairs)
-      k_rhs_quad<ff, true><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+      k_rhs_quad<ff, true><<<nbr, kRhsBlock, 0, st>>>(u, sh->Rsrc, g);
     else
-      k_rhs_quad<ff, false><<<nb, 128, 0, st>>>(u, sh->Rsrc, g);
+      k_rhs_quad<ff, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->Rsrc, g);
     count_launch();
   }
   if (stage == 0 || stage == 3) {
