@@ -44,6 +44,7 @@ int pw_decompose(const cffyn_shell*, const double*, double*, bool, cudaStream_t)
 int pw_reconstruct(const cffyn_shell*, const double*, double*, int, double*, double*, double*, double,
                    int*, cudaStream_t);
 int pw_cart(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
+int pw_triad_table(const cffyn_shell*);
 int pw_gauge(const cffyn_shell*, const double*, double*, cudaStream_t);
 int pw_to_internal(const cffyn_shell*, const double*, double*, long long, cudaStream_t);
 int pw_constraints(const cffyn_shell*, const double*, const double*, const double*, double*, cudaStream_t);
@@ -109,7 +110,7 @@ void free_shell(cffyn_shell* sh) {
   double** ptrs[] = {&sh->r,     &sh->sth,    &sh->cth,    &sh->sph, &sh->cph,  &sh->Dr,   &sh->Dth2,
                      &sh->Dph,   &sh->Fan,    &sh->Fsy,    &sh->Fraw, &sh->Fproj0, &sh->FprojC,
                      &sh->H,     &sh->dH,     &sh->U,      &sh->kacc, &sh->D,    &sh->S,
-                     &sh->Rsrc,  &sh->red};
+                     &sh->Rsrc,  &sh->red,    &sh->triad};
   for (double** p : ptrs)
     if (*p) cudaFree(*p);
   TcOp* to[] = {&sh->tDr, &sh->tDth2, &sh->tDph, &sh->tFan, &sh->tFsy, &sh->tF0,
@@ -211,8 +212,9 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
   };
   if ((rc = alloc(&sh->U, nvP)) || (rc = alloc(&sh->kacc, nvP)) || (rc = alloc(&sh->D, 3 * nvP)) ||
       (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->Rsrc, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, 12 * sh->P)) ||
-      (rc = alloc(&sh->red, 2)))
+      (rc = alloc(&sh->red, 2)) || (rc = alloc(&sh->triad, (size_t)9 * sh->N * sh->J)))
     return fail(rc);
+  if ((rc = pw_triad_table(sh))) return fail(rc);
   if (d.precision == CFFYN_MIXED)
     if (cudaMalloc(&sh->exps, 64 * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
   {

@@ -78,6 +78,7 @@ struct cffyn_shell {
 
   // grid (device)
   double *r = nullptr, *sth = nullptr, *cth = nullptr, *sph = nullptr, *cph = nullptr;
+  double* triad = nullptr;  // [n_phi][n_theta][9] real triad rows, internal storage
 
   // FP64 operators (device, row-major)
   double* Dr = nullptr;     // n_r x n_r

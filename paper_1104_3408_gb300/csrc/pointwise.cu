@@ -20,6 +20,7 @@
 //   k_constraints  sums of squares of C_iab = d_i g_ab - Phi_iab and
 //                  C_a = H_a + Gamma_a (App. A.1).
 #include <cstdio>
+#include <type_traits>
 
 #include "pw_common.cuh"
 
@@ -33,14 +34,39 @@ struct Triad {
   T R[3][3];
 };
 
+// rows e_r, e_theta, e_phi in Cartesian components at (theta_i, phi_jj),
+// formed in T arithmetic (set-up of the triad table)
 template <class T>
-__device__ __forceinline__ Triad<T> triad_at(const Geo& g, int i, int jj) {
+__device__ __forceinline__ Triad<T> triad_eval(const Geo& g, int i, int jj) {
   Triad<T> t;
   const T st = S<T>::c(g.sth[i]), ct = S<T>::c(g.cth[i]);
   const T sp = S<T>::c(g.sph[jj]), cp = S<T>::c(g.cph[jj]);
   t.R[0][0] = st * cp; t.R[0][1] = st * sp; t.R[0][2] = ct;
   t.R[1][0] = ct * cp; t.R[1][1] = ct * sp; t.R[1][2] = -st;
   t.R[2][0] = -sp;     t.R[2][1] = cp;      t.R[2][2] = S<T>::c(0.0);
+  return t;
+}
+
+template <class T>
+__global__ void k_triad_table(Geo g, double* tab) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.N * g.J) return;
+  const int i = e % g.N, jj = e / g.N;
+  const Triad<T> t = triad_eval<T>(g, i, jj);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Store<T, !std::is_same<T, double>::value>::st(tab, (long long)e * 9 + 3 * a + b, t.R[a][b]);
+}
+
+template <class T>
+__device__ __forceinline__ Triad<T> triad_at(const Geo& g, int i, int jj) {
+  Triad<T> t;
+  const long long o = ((long long)jj * g.N + i) * 9;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) t.R[a][b] = Store<T, !std::is_same<T, double>::value>::ld(g.triad, o + 3 * a + b);
   return t;
 }
 
@@ -352,52 +378,99 @@ __global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in
   decompose_group<T, FI>((int)blockIdx.y, in, out, geo.P, p, t);
 }
 
+// Output fields of each tensor group (see kGroups).
+__host__ __device__ constexpr bool in_group(int G, int f) {
+  return G == 0 ? (f == 0 || f == 10)
+       : G == 1 ? (f >= 1 && f <= 3)
+       : G == 2 ? (f >= 11 && f <= 13)
+       : G == 3 ? (f == 20 || f == 30 || f == 40)
+       : G == 4 ? (f >= 4 && f <= 9)
+       : G == 5 ? (f >= 14 && f <= 19)
+       : G == 6 ? (f >= 20 && (f % 10) >= 1 && (f % 10) <= 3)
+                : (f >= 20 && (f % 10) >= 4);
+}
+
 // mode: 0 = write filtered tensor to `dst`;
 //       1..4 = RK4 stage s (1-based) with filtered rhs k_s = reconstruct(sp);
 //       5..8 = RK4 stage without filter: k_s read as Cartesian from sp.
 // Stage updates: k_1: acc = k, U = u + dt/2 k; k_2: acc += 2k, U = u + dt/2 k;
 // k_3: acc += 2k, U = u + dt k; k_4: u = u + dt/6 (acc + k) (classical RK4).
-// The state sums are FP64 additions; the increments are formed in T.
+// The state sums are FP64 additions; the increments are formed in T.  One
+// instance per tensor group G: the group's Cartesian k_s is formed into
+// registers first, then the state words of all its fields are loaded at once
+// and updated.
+template <class T, bool FD, int G>
+__device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp, double* __restrict__ dst,
+                                                   const Geo& geo, int mode, double* __restrict__ u,
+                                                   double* __restrict__ U, double* __restrict__ kacc,
+                                                   double dt, long long p, bool& bad) {
+  const long long P = geo.P;
+  using SI_ = Store<T, kIn<T>>;
+  T kv[50];
+  if (mode <= 4) {
+    const int i = (int)((p / geo.n_r) % geo.N);
+    const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+    const Triad<T> t = triad_at<T>(geo, i, jj);
+    reconstruct_group<T>(G, sp, P, p, t, [&](int f, T v) { kv[f] = v; });
+  } else {
+#pragma unroll
+    for (int f = 0; f < 50; ++f)
+      if (in_group(G, f)) kv[f] = ld<T, kIn<T>>(sp, P, p, f);
+  }
+  if (mode == 0) {
+#pragma unroll
+    for (int f = 0; f < 50; ++f)
+      if (in_group(G, f)) Store<T, FD>::st(dst, (long long)f * P + p, kv[f]);
+    return;
+  }
+  const int stage = (mode - 1) % 4;  // 0..3 for modes 1..8
+  double uv[50];
+  T ka[50];
+#pragma unroll
+  for (int f = 0; f < 50; ++f)
+    if (in_group(G, f)) {
+      uv[f] = u[(long long)f * P + p];
+      if (stage > 0) ka[f] = SI_::ld(kacc, (long long)f * P + p);
+    }
+  if (stage < 3) {
+    const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
+#pragma unroll
+    for (int f = 0; f < 50; ++f)
+      if (in_group(G, f)) {
+        const long long o = (long long)f * P + p;
+        bad |= !finite_s(kv[f]);
+        SI_::st(kacc, o, stage == 0 ? kv[f] : ka[f] + (kv[f] + kv[f]));
+        // stage state: FP64 sum on the FP64 path, double-float on the mixed path
+        SI_::st(U, o, S<T>::c(uv[f]) + cU * kv[f]);
+      }
+  } else {
+    const T sixth = S<T>::c(dt / 6.0);
+#pragma unroll
+    for (int f = 0; f < 50; ++f)
+      if (in_group(G, f)) {
+        bad |= !finite_s(kv[f]);
+        u[(long long)f * P + p] = uv[f] + S<T>::to_double(sixth * (ka[f] + kv[f]));
+      }
+  }
+}
+
 template <class T, bool FD>
 __global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
                                                      Geo geo, int mode, double* __restrict__ u,
                                                      double* __restrict__ U, double* __restrict__ kacc,
                                                      double dt, int* __restrict__ flag) {
-  const long long P = geo.P;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (p >= P) return;
-  const int grp = (int)blockIdx.y;
-  const int stage = (mode - 1) % 4;  // 0..3 for modes 1..8
-  const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
-  const T wk = S<T>::c(stage == 0 ? 1.0 : 2.0);
-  const T sixth = S<T>::c(dt / 6.0);
+  if (p >= geo.P) return;
   bool bad = false;
-  using SI_ = Store<T, kIn<T>>;
-  auto emit = [&](int f, T kf) {
-    const long long o = (long long)f * P + p;
-    if (mode == 0) {
-      Store<T, FD>::st(dst, o, kf);
-      return;
-    }
-    bad |= !finite_s(kf);
-    const double uv = u[o];
-    if (stage < 3) {
-      SI_::st(kacc, o, stage == 0 ? kf : SI_::ld(kacc, o) + wk * kf);
-      // stage state: FP64 sum on the FP64 path, double-float on the mixed path
-      SI_::st(U, o, S<T>::c(uv) + cU * kf);
-    } else {
-      u[o] = uv + S<T>::to_double(sixth * (SI_::ld(kacc, o) + kf));
-    }
-  };
-  if (mode == 0 || mode <= 4) {
-    const int i = (int)((p / geo.n_r) % geo.N);
-    const int jj = (int)(p / ((long long)geo.n_r * geo.N));
-    const Triad<T> t = triad_at<T>(geo, i, jj);
-    reconstruct_group<T>(grp, sp, P, p, t, emit);
-  } else {
-    // unfiltered stage: the group's Cartesian components straight from sp
-    const int lo = grp * 7, hi = min(50, lo + 7);  // 8 blocks of fields
-    for (int f = lo; f < hi; ++f) emit(f, ld<T, kIn<T>>(sp, P, p, f));
+  switch (blockIdx.y) {
+    case 0: reconstruct_update<T, FD, 0>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    case 1: reconstruct_update<T, FD, 1>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    case 2: reconstruct_update<T, FD, 2>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    case 3: reconstruct_update<T, FD, 3>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    case 4: reconstruct_update<T, FD, 4>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    case 5: reconstruct_update<T, FD, 5>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    case 6: reconstruct_update<T, FD, 6>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    default: reconstruct_update<T, FD, 7>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
   }
   if (bad) atomicOr(flag, 1);
 }
@@ -546,6 +619,18 @@ int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, bool ou
   else
     k_cart<false, false><<<nb, 256, 0, st>>>(D, out, nf, g);
   count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
+// Table of the real triad rows at every (theta_i, phi_j) (set-up).
+int pw_triad_table(const cffyn_shell* sh) {
+  Geo g = geo_of(sh);
+  const unsigned nb = blocks_for((long long)g.N * g.J, 128);
+  if (sh->d.precision == CFFYN_MIXED)
+    k_triad_table<ff><<<nb, 128>>>(g, sh->triad);
+  else
+    k_triad_table<double><<<nb, 128>>>(g, sh->triad);
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
 }

@@ -11,6 +11,7 @@ struct Geo {
   int n_r, N, J, nv;
   long long P;
   const double *r, *sth, *cth, *sph, *cph;
+  const double* triad;  // [J][N][9] rows of the real triad (internal storage)
 };
 
 // symmetric pair index of (a, b), a, b in 0..3 (tt,tx,ty,tz,xx,xy,xz,yy,yz,zz)
@@ -134,6 +135,7 @@ inline Geo geo_of(const cffyn_shell* sh) {
   g.cth = sh->cth;
   g.sph = sh->sph;
   g.cph = sh->cph;
+  g.triad = sh->triad;
   return g;
 }
 
