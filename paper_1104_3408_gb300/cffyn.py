@@ -26,7 +26,7 @@ EXPORTED = [
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
 ]
 PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
-                  "dft_fwd", "project", "dft_inv", "reconstruct"]
+                  "dft_fwd", "project", "dft_inv", "reconstruct", "field_exp"]
 
 
 class ShellDesc(ctypes.Structure):

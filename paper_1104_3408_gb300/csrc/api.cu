@@ -53,6 +53,8 @@ int pw_constraints(const cffyn_shell*, const double*, const double*, const doubl
 
 using namespace cffyn;
 
+static_assert(cffyn_shell::kPhases == CFFYN_PROFILE_PHASES, "phase count of the trace and the ABI");
+
 namespace {
 
 constexpr int kNR0 = 16;
@@ -87,7 +89,7 @@ int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, bool i
 }
 
 // spin slots in `spin` (nv x P) -> filtered spin slots back in `spin`;
-// scratch: D (3 nv P)
+// scratch: D (2 nv P)
 int filter_spin_slots(cffyn_shell* sh, double* spin, cudaStream_t st) {
   const size_t nvP = (size_t)sh->nv * sh->P;
   int rc;
@@ -325,14 +327,75 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
   return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
 }
 
+// The kernel groups of one RK4 step (Sec. 2.5) in order.  run(phase, fn)
+// enqueues fn() as part of `phase` (the groups of cffyn_profile_step; phase
+// 11 is the per-field exponent scan of the mixed path in front of each
+// operator group); tracing and profiling hooks live in run.
+extern "C++" {
+template <class Run>
+static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st, Run&& run) {
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  const long long P = (long long)sh->P;
+  const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
+  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  const long long lc = (long long)sh->R * sh->N * sh->n_r;  // coefficient values per function
+  int rc;
+  auto prep = [&](const double* in, bool pairs, long long len, int pairing) {
+    return run(11, [&] { return op_prepare(sh, in, pairs, sh->nv, len, pairing, st); });
+  };
+  // Yn filter of the spin slots in `spin` (in place through D and D + nvP)
+  auto filter = [&](double* spin) -> int {
+    int r;
+    if ((r = prep(spin, true, P, 1))) return r;
+    if ((r = run(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return r;
+    if ((r = prep(sh->D, true, lc, 1))) return r;
+    if ((r = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+      return r;
+    if ((r = prep(sh->D + nvP, true, lc, 1))) return r;
+    return run(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); });
+  };
+  for (int s = 0; s < 4; ++s) {
+    const double* X = s == 0 ? u : sh->U;
+    double* spin = sh->D + 2 * nvP;  // derivatives are dead after the rhs
+    const bool xp = s > 0;           // stage states U are pair-stored on the mixed path
+    if ((rc = prep(X, xp, P, 0))) return rc;
+    if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
+    if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) return rc;
+    if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) return rc;
+    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
+    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
+    if ((rc = run(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
+    if (per_sub) {
+      if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
+      if ((rc = filter(spin))) return rc;
+      if ((rc = run(10, [&] {
+             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+           })))
+        return rc;
+    } else {
+      if ((rc = run(10, [&] {
+             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+           })))
+        return rc;
+    }
+  }
+  if (!per_sub) {
+    if ((rc = run(6, [&] { return pw_decompose(sh, u, sh->S, false, st); }))) return rc;
+    if ((rc = filter(sh->S))) return rc;
+    if ((rc = run(10, [&] {
+           return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+         })))
+      return rc;
+  }
+  return CFFYN_OK;
+}
+}  // extern "C++"
+
 // One RK4 step on u (enqueued on st); see cffyn_rk4_step.  With tracing on,
 // an event is recorded after every kernel group; mark_phase says which group
 // ended at each mark, launches_per_step counts kernel launches per group.
 static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) {
-  const size_t nvP = (size_t)sh->nv * sh->P;
-  const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
   const bool tr = sh->trace != 0;
-  int rc;
   int nm = 0;
   for (int k = 0; k < cffyn_shell::kPhases; ++k) sh->launches_per_step[k] = 0;
   auto mark = [&](int phase) -> int {
@@ -352,73 +415,9 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
     sh->launches_per_step[phase] += (int)(g_launches - l0);
     return mark(phase);
   };
-  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
-  const long long lc = (long long)sh->R * sh->N * sh->n_r;
+  int rc;
   if ((rc = mark(-1))) return rc;
-  for (int s = 0; s < 4; ++s) {
-    const double* X = s == 0 ? u : sh->U;
-    double* spin = sh->D + 2 * nvP;  // derivatives are dead after the rhs
-    const bool xp = s > 0;  // stage states U are pair-stored on the mixed path
-    if ((rc = run(0, [&] {
-           int r = op_prepare(sh, X, xp, sh->nv, (long long)sh->P, 0, st);
-           return r ? r : op_deriv_r(sh, X, sh->D, sh->nv, xp, st);
-         })))
-      return rc;
-    if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) return rc;
-    if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) return rc;
-    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
-    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
-    if ((rc = run(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
-    if (per_sub) {
-      if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
-      if ((rc = run(7, [&] {
-             int r = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, 1, st);
-             return r ? r : op_dft_fwd(sh, spin, sh->D, sh->nv, st);
-           })))
-        return rc;
-      if ((rc = run(8, [&] {
-             int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
-             return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
-           })))
-        return rc;
-      if ((rc = run(9, [&] {
-             int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
-             return r ? r : op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st);
-           })))
-        return rc;
-      if ((rc = run(10, [&] {
-             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
-           })))
-        return rc;
-    } else {
-      if ((rc = run(10, [&] {
-             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
-           })))
-        return rc;
-    }
-  }
-  if (!per_sub) {
-    if ((rc = run(6, [&] { return pw_decompose(sh, u, sh->S, false, st); }))) return rc;
-    if ((rc = run(7, [&] {
-           int r = op_prepare(sh, sh->S, true, sh->nv, (long long)sh->P, 1, st);
-           return r ? r : op_dft_fwd(sh, sh->S, sh->D, sh->nv, st);
-         })))
-      return rc;
-    if ((rc = run(8, [&] {
-           int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
-           return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
-         })))
-      return rc;
-    if ((rc = run(9, [&] {
-           int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
-           return r ? r : op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st);
-         })))
-      return rc;
-    if ((rc = run(10, [&] {
-           return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
-         })))
-      return rc;
-  }
+  if ((rc = step_sequence(sh, u, dt, st, run))) return rc;
   sh->n_marks = nm;
   return CFFYN_OK;
 }
@@ -572,9 +571,6 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
   if (sh->nv == 50 && !sh->gauge_set) { set_error("gauge source not set"); return CFFYN_EINVAL; }
   if (!(dt > 0)) dt = sh->dt_default;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t nvP = (size_t)sh->nv * sh->P;
-  const size_t P = sh->P;
-  const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
   cudaEvent_t ev[2];
   CF_CUDA(cudaEventCreate(&ev[0]));
   CF_CUDA(cudaEventCreate(&ev[1]));
@@ -598,74 +594,8 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     launches_out[k] += (int)(g_launches - l0);
     return CFFYN_OK;
   };
-  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
-  const long long lc = (long long)sh->R * sh->N * sh->n_r;
   CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
-  for (int s = 0; s < 4 && !rc; ++s) {
-    const double* X = s == 0 ? u : sh->U;
-    double* spin = sh->D + 2 * nvP;
-    const bool xp = s > 0;
-    if ((rc = phase(0, [&] {
-           int r = op_prepare(sh, X, xp, sh->nv, (long long)sh->P, 0, st);
-           return r ? r : op_deriv_r(sh, X, sh->D, sh->nv, xp, st);
-         })))
-      break;
-    if ((rc = phase(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) break;
-    if ((rc = phase(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) break;
-    if ((rc = phase(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) break;
-    if ((rc = phase(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) break;
-    if ((rc = phase(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) break;
-    if (per_sub) {
-      if ((rc = phase(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) break;
-      if ((rc = phase(7, [&] {
-             int r = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, 1, st);
-             return r ? r : op_dft_fwd(sh, spin, sh->D, sh->nv, st);
-           })))
-        break;
-      if ((rc = phase(8, [&] {
-             int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
-             return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
-           })))
-        break;
-      if ((rc = phase(9, [&] {
-             int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
-             return r ? r : op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st);
-           })))
-        break;
-      if ((rc = phase(10, [&] {
-             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
-           })))
-        break;
-    } else {
-      if ((rc = phase(10, [&] {
-             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
-           })))
-        break;
-    }
-  }
-  if (!rc && !per_sub) {
-    rc = phase(6, [&] { return pw_decompose(sh, u, sh->S, false, st); });
-    if (!rc)
-      rc = phase(7, [&] {
-        int r = op_prepare(sh, sh->S, true, sh->nv, (long long)sh->P, 1, st);
-        return r ? r : op_dft_fwd(sh, sh->S, sh->D, sh->nv, st);
-      });
-    if (!rc)
-      rc = phase(8, [&] {
-        int r = op_prepare(sh, sh->D, true, sh->nv, lc, 1, st);
-        return r ? r : op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st);
-      });
-    if (!rc)
-      rc = phase(9, [&] {
-        int r = op_prepare(sh, sh->D + nvP, true, sh->nv, lc, 1, st);
-        return r ? r : op_dft_inv(sh, sh->D + nvP, sh->S, sh->nv, st);
-      });
-    if (!rc)
-      rc = phase(10, [&] {
-        return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
-      });
-  }
-  (void)P;
+  rc = step_sequence(sh, u, dt, st, phase);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   return rc;

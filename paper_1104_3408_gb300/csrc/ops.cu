@@ -247,17 +247,6 @@ __global__ void __launch_bounds__(256) k_op_fp64(OpArgs a, const double* __restr
 // ---------------------------------------------------------------------------
 // Split-precision core.
 
-// frexp exponent + 1022 of a raw element (0 for zero): FP64 word, or the
-// leading float of a pair (|hi + lo| < 2^frexp(hi) for a normalised pair)
-template <bool FI>
-__device__ __forceinline__ int raw_exp(long long w) {
-  if (FI) {
-    const int e = (int)(((unsigned int)w >> 23) & 0xff);
-    return e ? e - 126 + 1022 : 0;
-  }
-  return (int)((w >> 52) & 0x7ff);
-}
-
 // round(x 2^(47-E)) for one float, integer operations only
 __device__ __forceinline__ long long fixed47f(unsigned int u, int E) {
   const int e = (int)((u >> 23) & 0xff);
@@ -365,16 +354,51 @@ __device__ __forceinline__ long long i64_scaled_to_pair(long long T, int sc) {
 
 constexpr int kPairedFrom = 16;
 
+// The exponent word of a field is read off the largest magnitude bit pattern
+// (monotone in the exponent): the leading float of a pair, or the high word of
+// an FP64 value, sign cleared.  Each thread covers eight values (16-byte loads
+// when the field length is even), each CTA 2048, one atomic per CTA.
+constexpr int kExpThreads = 256, kExpPerThread = 8;
+
 template <bool FI>
-__global__ void k_field_exp(const long long* __restrict__ in, long long len, int* __restrict__ exps) {
+__device__ __forceinline__ unsigned int mag_key(long long w) {
+  return FI ? ((unsigned int)w & 0x7fffffffu) : ((unsigned int)((unsigned long long)w >> 32) & 0x7fffffffu);
+}
+
+template <bool FI>
+__global__ void __launch_bounds__(kExpThreads) k_field_exp(const long long* __restrict__ in, long long len,
+                                                           int* __restrict__ exps) {
+  __shared__ unsigned int wm[kExpThreads / 32];
   const int f = blockIdx.y;
   const long long* x = in + (long long)f * len;
-  int m = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < len;
-       e += (long long)gridDim.x * blockDim.x)
-    m = max(m, raw_exp<FI>(__ldg(x + e)));
-  m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
-  if ((threadIdx.x & 31) == 0 && m) atomicMax(exps + f, m);
+  const long long b0 = (long long)blockIdx.x * kExpThreads * kExpPerThread;
+  unsigned int m = 0;
+  if ((len & 1) == 0) {
+    const longlong2* x2 = reinterpret_cast<const longlong2*>(x);
+#pragma unroll
+    for (int i = 0; i < kExpPerThread / 2; ++i) {
+      const long long q = b0 / 2 + (long long)i * kExpThreads + threadIdx.x;  // pair index
+      if (2 * q < len) {
+        const longlong2 v = __ldg(x2 + q);
+        m = max(m, max(mag_key<FI>(v.x), mag_key<FI>(v.y)));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kExpPerThread; ++i) {
+      const long long e = b0 + (long long)i * kExpThreads + threadIdx.x;
+      if (e < len) m = max(m, mag_key<FI>(__ldg(x + e)));
+    }
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kExpThreads / 32; ++w) m = max(m, wm[w]);
+    const int e = FI ? (int)(m >> 23) : (int)(m >> 20);
+    const int word = FI ? (e ? e - 126 + 1022 : 0) : e;
+    if (word) atomicMax(exps + f, word);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -737,11 +761,11 @@ int set_op_smem_limits() {
 static int field_exps(const double* in, bool in_pairs, int nf, long long len, int* exps, cudaStream_t st) {
   CF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * 64, st));
   const long long* x = reinterpret_cast<const long long*>(in);
-  const int bx = (int)std::min<long long>((len + 255) / 256, 64);
+  const unsigned bx = (unsigned)((len + kExpThreads * kExpPerThread - 1) / (kExpThreads * kExpPerThread));
   if (in_pairs)
-    k_field_exp<true><<<dim3(bx, nf), 256, 0, st>>>(x, len, exps);
+    k_field_exp<true><<<dim3(bx, nf), kExpThreads, 0, st>>>(x, len, exps);
   else
-    k_field_exp<false><<<dim3(bx, nf), 256, 0, st>>>(x, len, exps);
+    k_field_exp<false><<<dim3(bx, nf), kExpThreads, 0, st>>>(x, len, exps);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;

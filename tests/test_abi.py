@@ -73,3 +73,9 @@ def test_static_scratch_limit_and_null_shell(lib):
     assert m and int(m[1]) * int(m[2]) * int(m[3]) == cffyn.STATIC_SCRATCH_BYTES
     assert lib.cffyn_derivs_static(None, None, 1, None, None) == cffyn.EINVAL
     assert b"NULL" in lib.cffyn_last_error()
+
+
+def test_profile_phase_names_match_the_header():
+    with open(os.path.join(ROOT, "include", "cffyn.h")) as fh:
+        n = int(re.search(r"#define CFFYN_PROFILE_PHASES (\d+)", fh.read())[1])
+    assert len(cffyn.PROFILE_PHASES) == n == len(set(cffyn.PROFILE_PHASES))
