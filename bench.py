@@ -40,6 +40,9 @@ def _args():
     ap.add_argument("--workload", default="ks_33x48x96")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run one eager RK4 step with per-group device times and print them "
+                         "(the fixed launch sequence used for profiler captures)")
     return ap.parse_args()
 
 
@@ -411,8 +414,33 @@ def run_reference(args, rank):
     }
 
 
+def run_profile_step(args):
+    """One eager RK4 step of the workload (mixed path): gauge from the state,
+    then Shell.profile_step.  Launch order: the three gauge-derivative operator
+    launches, then per stage the groups of cffyn_profile_step."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3408_gb300 import cffyn
+
+    w = _workload(args.workload)
+    sh = cffyn.Shell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"],
+                     precision=cffyn.MIXED)
+    u = torch.from_numpy(_state(w)).cuda()
+    sh.init_gauge_from_state(u)
+    prof = sh.profile_step(u)
+    torch.cuda.synchronize()
+    sh.destroy()
+    return {"workload": w["name"], "profile_step_ms": {k: t for k, (t, n) in prof.items()},
+            "launches": {k: n for k, (t, n) in prof.items()}}
+
+
 def main():
     args = _args()
+    if args.profile_step:
+        print(json.dumps(run_profile_step(args)), flush=True)
+        return
     rank, local_rank, ws, dist = _dist()
     if args.impl == "reference":
         out = run_reference(args, rank)

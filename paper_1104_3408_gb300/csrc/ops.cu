@@ -8,18 +8,16 @@
 // the theta double cover and the complex spin projection) and its own scatter
 // of P output rows (two segments).  No transposes are materialised.
 //
-// Two arithmetic cores share the tiling and the gathers:
-//   FP64   plain double FMA on CUDA cores (the reference path);
-//   MIXED  split-precision products on the tensor cores: W and each input
-//          column are written as 47-bit fixed-point integers relative to a
-//          per-row / per-column power of two and cut into six balanced 8-bit
-//          digits held exactly in BF16; digit products i + j = d are summed by
-//          mma.sync m16n8k16 in FP32, where they are exact integers (at most
-//          6 * 96 * 2^14 < 2^24), and folded into a 64-bit integer with weight
-//          256^(5-d); pairs with i + j > 5 are dropped (relative truncation
-//          about 6 * 2^-48 of |W| |x| K).  The result is rebuilt as an FP64
-//          number with integer operations only (this part's FP64 and
-//          conversion pipes are narrow).
+// Two arithmetic cores share the column descriptors and the gathers:
+//   FP64   plain double FMA on CUDA cores (k_op_fp64, the reference path);
+//   MIXED  split-precision products on the fifth-generation tensor cores
+//          (k_op_tc): W and each input column are written as 47-bit
+//          fixed-point integers relative to a per-row / per-field power of two
+//          and cut into six balanced 8-bit digits held exactly in BF16; digit
+//          products are summed by tcgen05.mma in FP32 accumulators in tensor
+//          memory (see the k_op_tc comment for the exactness argument); pairs
+//          with i + j > 5 are dropped (relative truncation about 6 * 2^-48 of
+//          |W| |x| K).
 #include <algorithm>
 #include <cstdio>
 
@@ -423,7 +421,7 @@ __global__ void __launch_bounds__(kExpThreads) k_field_exp(const long long* __re
 // to the leading one, about 2^-56 of the result's scale, under the truncation
 // of the dropped pairs i + j > 5 (about 6 * 2^-48).  The epilogue sums
 // (acc_0 + acc_1 2^-8 + ... + acc_4 2^-32) 2^(E_row + E_col - 14) as a
-// float pair with error-free FP32 transformations.
+// float pair (fold_pair).
 
 constexpr int kTcCols = 128;
 constexpr int kTcXSlice = kTcCols * 16 * 2;                 // bytes of one data slice per k-step
@@ -463,24 +461,24 @@ __device__ __forceinline__ void gather(const OpArgs& a, const ColDesc& d, int k0
 }
 
 // (hi, lo) float pair, packed like the mixed path's internal storage, of
-// (a0 + a1 2^-8 + a2 2^-16 + a3 2^-24 + a4 2^-32) 2^k.
-__device__ __forceinline__ long long fold_pair(float a0, float a1, float a2, float a3, float a4, int k) {
+// (a0 + a1 2^-8 + a2 2^-16 + a3 2^-24 + a4 2^-32) f1 f2 f3 (f1, f2, f3 powers of
+// two).  a0 + a1 2^-8 + a2 2^-16 is summed with error-free transformations;
+// a3 2^-24 + a4 2^-32 in plain FP32: |a3| < 4 K 2^14, so its rounding is
+// below 2^-26 of K 2^14, the scale of a0, i.e. at the level of the dropped
+// digit pairs (5 K 2^14 2^-48 in the same units).
+__device__ __forceinline__ long long fold_pair(float a0, float a1, float a2, float a3, float a4, float f1,
+                                               float f2, float f3) {
+  const float t = __fmaf_rn(a4, 2.3283064365386963e-10f, fm(a3, 5.9604644775390625e-08f));
   ff r = two_sum(a0, fm(a1, 0.00390625f));
-  float e = r.lo;
-  r = two_sum(r.hi, fm(a2, 1.52587890625e-05f));
-  e = fa(e, r.lo);
-  r = two_sum(r.hi, fm(a3, 5.9604644775390625e-08f));
-  e = fa(e, r.lo);
-  r = two_sum(r.hi, fm(a4, 2.3283064365386963e-10f));
-  e = fa(e, r.lo);
-  r = fast_two_sum(r.hi, e);
-  // 2^k as one or two exact float factors (k below -126 only for results
-  // under the float range)
-  const int k1 = max(-126, min(127, k));
-  const int k2 = max(-126, min(127, k - k1));
-  const float f1 = __int_as_float((k1 + 127) << 23), f2 = __int_as_float((k2 + 127) << 23);
-  const float hi = fm(fm(r.hi, f1), f2), lo = fm(fm(r.lo, f1), f2);
+  const ff q = two_sum(r.hi, fm(a2, 1.52587890625e-05f));
+  r = fast_two_sum(q.hi, fa(fa(r.lo, q.lo), t));
+  const float hi = fm(fm(fm(r.hi, f1), f2), f3), lo = fm(fm(fm(r.lo, f1), f2), f3);
   return (long long)(((unsigned long long)__float_as_uint(lo) << 32) | __float_as_uint(hi));
+}
+
+// 2^k as a float, k clamped to the normal range
+__device__ __forceinline__ float pow2f(int k) {
+  return __int_as_float((max(-126, min(127, k)) + 127) << 23);
 }
 
 // Digit slices of a float pair x = hi + lo (|lo| < ulp(hi), |x| < 2^E) on the
@@ -535,7 +533,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
   extern __shared__ __align__(128) unsigned char smtc[];
   __shared__ uint64_t xfull[S], wfull[S], empty[S], accf;
   __shared__ uint32_t tmem_base;
-  __shared__ int rowE[ROWS];
+  __shared__ float rowF[ROWS];  // 2^E_row
   const int tid = threadIdx.x;
   const bool producer = tid < C::kProd;
   const long long tile = blockIdx.x / W.ngroups;
@@ -551,7 +549,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
   int ce = exps[col.fld];
   if (pairing && col.fld >= kPairedFrom) ce = max(ce, exps[col.fld ^ 1]);
   const int E = ce - 1022;
-  if (tid < ROWS) rowE[tid] = W.rowexp[grp * ROWS + tid];
+  if (tid < ROWS) rowF[tid] = pow2f(W.rowexp[grp * ROWS + tid]);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       tc::bar_init(&xfull[s], C::kProd);
@@ -680,6 +678,10 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
     const int g = tid >> 7;
     const int prow = a.g.P - grp * ROWS;  // valid rows of this group
     const uint32_t lane = tm + ((uint32_t)(((tid >> 5) & 3) * 32) << 16);
+    // 2^(E_col - 14) as two factors (the second is 1 unless E_col - 14 is
+    // below the float range, i.e. for outputs that underflow anyway)
+    const int ec = E - 14;
+    const float cf1 = pow2f(ec), cf2 = pow2f(ec - max(-126, min(127, ec)));
 #pragma unroll 1
     for (int p0 = g * R; p0 < (g + 1) * R && p0 < prow; p0 += 8) {
       uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
@@ -698,7 +700,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
         if (p0 + j < prow) {
           const long long w =
               fold_pair(__uint_as_float(v0[j]), __uint_as_float(v1[j]), __uint_as_float(v2[j]),
-                        __uint_as_float(v3[j]), __uint_as_float(v4[j]), rowE[p0 + j] + E - 14);
+                        __uint_as_float(v3[j]), __uint_as_float(v4[j]), rowF[p0 + j], cf1, cf2);
           store_elem(a, col, grp * ROWS + p0 + j, __longlong_as_double(w));
         }
       }
