@@ -41,8 +41,8 @@ void free_tc(TcOp&);
 int pw_rhs(const cffyn_shell*, const double*, const double*, double*, cudaStream_t);
 int pw_rhs_part(const cffyn_shell*, const double*, const double*, double*, int, bool, bool, cudaStream_t);
 int pw_decompose(const cffyn_shell*, const double*, double*, bool, cudaStream_t);
-int pw_reconstruct(const cffyn_shell*, const double*, double*, int, double*, double*, double*, double,
-                   int*, cudaStream_t);
+int pw_reconstruct(const cffyn_shell*, const double*, double*, int, double*, double*, double*, double*,
+                   double, int*, cudaStream_t);
 int pw_cart(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int pw_triad_table(const cffyn_shell*);
 int pw_gauge(const cffyn_shell*, const double*, double*, cudaStream_t);
@@ -112,7 +112,7 @@ void free_shell(cffyn_shell* sh) {
   double** ptrs[] = {&sh->r,     &sh->sth,    &sh->cth,    &sh->sph, &sh->cph,  &sh->Dr,   &sh->Dth2,
                      &sh->Dph,   &sh->Fan,    &sh->Fsy,    &sh->Fraw, &sh->Fproj0, &sh->FprojC,
                      &sh->H,     &sh->dH,     &sh->U,      &sh->kacc, &sh->D,    &sh->S,
-                     &sh->Rsrc,  &sh->red,    &sh->triad};
+                     &sh->Rsrc,  &sh->red,    &sh->triad, &sh->Uf};
   for (double** p : ptrs)
     if (*p) cudaFree(*p);
   TcOp* to[] = {&sh->tDr, &sh->tDth2, &sh->tDph, &sh->tFan, &sh->tFsy, &sh->tF0,
@@ -217,8 +217,10 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
       (rc = alloc(&sh->red, 2)) || (rc = alloc(&sh->triad, (size_t)9 * sh->N * sh->J)))
     return fail(rc);
   if ((rc = pw_triad_table(sh))) return fail(rc);
-  if (d.precision == CFFYN_MIXED)
+  if (d.precision == CFFYN_MIXED) {
     if (cudaMalloc(&sh->exps, 64 * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
+    if ((rc = alloc(&sh->Uf, nvP))) return fail(rc);
+  }
   {
     int host[33];
     for (int i = 0; i < 16; ++i) host[i] = i;
@@ -324,7 +326,7 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = pw_decompose(sh, u, sh->S, false, st))) return rc;
   if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
-  return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+  return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
 }
 
 // The kernel groups of one RK4 step (Sec. 2.5) in order.  run(phase, fn)
@@ -354,10 +356,14 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
     if ((r = prep(sh->D + nvP, true, lc, 1))) return r;
     return run(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); });
   };
+  const bool mixed = sh->d.precision == CFFYN_MIXED;
   for (int s = 0; s < 4; ++s) {
-    const double* X = s == 0 ? u : sh->U;
+    // mixed path: every stage reads pairs (the initial state from Uf, which
+    // cffyn_rk4_step fills from u before the first step and the last stage
+    // keeps current); FP64 path: u, then U
+    const double* X = s == 0 ? (mixed ? sh->Uf : u) : sh->U;
     double* spin = sh->D + 2 * nvP;  // derivatives are dead after the rhs
-    const bool xp = s > 0;           // stage states U are pair-stored on the mixed path
+    const bool xp = mixed;
     if ((rc = prep(X, xp, P, 0))) return rc;
     if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
     if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) return rc;
@@ -369,21 +375,21 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
       if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
       if ((rc = filter(spin))) return rc;
       if ((rc = run(10, [&] {
-             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
            })))
         return rc;
     } else {
       if ((rc = run(10, [&] {
-             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, dt, sh->flag, st);
+             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
            })))
         return rc;
     }
   }
   if (!per_sub) {
-    if ((rc = run(6, [&] { return pw_decompose(sh, u, sh->S, false, st); }))) return rc;
+    if ((rc = run(6, [&] { return pw_decompose(sh, mixed ? sh->Uf : u, sh->S, mixed, st); }))) return rc;
     if ((rc = filter(sh->S))) return rc;
     if ((rc = run(10, [&] {
-           return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+           return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, sh->Uf, 0.0, sh->flag, st);
          })))
       return rc;
   }
@@ -460,6 +466,7 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
     sh->graph_trace = sh->trace;
   }
   CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
+  if (sh->Uf && (rc = pw_to_internal(sh, u, sh->Uf, (long long)sh->nv * sh->P, st))) return rc;
   for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
   CF_CUDA(cudaMemcpyAsync(sh->flag_host, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(cudaStreamSynchronize(st));
@@ -595,6 +602,7 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     return CFFYN_OK;
   };
   CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
+  if (sh->Uf && (rc = pw_to_internal(sh, u, sh->Uf, (long long)sh->nv * sh->P, st))) return rc;
   rc = step_sequence(sh, u, dt, st, phase);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);

@@ -103,6 +103,7 @@ struct cffyn_shell {
 
   // workspace
   double* U = nullptr;     // stage state [nv][P]
+  double* Uf = nullptr;    // mixed path: the step's initial state in internal storage [nv][P]
   double* kacc = nullptr;  // RK4 accumulator [nv][P]
   double* D = nullptr;     // spherical derivatives [3][nv][P] (also DFT coefficients)
   double* S = nullptr;     // rhs / spin functions [nv][P]

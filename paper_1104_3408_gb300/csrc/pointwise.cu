@@ -395,15 +395,19 @@ __host__ __device__ constexpr bool in_group(int G, int f) {
 //       5..8 = RK4 stage without filter: k_s read as Cartesian from sp.
 // Stage updates: k_1: acc = k, U = u + dt/2 k; k_2: acc += 2k, U = u + dt/2 k;
 // k_3: acc += 2k, U = u + dt k; k_4: u = u + dt/6 (acc + k) (classical RK4).
-// The state sums are FP64 additions; the increments are formed in T.  One
+// The state sums are FP64 additions; the increments are formed in T.  On the
+// mixed path uf holds the step's initial state as pairs: stages 1-3 read it
+// as the base of U, the last stage (and mode 0) write the new state into it.
+// One
 // instance per tensor group G: the group's Cartesian k_s is formed into
 // registers first, then the state words of all its fields are loaded at once
 // and updated.
-template <class T, bool FD, int G>
+template <class T, bool FD, int G, int KIND>
 __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp, double* __restrict__ dst,
                                                    const Geo& geo, int mode, double* __restrict__ u,
                                                    double* __restrict__ U, double* __restrict__ kacc,
-                                                   double dt, long long p, bool& bad) {
+                                                   double* __restrict__ uf, double dt, long long p,
+                                                   bool& bad) {
   const long long P = geo.P;
   using SI_ = Store<T, kIn<T>>;
   T kv[50];
@@ -417,22 +421,30 @@ __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp
     for (int f = 0; f < 50; ++f)
       if (in_group(G, f)) kv[f] = ld<T, kIn<T>>(sp, P, p, f);
   }
-  if (mode == 0) {
+  constexpr bool kPair = kIn<T>;  // mixed path: the step's initial state also as pairs in uf
+  if (KIND == 0) {
 #pragma unroll
     for (int f = 0; f < 50; ++f)
-      if (in_group(G, f)) Store<T, FD>::st(dst, (long long)f * P + p, kv[f]);
+      if (in_group(G, f)) {
+        Store<T, FD>::st(dst, (long long)f * P + p, kv[f]);
+        if (kPair && uf) SI_::st(uf, (long long)f * P + p, kv[f]);
+      }
     return;
   }
-  const int stage = (mode - 1) % 4;  // 0..3 for modes 1..8
+  const int stage = (mode - 1) % 4;  // 0..3 for modes 1..8; KIND 2 is stage 3
   double uv[50];
-  T ka[50];
+  T ub[50], ka[50];
 #pragma unroll
   for (int f = 0; f < 50; ++f)
     if (in_group(G, f)) {
-      uv[f] = u[(long long)f * P + p];
-      if (stage > 0) ka[f] = SI_::ld(kacc, (long long)f * P + p);
+      const long long o = (long long)f * P + p;
+      if (kPair && KIND == 1)
+        ub[f] = SI_::ld(uf, o);
+      else
+        uv[f] = u[o];
+      if (KIND == 2 || stage > 0) ka[f] = SI_::ld(kacc, o);
     }
-  if (stage < 3) {
+  if (KIND == 1) {
     const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
 #pragma unroll
     for (int f = 0; f < 50; ++f)
@@ -441,37 +453,43 @@ __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp
         bad |= !finite_s(kv[f]);
         SI_::st(kacc, o, stage == 0 ? kv[f] : ka[f] + (kv[f] + kv[f]));
         // stage state: FP64 sum on the FP64 path, double-float on the mixed path
-        SI_::st(U, o, S<T>::c(uv[f]) + cU * kv[f]);
+        SI_::st(U, o, (kPair ? ub[f] : S<T>::c(uv[f])) + cU * kv[f]);
       }
   } else {
     const T sixth = S<T>::c(dt / 6.0);
 #pragma unroll
     for (int f = 0; f < 50; ++f)
       if (in_group(G, f)) {
+        const long long o = (long long)f * P + p;
         bad |= !finite_s(kv[f]);
-        u[(long long)f * P + p] = uv[f] + S<T>::to_double(sixth * (ka[f] + kv[f]));
+        const double un = uv[f] + S<T>::to_double(sixth * (ka[f] + kv[f]));
+        u[o] = un;
+        if (kPair && uf) SI_::st(uf, o, S<T>::c(un));
       }
   }
 }
 
-template <class T, bool FD>
+template <class T, bool FD, int KIND>
 __global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
                                                      Geo geo, int mode, double* __restrict__ u,
                                                      double* __restrict__ U, double* __restrict__ kacc,
-                                                     double dt, int* __restrict__ flag) {
+                                                     double* __restrict__ uf, double dt,
+                                                     int* __restrict__ flag) {
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= geo.P) return;
   bool bad = false;
+#define CFFYN_RECON(G) reconstruct_update<T, FD, G, KIND>(sp, dst, geo, mode, u, U, kacc, uf, dt, p, bad)
   switch (blockIdx.y) {
-    case 0: reconstruct_update<T, FD, 0>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
-    case 1: reconstruct_update<T, FD, 1>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
-    case 2: reconstruct_update<T, FD, 2>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
-    case 3: reconstruct_update<T, FD, 3>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
-    case 4: reconstruct_update<T, FD, 4>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
-    case 5: reconstruct_update<T, FD, 5>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
-    case 6: reconstruct_update<T, FD, 6>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
-    default: reconstruct_update<T, FD, 7>(sp, dst, geo, mode, u, U, kacc, dt, p, bad); break;
+    case 0: CFFYN_RECON(0); break;
+    case 1: CFFYN_RECON(1); break;
+    case 2: CFFYN_RECON(2); break;
+    case 3: CFFYN_RECON(3); break;
+    case 4: CFFYN_RECON(4); break;
+    case 5: CFFYN_RECON(5); break;
+    case 6: CFFYN_RECON(6); break;
+    default: CFFYN_RECON(7); break;
   }
+#undef CFFYN_RECON
   if (bad) atomicOr(flag, 1);
 }
 
@@ -593,15 +611,29 @@ int pw_decompose(const cffyn_shell* sh, const double* in, double* out, bool in_p
   return CFFYN_OK;
 }
 
-// dst (mode 0) is an FP64 array
+// dst (mode 0) is an FP64 array; uf (mixed path): the step's initial state as
+// pairs, read by stages 1-3 and written by the last stage and by mode 0
 int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mode, double* u, double* U,
-                   double* kacc, double dt, int* flag, cudaStream_t st) {
+                   double* kacc, double* uf, double dt, int* flag, cudaStream_t st) {
   Geo g = geo_of(sh);
   const dim3 grid(blocks_for(g.P, 128), kGroups);
-  if (sh->d.precision == CFFYN_MIXED)
-    k_reconstruct<ff, false><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, dt, flag);
-  else
-    k_reconstruct<double, false><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, dt, flag);
+  // kernel instance by stage kind: 0 filtered result, 1 stages 1-3, 2 last stage
+  const int kind = mode == 0 ? 0 : ((mode - 1) % 4 == 3 ? 2 : 1);
+  if (sh->d.precision == CFFYN_MIXED) {
+    if (kind == 0)
+      k_reconstruct<ff, false, 0><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, uf, dt, flag);
+    else if (kind == 1)
+      k_reconstruct<ff, false, 1><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, uf, dt, flag);
+    else
+      k_reconstruct<ff, false, 2><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, uf, dt, flag);
+  } else {
+    if (kind == 0)
+      k_reconstruct<double, false, 0><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, nullptr, dt, flag);
+    else if (kind == 1)
+      k_reconstruct<double, false, 1><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, nullptr, dt, flag);
+    else
+      k_reconstruct<double, false, 2><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, nullptr, dt, flag);
+  }
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
