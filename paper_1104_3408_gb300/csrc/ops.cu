@@ -428,6 +428,16 @@ constexpr int kTcXSlice = kTcCols * 16 * 2;                 // bytes of one data
 constexpr int kTcXBytes = kSlices * kTcXSlice;               // 24576
 constexpr unsigned long long kTcWaitNs = 1000000000ull;      // bounded waits: 1 s
 
+// Up to four operator applications with the same row-group size in one
+// launch (the projections of the spin classes); blockIdx.y = class * nm + m.
+constexpr int kMaxBatch = 4;
+struct TcBatch {
+  OpArgs a[kMaxBatch];
+  TcOp W[kMaxBatch];
+  long long tiles[kMaxBatch];  // column tiles of each class
+  int nclass, nm;
+};
+
 template <int ROWS>
 struct TcCfg {
   static constexpr int kProd = ROWS == 48 ? 256 : 512;                 // producer threads
@@ -526,7 +536,7 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
 }
 
 template <bool FI, int ROWS>
-__global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp W, const int* __restrict__ exps,
+__global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, const int* __restrict__ exps,
                                                                  int pairing, int* __restrict__ flag) {
   using C = TcCfg<ROWS>;
   constexpr int S = C::kStages, KQ = C::kKQ;
@@ -534,12 +544,17 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
   __shared__ uint64_t xfull[S], wfull[S], empty[S], accf;
   __shared__ uint32_t tmem_base;
   __shared__ float rowF[ROWS];  // 2^E_row
+  // operator class and azimuthal number of this CTA (blockIdx.y = class * nm + m)
+  const int cls = B.nclass > 1 ? (int)blockIdx.y / B.nm : 0;
+  OpArgs a = B.a[cls];
+  TcOp W = B.W[cls];
+  if ((long long)blockIdx.x >= B.tiles[cls] * W.ngroups) return;  // past this class's columns
   const int tid = threadIdx.x;
   const bool producer = tid < C::kProd;
   const long long tile = blockIdx.x / W.ngroups;
   const int grp = (int)(blockIdx.x - tile * W.ngroups);
   if (a.batched_m) {
-    a.m = blockIdx.y;
+    a.m = (int)blockIdx.y - cls * B.nm;
     W.w += (size_t)a.m * W.w_stride;
     W.rowexp += (size_t)a.m * W.rowexp_stride;
   }
@@ -717,6 +732,31 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(OpArgs a, TcOp 
 // ---------------------------------------------------------------------------
 // Host side
 
+// Mixed path: one launch of the tcgen05 core over the classes of b (same row
+// group size, same input storage), grid = (max tiles x row groups,
+// classes x nm).
+static int launch_batch(const cffyn_shell* sh, const TcBatch& b, cudaStream_t st, int pairing, bool in_pairs,
+                        const int* exps) {
+  long long gx = 0;
+  for (int c = 0; c < b.nclass; ++c) gx = std::max(gx, b.tiles[c] * b.W[c].ngroups);
+  if (gx == 0) return CFFYN_OK;
+  const dim3 grid((unsigned)gx, (unsigned)(b.nclass * b.nm));
+  if (b.W[0].rows == 48) {
+    if (in_pairs)
+      k_op_tc<true, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, sh->flag);
+    else
+      k_op_tc<false, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, sh->flag);
+  } else {
+    if (in_pairs)
+      k_op_tc<true, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, sh->flag);
+    else
+      k_op_tc<false, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, sh->flag);
+  }
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
 // FP64 core, or on the mixed path the tcgen05 core with the per-field
 // exponents of the input at exps (op_prepare fills sh->exps); in_pairs: the
 // input is pair-stored.  Mixed-path outputs are pair-stored.
@@ -728,25 +768,18 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
     unsigned gy = (unsigned)((a.g.P + F64_PT - 1) / F64_PT);
     size_t smem = (size_t)(F64_PT * a.g.K + a.g.K * F64_QT) * sizeof(double);
     k_op_fp64<<<dim3(gx, gy, extra.y), 256, smem, st>>>(a, W64);
-  } else {
-    const long long tiles = (a.g.ncols + kTcCols - 1) / kTcCols;
-    const dim3 grid((unsigned)(tiles * Wt->ngroups), extra.y);
-    const int* ex = exps ? exps : sh->exps;
-    if (Wt->rows == 48) {
-      if (in_pairs)
-        k_op_tc<true, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
-      else
-        k_op_tc<false, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
-    } else {
-      if (in_pairs)
-        k_op_tc<true, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
-      else
-        k_op_tc<false, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(a, *Wt, ex, pairing, sh->flag);
-    }
+    count_launch();
+    CF_CUDA(cudaGetLastError());
+    return CFFYN_OK;
   }
-  count_launch();
-  CF_CUDA(cudaGetLastError());
-  return CFFYN_OK;
+  TcBatch b;
+  memset(&b, 0, sizeof(b));
+  b.a[0] = a;
+  b.W[0] = *Wt;
+  b.tiles[0] = (a.g.ncols + kTcCols - 1) / kTcCols;
+  b.nclass = 1;
+  b.nm = (int)extra.y;
+  return launch_batch(sh, b, st, pairing, in_pairs, exps ? exps : sh->exps);
 }
 
 int set_op_smem_limits() {
@@ -867,12 +900,17 @@ int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cud
                  &sh->tFsy, st, 1);
 }
 
-// Projection of all spin classes, coefficients C -> C2 (same layout); one
-// launch per class covering every m = 0..L.
+// Projection of all spin classes, coefficients C -> C2 (same layout): every
+// class and every m = 0..L in one launch on the mixed path, one launch per
+// class on the FP64 path.
 int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* slots_r0, int n_r0,
                const int* const slots_c[3], const int n_c[3], cudaStream_t st) {
   const int N = sh->N;
   const int nm = sh->L + 1;
+  OpArgs cls[4];
+  const double* W64[4];
+  const TcOp* Wt[4];
+  int ncls = 0;
   if (n_r0 > 0) {
     OpArgs a = base_args(sh);
     a.in = C;
@@ -885,8 +923,9 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     a.g.K = a.g.K0 = a.g.P = a.g.P0 = N;
     a.g.in_rs = a.g.out_rs = sh->n_r;
     a.g.ncols = (long long)n_r0 * 2 * sh->n_r;
-    int rc = launch(sh, a, sh->Fproj0, &sh->tF0, dim3(1, nm), st, 1, true);
-    if (rc) return rc;
+    cls[ncls] = a;
+    W64[ncls] = sh->Fproj0;
+    Wt[ncls++] = &sh->tF0;
   }
   for (int s = 0; s < 3; ++s) {
     if (n_c[s] <= 0) continue;
@@ -903,7 +942,25 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     b.g.P = b.g.P0 = N;
     b.g.in_rs = b.g.out_rs = sh->n_r;
     b.g.ncols = (long long)n_c[s] * 4 * sh->n_r;
-    int rc = launch(sh, b, sh->FprojC + (size_t)s * nm * N * 2 * N, &sh->tFC[s], dim3(1, nm), st, 1, true);
+    cls[ncls] = b;
+    W64[ncls] = sh->FprojC + (size_t)s * nm * N * 2 * N;
+    Wt[ncls++] = &sh->tFC[s];
+  }
+  if (sh->d.precision == CFFYN_MIXED) {
+    // every class of the projection in one launch (all have N rows)
+    TcBatch bt;
+    memset(&bt, 0, sizeof(bt));
+    for (int c = 0; c < ncls; ++c) {
+      bt.a[c] = cls[c];
+      bt.W[c] = *Wt[c];
+      bt.tiles[c] = (cls[c].g.ncols + kTcCols - 1) / kTcCols;
+    }
+    bt.nclass = ncls;
+    bt.nm = nm;
+    return launch_batch(sh, bt, st, 1, true, sh->exps);
+  }
+  for (int c = 0; c < ncls; ++c) {
+    int rc = launch(sh, cls[c], W64[c], Wt[c], dim3(1, nm), st, 1, true);
     if (rc) return rc;
   }
   return CFFYN_OK;
