@@ -16,7 +16,12 @@
  * Fields (n_fields = 50, 54 or 58; App. A.1 eqs. gdot, Phidot, Pidot): the
  * symmetric pairs (tt,tx,ty,tz,xx,xy,xz,yy,yz,zz) of g_ab (fields 0..9),
  * Pi_ab (10..19), Phi_xab (20..29), Phi_yab (30..39), Phi_zab (40..49); then
- * H_a (50..53) and dH_a/dt (54..57) where present.
+ * H_a (50..53) and dH_a/dt (54..57) where present.  With 54 fields the
+ * gauge source is evolved with d_t H_a = 0; with 58 fields d_t H_a = G_a
+ * (fields 54..57) and d_t G_a = 0, and G_a enters eq. Pidot as the time
+ * derivative of H_b in nabla_(a H_b).  The gauge fields are filtered like
+ * the others (H_t a scalar, H_i a vector) and keep their right-hand sides on
+ * the outermost sphere.
  *
  * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream).  Calls enqueue work and return; results are ready when the stream
@@ -108,7 +113,8 @@ CFFYN_API double cffyn_default_dt(const cffyn_shell* sh);
 
 /* Static gauge source H_a (eq. gauge), H[4][n_phi][n_theta][n_r] device FP64.
  * The library stores H and its Cartesian derivatives d_i H_a computed with the
- * shell's spectral operators.  Used when n_fields == 50. */
+ * shell's spectral operators.  n_fields == 50 only; CFFYN_EINVAL for 54/58
+ * fields, whose gauge source is fields 50..53 of the state. */
 CFFYN_API int cffyn_set_gauge(cffyn_shell* sh, const double* H, void* stream);
 
 /* H_a = -Gamma_a(u) (eq. gauge and eq. Gamma from undifferentiated fields),

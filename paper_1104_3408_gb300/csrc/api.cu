@@ -46,8 +46,9 @@ int pw_reconstruct(const cffyn_shell*, const double*, double*, int, double*, dou
 int pw_cart(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int pw_triad_table(const cffyn_shell*);
 int pw_gauge(const cffyn_shell*, const double*, double*, cudaStream_t);
+int pw_gauge_into_state(const cffyn_shell*, double*, cudaStream_t);
 int pw_to_internal(const cffyn_shell*, const double*, double*, long long, cudaStream_t);
-int pw_constraints(const cffyn_shell*, const double*, const double*, const double*, double*, cudaStream_t);
+int pw_constraints(const cffyn_shell*, const double*, const double*, const double*, bool, double*, cudaStream_t);
 
 }  // namespace cffyn
 
@@ -57,11 +58,11 @@ static_assert(cffyn_shell::kPhases == CFFYN_PROFILE_PHASES, "phase count of the 
 
 namespace {
 
-constexpr int kNR0 = 16;
-constexpr int kNC[3] = {11, 5, 1};
 const int* slots_r0(const cffyn_shell* sh) { return sh->slots; }
 const int* slots_c(const cffyn_shell* sh, int s) {
-  return sh->slots + 16 + (s == 0 ? 0 : (s == 1 ? 11 : 16));
+  int o = sh->nR0;
+  for (int q = 0; q < s; ++q) o += sh->nC[q];
+  return sh->slots + o;
 }
 
 int check_ptr(const void* p, const char* what) {
@@ -100,7 +101,7 @@ int filter_spin_slots(cffyn_shell* sh, double* spin, cudaStream_t st) {
   if ((rc = op_dft_fwd(sh, spin, C, sh->nv, st))) return rc;
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
   if ((rc = op_prepare(sh, C, true, sh->nv, lc, 1, st))) return rc;
-  if ((rc = op_project(sh, C, C2, slots_r0(sh), kNR0, cl, kNC, st))) return rc;
+  if ((rc = op_project(sh, C, C2, slots_r0(sh), sh->nR0, cl, sh->nC, st))) return rc;
   if ((rc = op_prepare(sh, C2, true, sh->nv, lc, 1, st))) return rc;
   if ((rc = op_dft_inv(sh, C2, spin, sh->nv, st))) return rc;
   return CFFYN_OK;
@@ -158,10 +159,6 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     set_error("n_fields must be 50, 54 or 58");
     return CFFYN_EINVAL;
   }
-  if (d.n_fields != 50) {
-    set_error("n_fields %d: gauge-field groups are not implemented", d.n_fields);
-    return CFFYN_ENOTIMPL;
-  }
   if (d.precision != CFFYN_FP64 && d.precision != CFFYN_MIXED) {
     set_error("precision must be CFFYN_FP64 or CFFYN_MIXED");
     return CFFYN_EINVAL;
@@ -182,6 +179,9 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
   sh->L = d.L;
   sh->R = 2 * d.L + 1;
   sh->nv = d.n_fields;
+  sh->ng = (d.n_fields - 50) / 4;
+  sh->nR0 = 16 + 2 * sh->ng;
+  sh->nC[0] = 11 + sh->ng;
   sh->P = (size_t)d.n_r * d.n_theta * d.n_phi;
   cudaGetDevice(&sh->device);
   {
@@ -213,7 +213,7 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     return CFFYN_OK;
   };
   if ((rc = alloc(&sh->U, nvP)) || (rc = alloc(&sh->kacc, nvP)) || (rc = alloc(&sh->D, 3 * nvP)) ||
-      (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->Rsrc, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, 12 * sh->P)) ||
+      (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->Rsrc, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, (sh->nv == 58 ? 16 : 12) * sh->P)) ||
       (rc = alloc(&sh->red, 2)) || (rc = alloc(&sh->triad, (size_t)9 * sh->N * sh->J)))
     return fail(rc);
   if ((rc = pw_triad_table(sh))) return fail(rc);
@@ -222,13 +222,22 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     if ((rc = alloc(&sh->Uf, nvP))) return fail(rc);
   }
   {
-    int host[33];
-    for (int i = 0; i < 16; ++i) host[i] = i;
-    for (int q = 0; q < 11; ++q) host[16 + q] = 16 + 2 * q;
-    for (int q = 0; q < 5; ++q) host[27 + q] = 38 + 2 * q;
-    host[32] = 48;
-    if (cudaMalloc(&sh->slots, sizeof(host)) != cudaSuccess) return fail(CFFYN_ENOMEM);
-    if (cudaMemcpy(sh->slots, host, sizeof(host), cudaMemcpyHostToDevice) != cudaSuccess)
+    // R0: the 16 real slots of the 50 GHG fields, then H_t and H_r of every
+    // gauge group; C1: the 11 spin-1 pairs, then each gauge group's angular
+    // pair; C2 and C3 as for 50 fields
+    int host[64];
+    int n = 0;
+    for (int i = 0; i < 16; ++i) host[n++] = i;
+    for (int q = 0; q < sh->ng; ++q) {
+      host[n++] = 50 + 4 * q;
+      host[n++] = 51 + 4 * q;
+    }
+    for (int q = 0; q < 11; ++q) host[n++] = 16 + 2 * q;
+    for (int q = 0; q < sh->ng; ++q) host[n++] = 52 + 4 * q;
+    for (int q = 0; q < 5; ++q) host[n++] = 38 + 2 * q;
+    host[n++] = 48;
+    if (cudaMalloc(&sh->slots, n * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
+    if (cudaMemcpy(sh->slots, host, n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(CFFYN_ECUDA);
   }
   if (cudaMalloc(&sh->flag, 64) != cudaSuccess) return fail(CFFYN_ENOMEM);
@@ -281,6 +290,10 @@ static int gauge_derivs(cffyn_shell* sh, cudaStream_t st) {
 
 int cffyn_set_gauge(cffyn_shell* sh, const double* H, void* stream) {
   if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  if (sh->nv != 50) {
+    set_error("n_fields %d: the gauge source is fields 50..53 of the state", sh->nv);
+    return CFFYN_EINVAL;
+  }
   int rc;
   if ((rc = check_ptr(H, "H"))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
@@ -293,6 +306,7 @@ int cffyn_init_gauge_from_state(cffyn_shell* sh, double* u, void* stream) {
   int rc;
   if ((rc = check_ptr(u, "u"))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  if (sh->nv != 50) return pw_gauge_into_state(sh, u, st);
   if ((rc = pw_gauge(sh, u, sh->H, st))) return rc;
   return gauge_derivs(sh, st);
 }
@@ -351,7 +365,7 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
     if ((r = prep(spin, true, P, 1))) return r;
     if ((r = run(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return r;
     if ((r = prep(sh->D, true, lc, 1))) return r;
-    if ((r = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), kNR0, cl, kNC, st); })))
+    if ((r = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st); })))
       return r;
     if ((r = prep(sh->D + nvP, true, lc, 1))) return r;
     return run(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); });
@@ -532,7 +546,9 @@ int cffyn_constraint_norms(cffyn_shell* sh, const double* u, double out[2], void
   if ((rc = pw_cart(sh, sh->D, dcart, 10, false, st))) return rc;
   double* red = sh->red;
   CF_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
-  if ((rc = pw_constraints(sh, u, dcart, sh->H, red, st))) return rc;
+  // the gauge source: the stored one (50 fields) or fields 50..53 of u
+  const bool h_int = sh->nv == 50;
+  if ((rc = pw_constraints(sh, u, dcart, h_int ? sh->H : u + (size_t)50 * sh->P, h_int, red, st))) return rc;
   double h[2];
   CF_CUDA(cudaMemcpyAsync(h, red, sizeof(h), cudaMemcpyDeviceToHost, st));
   CF_CUDA(cudaStreamSynchronize(st));

@@ -34,20 +34,6 @@ void count_launch();
   } while (0)
 
 // --------------------------------------------------------------------------
-// Spin-function layout of the filter (one real slot per Cartesian field).
-// Slots [0, 16): real functions filtered with F^0_m (spin 0, including the
-// real and imaginary parts of the two complex spin-0 components); then
-// complex functions as (re, im) slot pairs: 11 of spin 1 from slot 16, 5 of
-// spin 2 from slot 38, 1 of spin 3 at slot 48.  Gauge groups of 54/58-field
-// states append: H_t (real), H_r (real), H_m (spin 1) per group, stored after
-// slot 50 as [R0 R0 re im] per group.
-struct SpinLayout {
-  int n_real;         // number of real spin-0 slots
-  int n_cplx[4];      // complex pairs per spin 0..3 (spin 0 pairs are counted as reals)
-  int cplx_base[4];   // first slot of each spin class
-};
-
-// --------------------------------------------------------------------------
 // Split-precision operator for the tcgen05 core: W cut into row groups of
 // `rows` = 48 (P <= 48) or 96 rows and k-steps of 16 columns; per (group,
 // k-step) eleven BF16 digit slices of rows x 16 in the K-major no-swizzle
@@ -94,11 +80,18 @@ struct cffyn_shell {
   // m = 0..L, tFC per spin 1..3
   cffyn::TcOp tDr, tDth2, tDph, tFan, tFsy, tF0, tFC[3];
 
-  cffyn::SpinLayout spin;
+  // spin slots of the filter (one real slot per Cartesian field): nR0 real
+  // functions filtered with F^0_m (spin 0, including the real and imaginary
+  // parts of the two complex spin-0 components), then nC[s - 1] complex
+  // functions of spin s as (re, im) slot pairs; `slots` holds the slot
+  // indices of each list.  Each gauge group of a 54/58-field state adds two
+  // real slots (H_t, H_r) and one spin-1 pair.
+  int ng = 0;                    // gauge groups: (nv - 50) / 4
+  int nR0 = 16, nC[3] = {11, 5, 1};
 
   // gauge
   double* H = nullptr;    // [4][P]
-  double* dH = nullptr;   // [3][4][P]
+  double* dH = nullptr;   // [3][4][P] d_i H_a, + [4][P] d_t H_a for 58 fields
   bool gauge_set = false;
 
   // workspace
@@ -112,7 +105,7 @@ struct cffyn_shell {
   double* red = nullptr;   // device reduction words (2 doubles)
   int* flag = nullptr;     // device non-finite flag
   int* flag_host = nullptr;  // pinned host copy of the flag
-  int* slots = nullptr;    // device slot lists: R0 (16) | C1 (11) | C2 (5) | C3 (1)
+  int* slots = nullptr;    // device slot lists: R0 (nR0) | C1 (nC[0]) | C2 (nC[1]) | C3 (nC[2])
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
 
   // graph of one RK4 step

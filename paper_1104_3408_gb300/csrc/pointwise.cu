@@ -106,8 +106,9 @@ __device__ __forceinline__ void unrot_mat(const Triad<T>& t, const T O[3][3], T 
     for (int b = 0; b < 3; ++b) Tm[a][b] = X[a][0] * t.R[0][b] + X[a][1] * t.R[1][b] + X[a][2] * t.R[2][b];
 }
 
-// Slot assignment (see SpinLayout in common.cuh); the numbers below are the
-// slots written by k_decompose and read back by k_reconstruct.
+// Slot assignment: 16 real spin-0 slots, then (re, im) pairs of spin 1 from
+// slot 16, of spin 2 from slot 38 and of spin 3 at slot 48; the numbers
+// below are the slots written by k_decompose and read back by k_reconstruct.
 #define SLOT_R0(n) (n)
 #define SLOT_C1(q) (16 + 2 * (q))
 #define SLOT_C2(q) (38 + 2 * (q))
@@ -129,7 +130,12 @@ template <> constexpr bool kIn<ff> = true;
 // holds at most the 18 components of Phi_ijk:
 //   0: g_tt, Pi_tt   1: g_ti   2: Pi_ti   3: Phi_itt   4: g_ij   5: Pi_ij
 //   6: Phi_itj       7: Phi_ijk
+// and for 54/58-field states the gauge groups 8: H_a (fields 50..53) and
+// 9: d_t H_a (54..57), each a scalar and a vector; group 8 + g writes the
+// slots 50 + 4g: H_t and the radial component (spin 0), then the spin-1
+// pair of the angular components.
 constexpr int kGroups = 8;
+constexpr int kMaxNv = 58;
 
 template <class T, bool FI>
 __device__ __forceinline__ void decompose_group(int grp, const double* __restrict__ in,
@@ -190,6 +196,19 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
       st<kIn<T>>(out, P, p, SLOT_C2(2) + 1, O[1][2] + O[2][1]);
       st<kIn<T>>(out, P, p, SLOT_R0(12), O[1][1] + O[2][2]);
       st<kIn<T>>(out, P, p, SLOT_R0(13), O[2][1] - O[1][2]);
+      break;
+    }
+    case 8:
+    case 9: {
+      const int fb = 50 + 4 * (grp - 8);
+      st<kIn<T>>(out, P, p, fb, ld<T, FI>(in, P, p, fb));
+      T v[3], o[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) v[a] = ld<T, FI>(in, P, p, fb + 1 + a);
+      rot_vec(t, v, o);
+      st<kIn<T>>(out, P, p, fb + 1, o[0]);
+      st<kIn<T>>(out, P, p, fb + 2, o[1]);
+      st<kIn<T>>(out, P, p, fb + 3, o[2]);
       break;
     }
     default: {
@@ -313,6 +332,18 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
         for (int b = 0; b < 3; ++b) emit(20 + 10 * a + SI(0, b + 1), Tm[a][b]);
       break;
     }
+    case 8:
+    case 9: {
+      const int fb = 50 + 4 * (grp - 8);
+      emit(fb, ld<T, kIn<T>>(sp, P, p, fb));
+      T o[3] = {ld<T, kIn<T>>(sp, P, p, fb + 1), ld<T, kIn<T>>(sp, P, p, fb + 2),
+                ld<T, kIn<T>>(sp, P, p, fb + 3)};
+      T v[3];
+      unrot_vec(t, o, v);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) emit(fb + 1 + a, v[a]);
+      break;
+    }
     default: {
       T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];
       Pr[0] = ld<T, kIn<T>>(sp, P, p, SLOT_R0(10));
@@ -386,8 +417,10 @@ __host__ __device__ constexpr bool in_group(int G, int f) {
        : G == 3 ? (f == 20 || f == 30 || f == 40)
        : G == 4 ? (f >= 4 && f <= 9)
        : G == 5 ? (f >= 14 && f <= 19)
-       : G == 6 ? (f >= 20 && (f % 10) >= 1 && (f % 10) <= 3)
-                : (f >= 20 && (f % 10) >= 4);
+       : G == 6 ? (f >= 20 && f < 50 && (f % 10) >= 1 && (f % 10) <= 3)
+       : G == 7 ? (f >= 20 && f < 50 && (f % 10) >= 4)
+       : G == 8 ? (f >= 50 && f < 54)
+                : (f >= 54 && f < 58);
 }
 
 // mode: 0 = write filtered tensor to `dst`;
@@ -410,7 +443,7 @@ __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp
                                                    bool& bad) {
   const long long P = geo.P;
   using SI_ = Store<T, kIn<T>>;
-  T kv[50];
+  T kv[kMaxNv];
   if (mode <= 4) {
     const int i = (int)((p / geo.n_r) % geo.N);
     const int jj = (int)(p / ((long long)geo.n_r * geo.N));
@@ -418,13 +451,13 @@ __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp
     reconstruct_group<T>(G, sp, P, p, t, [&](int f, T v) { kv[f] = v; });
   } else {
 #pragma unroll
-    for (int f = 0; f < 50; ++f)
+    for (int f = 0; f < kMaxNv; ++f)
       if (in_group(G, f)) kv[f] = ld<T, kIn<T>>(sp, P, p, f);
   }
   constexpr bool kPair = kIn<T>;  // mixed path: the step's initial state also as pairs in uf
   if (KIND == 0) {
 #pragma unroll
-    for (int f = 0; f < 50; ++f)
+    for (int f = 0; f < kMaxNv; ++f)
       if (in_group(G, f)) {
         Store<T, FD>::st(dst, (long long)f * P + p, kv[f]);
         if (kPair && uf) SI_::st(uf, (long long)f * P + p, kv[f]);
@@ -432,10 +465,10 @@ __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp
     return;
   }
   const int stage = (mode - 1) % 4;  // 0..3 for modes 1..8; KIND 2 is stage 3
-  double uv[50];
-  T ub[50], ka[50];
+  double uv[kMaxNv];
+  T ub[kMaxNv], ka[kMaxNv];
 #pragma unroll
-  for (int f = 0; f < 50; ++f)
+  for (int f = 0; f < kMaxNv; ++f)
     if (in_group(G, f)) {
       const long long o = (long long)f * P + p;
       if (kPair && KIND == 1)
@@ -447,7 +480,7 @@ __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp
   if (KIND == 1) {
     const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
 #pragma unroll
-    for (int f = 0; f < 50; ++f)
+    for (int f = 0; f < kMaxNv; ++f)
       if (in_group(G, f)) {
         const long long o = (long long)f * P + p;
         bad |= !finite_s(kv[f]);
@@ -458,7 +491,7 @@ __device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp
   } else {
     const T sixth = S<T>::c(dt / 6.0);
 #pragma unroll
-    for (int f = 0; f < 50; ++f)
+    for (int f = 0; f < kMaxNv; ++f)
       if (in_group(G, f)) {
         const long long o = (long long)f * P + p;
         bad |= !finite_s(kv[f]);
@@ -487,7 +520,9 @@ __global__ void __launch_bounds__(128) k_reconstruct(const double* __restrict__ 
     case 4: CFFYN_RECON(4); break;
     case 5: CFFYN_RECON(5); break;
     case 6: CFFYN_RECON(6); break;
-    default: CFFYN_RECON(7); break;
+    case 7: CFFYN_RECON(7); break;
+    case 8: CFFYN_RECON(8); break;
+    default: CFFYN_RECON(9); break;
   }
 #undef CFFYN_RECON
   if (bad) atomicOr(flag, 1);
@@ -599,7 +634,7 @@ __global__ void k_constraints(const double* __restrict__ u, const double* __rest
 // in_pairs: the input is a pair-stored internal buffer (else an FP64 array)
 int pw_decompose(const cffyn_shell* sh, const double* in, double* out, bool in_pairs, cudaStream_t st) {
   Geo g = geo_of(sh);
-  const dim3 grid(blocks_for(g.P, 128), kGroups);
+  const dim3 grid(blocks_for(g.P, 128), kGroups + sh->ng);
   if (sh->d.precision != CFFYN_MIXED)
     k_decompose<double, false><<<grid, 128, 0, st>>>(in, out, g);
   else if (in_pairs)
@@ -616,7 +651,7 @@ int pw_decompose(const cffyn_shell* sh, const double* in, double* out, bool in_p
 int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mode, double* u, double* U,
                    double* kacc, double* uf, double dt, int* flag, cudaStream_t st) {
   Geo g = geo_of(sh);
-  const dim3 grid(blocks_for(g.P, 128), kGroups);
+  const dim3 grid(blocks_for(g.P, 128), kGroups + sh->ng);
   // kernel instance by stage kind: 0 filtered result, 1 stages 1-3, 2 last stage
   const int kind = mode == 0 ? 0 : ((mode - 1) % 4 == 3 ? 2 : 1);
   if (sh->d.precision == CFFYN_MIXED) {
@@ -679,6 +714,17 @@ int pw_gauge(const cffyn_shell* sh, const double* u, double* H, cudaStream_t st)
   return CFFYN_OK;
 }
 
+// 54/58-field states: H_a = -Gamma_a(u) into fields 50..53 of u (FP64) and
+// d_t H_a (54..57) set to zero
+int pw_gauge_into_state(const cffyn_shell* sh, double* u, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  k_gauge<false><<<blocks_for(g.P, 128), 128, 0, st>>>(u, u + (size_t)50 * g.P, g);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  if (sh->nv == 58) CF_CUDA(cudaMemsetAsync(u + (size_t)54 * g.P, 0, (size_t)4 * g.P * sizeof(double), st));
+  return CFFYN_OK;
+}
+
 // FP64 caller array -> internal storage
 int pw_to_internal(const cffyn_shell* sh, const double* in, double* out, long long n, cudaStream_t st) {
   if (sh->d.precision == CFFYN_MIXED)
@@ -690,10 +736,12 @@ int pw_to_internal(const cffyn_shell* sh, const double* in, double* out, long lo
   return CFFYN_OK;
 }
 
-int pw_constraints(const cffyn_shell* sh, const double* u, const double* dcart, const double* H, double* red,
-                   cudaStream_t st) {
+// h_internal: H is the library's gauge buffer (internal storage), else FP64
+// (fields 50..53 of a 54/58-field state)
+int pw_constraints(const cffyn_shell* sh, const double* u, const double* dcart, const double* H, bool h_internal,
+                   double* red, cudaStream_t st) {
   Geo g = geo_of(sh);
-  if (sh->d.precision == CFFYN_MIXED)
+  if (sh->d.precision == CFFYN_MIXED && h_internal)
     k_constraints<true><<<blocks_for(g.P, 128), 128, 0, st>>>(u, dcart, H, g, red);
   else
     k_constraints<false><<<blocks_for(g.P, 128), 128, 0, st>>>(u, dcart, H, g, red);

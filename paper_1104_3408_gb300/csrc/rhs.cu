@@ -15,6 +15,9 @@
 //                with the chain rule (eq. dvdx) contracted into the shift and
 //                inverse metric once per point, plus the boundary condition
 //                on the outermost sphere.
+//   k_gauge_rhs  54/58-field states only, ahead of k_rhs_gamma: H_a and its
+//                derivatives from the state, and the gauge fields' own
+//                right-hand sides.
 //
 // Source buffer src[50][P]: [0,10) source of d_t Pi_ab, [10,40) source of
 // d_t Phi_iab (10 + 10 i + s), 40 alpha, [41,44) beta^i, [44,50) gamma^ij
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restric
                                                          const double* __restrict__ H,
                                                          const double* __restrict__ dH,
                                                          double* __restrict__ src, double* __restrict__ out,
-                                                         Geo geo) {
+                                                         Geo geo, int dtH) {
   __shared__ T sm[kGamSlots * kRhsBlock];
   const Slots<T, kRhsBlock> V{sm};
   const long long P = geo.P;
@@ -147,8 +150,13 @@ __global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restric
     for (int s = 0; s < 10; ++s) {
       const int a = s < 4 ? 0 : (s < 7 ? 1 : (s < 9 ? 2 : 3));
       const int b = s - (a == 0 ? 0 : (a == 1 ? 3 : (a == 2 ? 5 : 6)));
-      const T dHab = a == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (a - 1) * 4 + b);
-      const T dHba = b == 0 ? zero : ldA<T, kInt<T>>(dH, P, p, (b - 1) * 4 + a);
+      // d_a H_b: rows (x, b) = 4 x + b of dH for a = x + 1; d_t H_b is row
+      // 12 + b when the gauge source is evolved with its time derivative
+      // (58 fields), else zero
+      const T dHab = a == 0 ? (dtH ? ldA<T, kInt<T>>(dH, P, p, 12 + b) : zero)
+                            : ldA<T, kInt<T>>(dH, P, p, (a - 1) * 4 + b);
+      const T dHba = b == 0 ? (dtH ? ldA<T, kInt<T>>(dH, P, p, 12 + a) : zero)
+                            : ldA<T, kInt<T>>(dH, P, p, (b - 1) * 4 + a);
       Acc<T> acc;
       acc.fma_(half, dHab + dHba);
 #pragma unroll
@@ -503,24 +511,81 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
   }
 }
 
+// Gauge fields of 54/58-field states (App. A.1; eq. gauge with H_a a field
+// of the state): H_a from fields 50..53 into the gauge buffer, d_i H_a from
+// their spherical derivatives by the chain rule (eq. dvdx), and for 58
+// fields d_t H_a = G_a (fields 54..57) as rows 12..15 of dH.  The gauge
+// fields' right-hand sides: d_t H_a = G_a for 58 fields (0 for 54) and
+// d_t G_a = 0; the outer boundary condition leaves them alone.
+template <class T, bool FU, bool FO>
+__global__ void __launch_bounds__(128) k_gauge_rhs(const double* __restrict__ u, const double* __restrict__ D,
+                                                   double* __restrict__ H, double* __restrict__ dH,
+                                                   double* __restrict__ out, Geo geo) {
+  const long long P = geo.P;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int k = (int)(p % geo.n_r);
+  const int i = (int)((p / geo.n_r) % geo.N);
+  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const int nv = geo.nv;
+  const Jac<T> J = jacobian<T>(geo, k, i, jj);
+  const T zero = S<T>::c(0.0);
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    stA<T, kInt<T>>(H, P, p, b, ldA<T, FU>(u, P, p, 50 + b));
+    T ds[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) ds[m] = Store<T, kInt<T>>::ld(D, ((long long)m * nv + 50 + b) * P + p);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Acc<T> a;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) a.fma_(J.j[x][m], ds[m]);
+      stA<T, kInt<T>>(dH, P, p, 4 * x + b, a.get());
+    }
+    if (nv == 58) {
+      const T Gb = ldA<T, FU>(u, P, p, 54 + b);
+      stA<T, kInt<T>>(dH, P, p, 12 + b, Gb);
+      stA<T, FO>(out, P, p, 50 + b, Gb);
+      stA<T, FO>(out, P, p, 54 + b, zero);
+    } else {
+      stA<T, FO>(out, P, p, 50 + b, zero);
+    }
+  }
+}
+
 // stage = 0: all three kernels; 1: sources with Christoffels; 2: quadratic
 // sources; 3: principal parts + boundary.  u_pairs: the state is a pair-stored
 // internal buffer (the stage states of the mixed path); out_pairs: the output
-// is the internal rhs buffer (else an FP64 caller array).
+// is the internal rhs buffer (else an FP64 caller array); on the mixed path
+// both are pairs (a step) or neither (cffyn_rhs).
 int pw_rhs_part(const cffyn_shell* sh, const double* u, const double* D, double* out, int stage,
                 bool u_pairs, bool out_pairs, cudaStream_t st) {
   Geo g = geo_of(sh);
   const unsigned nb = blocks_for(g.P, 128), nbr = blocks_for(g.P, kRhsBlock);
   const bool mixed = sh->d.precision == CFFYN_MIXED;
+  if (mixed && u_pairs != out_pairs) {
+    set_error("internal: right-hand side storage (state %d, output %d) not instantiated", (int)u_pairs,
+              (int)out_pairs);
+    return CFFYN_EINVAL;
+  }
   if (stage == 0 || stage == 1) {
+    const int dtH = sh->nv == 58;
+    if (sh->ng > 0) {
+      if (!mixed)
+        k_gauge_rhs<double, false, false><<<nb, 128, 0, st>>>(u, D, sh->H, sh->dH, out, g);
+      else if (u_pairs)
+        k_gauge_rhs<ff, true, true><<<nb, 128, 0, st>>>(u, D, sh->H, sh->dH, out, g);
+      else
+        k_gauge_rhs<ff, false, false><<<nb, 128, 0, st>>>(u, D, sh->H, sh->dH, out, g);
+      count_launch();
+    }
     if (!mixed)
-      k_rhs_gamma<double, false, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
-    else if (u_pairs && out_pairs)
-      k_rhs_gamma<ff, true, true><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
-    else if (out_pairs)
-      k_rhs_gamma<ff, false, true><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+      k_rhs_gamma<double, false, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g, dtH);
+    else if (u_pairs)
+      k_rhs_gamma<ff, true, true><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g, dtH);
     else
-      k_rhs_gamma<ff, false, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g);
+      k_rhs_gamma<ff, false, false><<<nbr, kRhsBlock, 0, st>>>(u, sh->H, sh->dH, sh->Rsrc, out, g, dtH);
     count_launch();
   }
   if (stage == 0 || stage == 2) {
