@@ -66,7 +66,8 @@ def _workload(name):
 def _state(w):
     from paper_1104_3408_gb300 import inputs
     return inputs.kerr_schild_state(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"],
-                                    amp=w["amp"], ell=w["ell"], seed=w["seed"])
+                                    n_fields=w.get("n_fields", 50), amp=w["amp"], ell=w["ell"],
+                                    seed=w["seed"])
 
 
 def _peaks():
@@ -226,7 +227,8 @@ def run_ours(args, rank, local_rank, ws, dist):
     units_per_step = P * w["n_fields"]
     u0 = _state(w)
 
-    sh = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, precision=cffyn.MIXED)
+    sh = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, n_fields=w["n_fields"],
+                     precision=cffyn.MIXED)
     dt = w["lam"] * sh.default_dt() / 0.25
     u = torch.from_numpy(u0).cuda()
     sh.init_gauge_from_state(u)
@@ -278,7 +280,8 @@ def run_ours(args, rank, local_rank, ws, dist):
     # ---- plain FP64 GPU path on the same workload
     fp64 = None
     if not args.no_fp64:
-        s64 = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, precision=cffyn.FP64)
+        s64 = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, n_fields=w["n_fields"],
+                          precision=cffyn.FP64)
         v = torch.from_numpy(u0).cuda()
         s64.init_gauge_from_state(v)
         vf = torch.empty_like(v)
@@ -357,12 +360,226 @@ def run_ours(args, rank, local_rank, ws, dist):
     return out
 
 
+def _oracle_state(w, u0):
+    """The bench state with the gauge source of 54/58-field states filled in
+    (H_a = -Gamma_a in fields 50..53), as the library's gauge initialisation does."""
+    from oracle import ghg
+    if w["n_fields"] == 50:
+        return u0
+    u = u0.copy()
+    u[50:54] = ghg.gauge_source_from_state(u[:50].reshape(50, -1)).reshape((4,) + u.shape[1:])
+    return u
+
+
+def _shell_units(d):
+    return d["n_r"] * d["n_theta"] * d["n_phi"] * 50
+
+
+def _shells_for_rank(descs, rank, ws):
+    """Greedy longest-first assignment of the batch's shells to ranks by
+    points x fields; returns this rank's shell indices."""
+    order = sorted(range(len(descs)), key=lambda i: (-_shell_units(descs[i]), i))
+    load = [0] * ws
+    mine = []
+    for i in order:
+        r = min(range(ws), key=lambda k: (load[k], k))
+        load[r] += _shell_units(descs[i])
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def run_batch(args, rank, local_rank, ws, dist):
+    """The uneven-shell batch: every shell of this rank advanced by one batch
+    RK4 step per graph launch (cffyn_batch_rk4_step).  Across ranks the shells
+    are split by cost (total work fixed: strong scaling)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3408_gb300 import cffyn, inputs
+
+    torch.cuda.set_device(local_rank)
+    w = _workload(args.workload)
+    descs = inputs.shell_batch(w["n_shells"], seed=w["seed"])
+    mine = _shells_for_rank(descs, rank, ws)
+
+    def state(d):
+        return inputs.kerr_schild_state(d["n_r"], d["n_theta"], d["n_phi"], d["r_in"], d["r_out"],
+                                        amp=d["amp"], ell=d["ell"], seed=d["seed"])
+
+    def make(d, prec):
+        sh = cffyn.Shell(d["n_r"], d["n_theta"], d["n_phi"], d["r_in"], d["r_out"], d["L"],
+                         precision=prec)
+        u = torch.from_numpy(state(d)).cuda()
+        sh.init_gauge_from_state(u)
+        v = torch.empty_like(u)
+        sh.filter(u, v)
+        return sh, v
+
+    t_setup = time.perf_counter()
+    shells, us = zip(*[make(descs[i], cffyn.MIXED) for i in mine])
+    shells, us = list(shells), list(us)
+    t_setup = time.perf_counter() - t_setup
+    units = sum(_shell_units(descs[i]) for i in mine)
+    units_all = sum(_shell_units(d) for d in descs)
+    b = cffyn.Batch(shells)
+    st = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        b.rk4_step(us, None, 1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 1.0:
+        b.rk4_step(us, None, 1)
+    torch.cuda.synchronize()
+    a_ev = torch.cuda.Event(enable_timing=True)
+    b_ev = torch.cuda.Event(enable_timing=True)
+    a_ev.record(st)
+    b.rk4_step(us, None, args.steps)
+    b_ev.record(st)
+    torch.cuda.synchronize()
+    t_ms = a_ev.elapsed_time(b_ev)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    t_max = t_ms
+    if dist:
+        t = torch.tensor([t_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = units_all * args.steps / (t_max * 1e-3) if dist else units * args.steps / (t_max * 1e-3)
+    if rank != 0:
+        b.destroy()
+        return None
+
+    # ---- the same shells stepped one by one (no batch), mixed and FP64
+    def loop_rate(shs, vs, k):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(k):
+            for sh, v in zip(shs, vs):
+                sh.rk4_step(v, 0.0, 1)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return units * k / (e0.elapsed_time(e1) * 1e-3)
+
+    for sh, v in zip(shells, us):
+        sh.rk4_step(v, 0.0, 1)      # capture each shell's own graph
+    mixed_loop = loop_rate(shells, us, 2)
+    # kernel launches of one shell's step (the same sequence for every
+    # 50-field mixed shell), from a traced lone step
+    shells[0].set_trace(True)
+    shells[0].rk4_step(us[0], 0.0, 1)
+    launches_per_shell_step = sum(shells[0].get_trace()[1].values())
+    shells[0].set_trace(False)
+    fp64 = None
+    if not args.no_fp64:
+        s64, v64 = zip(*[make(descs[i], cffyn.FP64) for i in mine])
+        for sh, v in zip(s64, v64):
+            sh.rk4_step(v, 0.0, 1)
+        fp64_loop = loop_rate(s64, v64, 1)
+        # accuracy: 100 steps of the first 8 shells, mixed batch vs FP64 loop
+        k8 = min(8, len(mine))
+        s8, u8 = zip(*[make(descs[i], cffyn.MIXED) for i in mine[:k8]])
+        b8 = cffyn.Batch(list(s8))
+        _, r8 = zip(*[make(descs[i], cffyn.FP64) for i in mine[:k8]])
+        b8.rk4_step(list(u8), None, 100)
+        for sh, v in zip(s64[:k8], r8):
+            sh.rk4_step(v, 0.0, 100)
+        err = max(float((x - y).abs().max() / y.abs().max()) for x, y in zip(u8, r8))
+        b8.destroy()
+        for sh in list(s8) + list(s64):
+            sh.destroy()
+        fp64 = {"per_shell_loop_value": fp64_loop, "batch_over_fp64_loop": value / fp64_loop,
+                "err_fields_100_steps_vs_fp64_gpu": err, "err_shells": k8}
+
+    # ---- end to end with host buffers: copy in, one batch step, copy out
+    hs = [u.cpu().pin_memory() for u in us]
+    ke = 3
+    b.rk4_step(us, None, 1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(ke):
+        for u, h in zip(us, hs):
+            u.copy_(h, non_blocking=True)
+        b.rk4_step(us, None, 1)
+        for u, h in zip(us, hs):
+            h.copy_(u, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    nbytes = int(sum(u.numel() for u in us) * 8)
+    e2e = {"value": units * ke / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": ke}
+
+    # ---- whole-step tensor roofline (a lower bound of the operator family's share)
+    hbm, bf16s, peak_kind = _peaks()
+    fl = 0.0
+    for i in mine:
+        d = descs[i]
+        per = 2 * d["n_r"] + 16 * d["n_theta"] + 2 * (d["L"] + 1)
+        fl += 4.0 * per * _shell_units(d)
+    achieved = PAIRS * fl * args.steps / (t_ms * 1e-3) / 1e12
+    roof = {"bound": "tensor", "kernel": "k_op_tc (operator work over the whole batch step time)",
+            "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
+            "traffic": None, "peak_source": f"bf16_tflops_sustained ({peak_kind})",
+            "scope": "divides by the whole step (all kernel families), so it is a lower bound "
+                     "of the operator kernels' own fraction"}
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        d = descs[mine[0]]
+        wd = dict(d, n_fields=50, name="batch shell 0")
+        cpu = _cpu_baseline(wd, state(d))
+        cpu["sample"] = ("one RK4 stage of the batch's first shell "
+                         f"({d['n_r']}x{d['n_theta']}x{d['n_phi']}) = 1/4 step; numpy FP64")
+    nshapes = {}
+    for i in mine:
+        k = f"{descs[i]['n_r']}x{descs[i]['n_theta']}x{descs[i]['n_phi']}"
+        nshapes[k] = nshapes.get(k, 0) + 1
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "mixed: bf16-digit tensor products (exact fp32 sums, int64 recombination), "
+                 "fp32-pair pointwise, f64 state",
+        "data": "synthetic (seeded Kerr-Schild + l<=4 perturbations, amplitudes log-uniform "
+                "1e-6..1e-3)",
+        "config": {"workload": w["name"], "n_shells": len(descs), "shells_this_rank": len(mine),
+                   "pt_field_per_step": units_all, "shapes": nshapes, "n_fields": 50,
+                   "L": "n_theta - 2", "r": [1.8, 11.0], "filter": "Yn on every stage rhs",
+                   "precision": "mixed", "parallelism": f"shells split by cost over {ws} rank(s)",
+                   "l2": f"inputs larger than L2 ({units * 8 / 1e9:.1f} GB of state per rank)",
+                   "setup_s": t_setup},
+        "roofline": roof,
+        "mixed_per_shell_loop_value": mixed_loop,
+        "batch_over_mixed_loop": value / mixed_loop,
+        "gpu_launches": launches_per_shell_step * len(mine) * args.steps,
+        "launches_per_shell_step": launches_per_shell_step,
+        "fp64_gpu": fp64,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    b.destroy()
+    for sh in shells:
+        sh.destroy()
+    return out
+
+
 def _cpu_baseline(w, u0, nthreads=None):
     """The oracle, as it stands, on one RK4 stage (derivatives + right-hand side
     + boundary + Yn filter) of the same workload: a quarter of a step."""
     import oracle
     t0 = time.perf_counter()
-    sh = oracle.OracleShell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"])
+    sh = oracle.OracleShell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"],
+                            n_fields=w["n_fields"])
+    u0 = _oracle_state(w, u0)
     sh.init_gauge_from_state(u0)
     _ = sh.sf
     t1 = time.perf_counter()
@@ -382,9 +599,10 @@ def run_reference(args, rank):
     if rank != 0:
         return None
     w = _workload(args.workload)
-    u0 = _state(w)
+    u0 = _oracle_state(w, _state(w))
     import oracle
-    sh = oracle.OracleShell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"])
+    sh = oracle.OracleShell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"],
+                            n_fields=w["n_fields"])
     sh.init_gauge_from_state(u0)
     _ = sh.sf
     for _ in range(min(args.warmup, 1)):
@@ -426,7 +644,7 @@ def run_profile_step(args):
 
     w = _workload(args.workload)
     sh = cffyn.Shell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"],
-                     precision=cffyn.MIXED)
+                     n_fields=w["n_fields"], precision=cffyn.MIXED)
     u = torch.from_numpy(_state(w)).cuda()
     sh.init_gauge_from_state(u)
     prof = sh.profile_step(u)
@@ -442,8 +660,13 @@ def main():
         print(json.dumps(run_profile_step(args)), flush=True)
         return
     rank, local_rank, ws, dist = _dist()
+    batch = "n_shells" in _workload(args.workload)
     if args.impl == "reference":
-        out = run_reference(args, rank)
+        out = run_reference(args, rank) if not batch else {
+            "impl": "reference", "unavailable": "the reference arm times the oracle on the "
+            "single-shell workloads only"}
+    elif batch:
+        out = run_batch(args, rank, local_rank, ws, dist)
     else:
         out = run_ours(args, rank, local_rank, ws, dist)
     if rank == 0 and out is not None:

@@ -150,6 +150,34 @@ CFFYN_API int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* 
  * (the results are then invalid; the context stays usable). */
 CFFYN_API int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream);
 
+/* Batch of independent shells advanced together (the uneven-shell batch;
+ * the shells need not share sizes, field counts, precision or filter mode).
+ * The batch borrows the handles: they must stay alive, on the device that
+ * is current at cffyn_create_batch, until cffyn_destroy_batch, and must not
+ * be used by other calls while a batch call runs.  A shell may appear in one
+ * batch position only (its workspace is per handle): duplicates are
+ * CFFYN_EINVAL.  The batch owns only its streams, events, graphs and a
+ * pinned flag array.  n >= 1. */
+typedef struct cffyn_batch cffyn_batch;
+CFFYN_API int cffyn_create_batch(int n, cffyn_shell* const* shells, cffyn_batch** out);
+
+/* n_steps RK4 steps (as cffyn_rk4_step, Sec. 2.5) of every shell of the
+ * batch: u is a host array of n device state pointers (u[i] in the layout of
+ * shells[i]); dt a host array of n step sizes (NULL, or an entry <= 0,
+ * selects that shell's cffyn_default_dt).  One step of the whole batch is one
+ * CUDA graph launch in which each shell's step is an independent branch, so
+ * that small shells run side by side on the GPU; the graph is captured on
+ * the first call and replayed while u and dt stay the same.  Every 50-field
+ * shell needs its gauge (CFFYN_EINVAL before anything is enqueued
+ * otherwise).  Synchronises `stream` at the end and returns
+ * CFFYN_ETIMEOUT / CFFYN_ENONFINITE as cffyn_rk4_step does, naming the first
+ * shell that reported it. */
+CFFYN_API int cffyn_batch_rk4_step(cffyn_batch* b, double* const* u, const double* dt, int n_steps,
+                                   void* stream);
+
+/* Releases the batch (not its shells).  NULL is allowed. */
+CFFYN_API int cffyn_destroy_batch(cffyn_batch* b);
+
 /* RMS over all points of C_iab = d_i g_ab - Phi_iab (30 components, numerical
  * derivative) and of C_a = H_a + Gamma_a (4 components) (App. A.1), reduced
  * in FP64 on the device; out[0] = C_iab RMS, out[1] = C_a RMS (host memory).

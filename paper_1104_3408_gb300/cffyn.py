@@ -24,6 +24,7 @@ EXPORTED = [
     "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_constraint_norms",
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
+    "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch",
 ]
 PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
                   "dft_fwd", "project", "dft_inv", "reconstruct", "field_exp"]
@@ -78,6 +79,9 @@ def load(path=LIB_PATH):
         "cffyn_set_trace": ([vp, i], i),
         "cffyn_get_trace": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_longlong)], i),
+        "cffyn_create_batch": ([i, ctypes.POINTER(vp), ctypes.POINTER(vp)], i),
+        "cffyn_batch_rk4_step": ([vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double), i, vp], i),
+        "cffyn_destroy_batch": ([vp], i),
         "cffyn_last_error": ([], ctypes.c_char_p),
         "cffyn_version": ([], ctypes.c_char_p),
     }
@@ -219,6 +223,38 @@ class Shell:
         return a
 
 
+class Batch:
+    """Independent shells advanced together (a cffyn_batch handle).  The
+    batch borrows the Shell objects and keeps references to them."""
+
+    def __init__(self, shells):
+        self.shells = list(shells)
+        arr = (ctypes.c_void_p * len(self.shells))(*[s.h.value for s in self.shells])
+        h = ctypes.c_void_p()
+        _check(load().cffyn_create_batch(len(self.shells), arr, ctypes.byref(h)))
+        self.h = h
+
+    def rk4_step(self, us, dts=None, n_steps=1, stream=None):
+        n = len(self.shells)
+        if len(us) != n:
+            raise ValueError(f"{n} states expected")
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(u, "u[i]").value for u in us])
+        dt_arr = None if dts is None else (ctypes.c_double * n)(*[float(d) for d in dts])
+        _check(load().cffyn_batch_rk4_step(self.h, ptrs, dt_arr, int(n_steps), _stream(stream)))
+        return us
+
+    def destroy(self):
+        if self.h:
+            load().cffyn_destroy_batch(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
 # C-ABI names, one to one (module-level functions taking a Shell)
 def create_shell(n_r, n_theta, n_phi, r_in, r_out, L, **kw):
     return Shell(n_r, n_theta, n_phi, r_in, r_out, L, **kw)
@@ -238,6 +274,18 @@ def rk4_step(sh, u, dt=0.0, n_steps=1, stream=None):
 
 def derivs(sh, u, out, stream=None):
     return sh.derivs(u, out, stream)
+
+
+def create_batch(shells):
+    return Batch(shells)
+
+
+def batch_rk4_step(b, us, dts=None, n_steps=1, stream=None):
+    return b.rk4_step(us, dts, n_steps, stream)
+
+
+def destroy_batch(b):
+    b.destroy()
 
 
 def destroy(sh):

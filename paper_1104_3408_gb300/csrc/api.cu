@@ -442,15 +442,56 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
   return CFFYN_OK;
 }
 
+extern "C++" {
+namespace cffyn {
+
+// One RK4 step enqueued on st without trace marks (a branch of a batch graph).
+int enqueue_step_branch(cffyn_shell* sh, double* u, double dt, cudaStream_t st) {
+  auto run = [](int, auto&& fn) -> int { return fn(); };
+  return step_sequence(sh, u, dt, st, run);
+}
+
+// Work in front of the first step of a call: clear the finiteness flag and,
+// on the mixed path, copy u into the pair-stored initial state Uf (the last
+// stage of every step keeps Uf current afterwards).
+int enqueue_step_prologue(cffyn_shell* sh, double* u, cudaStream_t st) {
+  CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
+  if (sh->Uf) return pw_to_internal(sh, u, sh->Uf, (long long)sh->nv * sh->P, st);
+  return CFFYN_OK;
+}
+
+// Status of a step call from the flag word its kernels set.
+int step_flag_status(int flag) {
+  if (flag & 2) {
+    set_error("a bounded tensor-core wait gave up (operator results are invalid)");
+    return CFFYN_ETIMEOUT;
+  }
+  if (flag) {
+    set_error("non-finite value in a stage right-hand side");
+    return CFFYN_ENONFINITE;
+  }
+  return CFFYN_OK;
+}
+
+int check_step_ready(const cffyn_shell* sh) {
+  if (sh->nv == 50 && !sh->gauge_set) {
+    set_error("gauge source not set (cffyn_set_gauge / cffyn_init_gauge_from_state)");
+    return CFFYN_EINVAL;
+  }
+  return CFFYN_OK;
+}
+
+int check_state_ptr(const void* p, const char* what) { return check_ptr(p, what); }
+
+}  // namespace cffyn
+}  // extern "C++"
+
 int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream) {
   if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
   int rc;
   if ((rc = check_ptr(u, "u"))) return rc;
   if (n_steps < 0) { set_error("n_steps < 0"); return CFFYN_EINVAL; }
-  if (sh->nv == 50 && !sh->gauge_set) {
-    set_error("gauge source not set (cffyn_set_gauge / cffyn_init_gauge_from_state)");
-    return CFFYN_EINVAL;
-  }
+  if ((rc = check_step_ready(sh))) return rc;
   if (n_steps == 0) return CFFYN_OK;
   if (!(dt > 0)) dt = sh->dt_default;
   cudaStream_t st = (cudaStream_t)stream;
@@ -479,8 +520,7 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
     sh->graph_dt = dt;
     sh->graph_trace = sh->trace;
   }
-  CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
-  if (sh->Uf && (rc = pw_to_internal(sh, u, sh->Uf, (long long)sh->nv * sh->P, st))) return rc;
+  if ((rc = enqueue_step_prologue(sh, u, st))) return rc;
   for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
   CF_CUDA(cudaMemcpyAsync(sh->flag_host, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(cudaStreamSynchronize(st));
@@ -498,15 +538,7 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
     }
     sh->trace_steps += n_steps;
   }
-  if (*sh->flag_host & 2) {
-    set_error("a bounded tensor-core wait gave up (operator results are invalid)");
-    return CFFYN_ETIMEOUT;
-  }
-  if (*sh->flag_host) {
-    set_error("non-finite value in a stage right-hand side");
-    return CFFYN_ENONFINITE;
-  }
-  return CFFYN_OK;
+  return step_flag_status(*sh->flag_host);
 }
 
 int cffyn_set_trace(cffyn_shell* sh, int on) {
@@ -617,8 +649,7 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     launches_out[k] += (int)(g_launches - l0);
     return CFFYN_OK;
   };
-  CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
-  if (sh->Uf && (rc = pw_to_internal(sh, u, sh->Uf, (long long)sh->nv * sh->P, st))) return rc;
+  if ((rc = enqueue_step_prologue(sh, u, st))) return rc;
   rc = step_sequence(sh, u, dt, st, phase);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);

@@ -171,4 +171,6 @@ WORKLOADS = {
                         n_fields=50, amp=1e-4, ell=4, seed=0, lam=0.25, steps=1000),
     "ks_65x96x192_58f": dict(n_r=65, n_theta=96, n_phi=192, r_in=1.8, r_out=41.0, L=94,
                              n_fields=58, amp=1e-4, ell=4, seed=0, lam=0.25, steps=200),
+    # the uneven-shell batch: shell_batch(n_shells, seed) draws the shells
+    "batch_256": dict(n_shells=256, n_fields=50, seed=0, lam=0.25, steps=100),
 }

@@ -79,3 +79,13 @@ def test_profile_phase_names_match_the_header():
     with open(os.path.join(ROOT, "include", "cffyn.h")) as fh:
         n = int(re.search(r"#define CFFYN_PROFILE_PHASES (\d+)", fh.read())[1])
     assert len(cffyn.PROFILE_PHASES) == n == len(set(cffyn.PROFILE_PHASES))
+
+
+def test_batch_arguments_are_checked_on_host(lib):
+    out = ctypes.c_void_p(1)
+    assert lib.cffyn_create_batch(0, None, ctypes.byref(out)) == cffyn.EINVAL
+    assert out.value is None
+    assert lib.cffyn_create_batch(1, None, None) == cffyn.EINVAL
+    assert lib.cffyn_batch_rk4_step(None, None, None, 1, None) == cffyn.EINVAL
+    assert b"batch" in lib.cffyn_last_error()
+    assert lib.cffyn_destroy_batch(None) == cffyn.OK
