@@ -151,7 +151,7 @@ FAMILIES = {
     "k_decompose": ["decompose"],
     "k_field_exp": ["field_exp"],
 }
-PAIRS = 21  # BF16 digit-pair products per operator product (i + j <= 5 of 6 x 6)
+PAIRS = 26  # BF16 digit-pair products per operator product (i + j <= 6 of 6 x 6)
 
 
 def _op_flops(w, phase):
@@ -180,7 +180,7 @@ def _roofline(w, per_step, launches, hbm, bf16s, peak_kind):
     """Roofline of the dominant kernel family of the traced step (largest device
     time per step).  The operator family is a dense contraction on the tensor
     cores: its algorithmic work is the method's FP64 operator flops times the
-    21 BF16 digit-pair products each one takes; it is timed inside the step, so
+    26 BF16 digit-pair products each one takes; it is timed inside the step, so
     the peak is the sustained BF16 figure.  Pointwise families are compared with
     HBM on their algorithmic bytes."""
     fam_ms = {f: sum(per_step.get(ph, 0.0) for ph in phs) for f, phs in FAMILIES.items()}
@@ -200,7 +200,7 @@ def _roofline(w, per_step, launches, hbm, bf16s, peak_kind):
         return {"bound": "tensor", "kernel": "k_op_tc (all operator launches of the step)",
                 "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
                 "traffic": None, "peak_source": f"bf16_tflops_sustained ({peak_kind})",
-                "work": "21 BF16 digit-pair products x method FP64 operator flops "
+                "work": "26 BF16 digit-pair products x method FP64 operator flops "
                         "(2n_r + 16N + 2(L+1) per pt-field per substep)",
                 "fp64_equiv_tflops": fl / t / 1e12,
                 "hbm_view": {"algorithmic_GBps": byts / t / 1e9, "frac": byts / t / 1e9 / hbm},

@@ -36,13 +36,13 @@ void count_launch();
 // --------------------------------------------------------------------------
 // Split-precision operator for the tcgen05 core: W cut into row groups of
 // `rows` = 48 (P <= 48) or 96 rows and k-steps of 16 columns; per (group,
-// k-step) eleven BF16 digit slices of rows x 16 in the K-major no-swizzle
+// k-step) sixteen BF16 digit slices of rows x 16 in the K-major no-swizzle
 // core-matrix order (core matrix = 8 rows x 8 columns, 128 contiguous bytes;
 // the two core matrices of an 8-row group adjacent, groups 256 bytes apart).
 // Slices 0..4 are digits 0..4 of W; slices 5..10 are digits 0..5 scaled by
-// 2^-8 (they carry the digit-sum-5 products into the digit-sum-4
-// accumulator).
-constexpr int kTcWSlices = 11;
+// 2^-8 and slices 11..15 digits 1..5 scaled by 2^-16 (they carry the
+// digit-sum-5 and digit-sum-6 products into the digit-sum-4 accumulator).
+constexpr int kTcWSlices = 16;
 struct TcOp {
   unsigned short* w = nullptr;  // [batch][group][kstep][slice][rows x 16]
   int* rowexp = nullptr;        // [batch][groups * rows]

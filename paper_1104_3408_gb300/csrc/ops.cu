@@ -410,18 +410,20 @@ __global__ void __launch_bounds__(kExpThreads) k_field_exp(const long long* __re
 //     their values (47-bit fixed point relative to the field's exponent, input
 //     words prefetched one k-step ahead) into the stage, then arrive on its
 //     `xfull` barrier; after the last k-step they run the epilogue;
-//   one MMA warp: bulk-copies (TMA) the operator's eleven slices of each
-//     k-step (see TcOp) a stage ahead and, once a stage is full, issues the 21
+//   one MMA warp: bulk-copies (TMA) the operator's sixteen slices of each
+//     k-step (see TcOp) a stage ahead and, once a stage is full, issues the 26
 //     digit-pair MMAs into five FP32 accumulators in TMEM and commits them to
 //     the stage's `empty` barrier:
 //   acc_d = sum_{i+j=d} W_i X_j                            d = 0..3
-//   acc_4 = sum_{i+j=4} W_i X_j + 2^-8 sum_{i+j=5} W_i X_j
+//   acc_4 = sum_{i+j=4} W_i X_j + 2^-8 sum_{i+j=5} W_i X_j + 2^-16 sum_{i+j=6} W_i X_j
 // acc_0..acc_3 are exact integers (below 4 * 192 * 2^14 < 2^24).  acc_4 is
 // not exact; its rounding is below 2^-24 of a term of weight 256^-4 relative
-// to the leading one, about 2^-56 of the result's scale, under the truncation
-// of the dropped pairs i + j > 5 (about 6 * 2^-48).  The epilogue sums
-// (acc_0 + acc_1 2^-8 + ... + acc_4 2^-32) 2^(E_row + E_col - 14) as a
-// float pair (fold_pair).
+// to the leading one, about 2^-56 of the result's scale, at the level of the
+// dropped pairs i + j > 6 (about 4 * 2^-56).  With the digit-sum-6 pairs the
+// result is as accurate as the 47-bit fixed point of its inputs; without
+// them the dropped digit-sum-6 products (weight 2^-48) were the largest
+// error.  The epilogue sums (acc_0 + acc_1 2^-8 + ... + acc_4 2^-32)
+// 2^(E_row + E_col - 14) as a float pair (fold_pair).
 
 constexpr int kTcCols = 128;
 constexpr int kTcXSlice = kTcCols * 16 * 2;                 // bytes of one data slice per k-step
@@ -444,11 +446,13 @@ struct TcCfg {
   static constexpr int kThreads = kProd + 32;                          // + the MMA warp
   static constexpr int kKQ = 16 * kTcCols / kProd;                     // k per producer per k-step
   static constexpr int kWSlice = ROWS * 16 * 2;                        // bytes of one operator slice
-  static constexpr int kWBytes = kTcWSlices * kWSlice;                 // 16896 | 33792
-  static constexpr int kStage = kTcXBytes + kWBytes;                   // 41472 | 58368
+  static constexpr int kWBytes = kTcWSlices * kWSlice;                 // 24576 | 49152
+  static constexpr int kStage = kTcXBytes + kWBytes;                   // 49152 | 73728
   static constexpr int kStages = ROWS == 48 ? 2 : 3;                   // 2 CTAs / 1 CTA per SM
-  static constexpr int kSmem = kStages * kStage;                       // 82944 | 175104
+  static constexpr int kSmem = kStages * kStage;                       // 98304 | 221184
   static constexpr uint32_t kTmemCols = ROWS == 48 ? 256 : 512;        // 5 accumulators x ROWS
+  static_assert(kSmem <= 227 * 1024, "dynamic shared memory per CTA");
+  static_assert(kStage % 1024 == 0, "stage alignment of the descriptors and bulk copies");
 };
 
 // Raw 64-bit words of N consecutive k of one column (zero outside K or in an
@@ -472,16 +476,17 @@ __device__ __forceinline__ void gather(const OpArgs& a, const ColDesc& d, int k0
 
 // (hi, lo) float pair, packed like the mixed path's internal storage, of
 // (a0 + a1 2^-8 + a2 2^-16 + a3 2^-24 + a4 2^-32) f1 f2 f3 (f1, f2, f3 powers of
-// two).  a0 + a1 2^-8 + a2 2^-16 is summed with error-free transformations;
-// a3 2^-24 + a4 2^-32 in plain FP32: |a3| < 4 K 2^14, so its rounding is
-// below 2^-26 of K 2^14, the scale of a0, i.e. at the level of the dropped
-// digit pairs (5 K 2^14 2^-48 in the same units).
+// two).  a0 + a1 2^-8 + a2 2^-16 + a3 2^-24 (exact values) is summed with
+// error-free transformations, so that the sum's only roundings are those of
+// the low words and of a4 2^-32 (below 2^-48 of |a0|); summing a3 2^-24 in
+// plain FP32 would cost about 2^-24 of it, more than the digit-sum-6 terms.
 __device__ __forceinline__ long long fold_pair(float a0, float a1, float a2, float a3, float a4, float f1,
                                                float f2, float f3) {
-  const float t = __fmaf_rn(a4, 2.3283064365386963e-10f, fm(a3, 5.9604644775390625e-08f));
   ff r = two_sum(a0, fm(a1, 0.00390625f));
   const ff q = two_sum(r.hi, fm(a2, 1.52587890625e-05f));
-  r = fast_two_sum(q.hi, fa(fa(r.lo, q.lo), t));
+  const ff v = two_sum(q.hi, fm(a3, 5.9604644775390625e-08f));
+  const float low = __fmaf_rn(a4, 2.3283064365386963e-10f, fa(fa(r.lo, q.lo), v.lo));
+  r = fast_two_sum(v.hi, low);
   const float hi = fm(fm(fm(r.hi, f1), f2), f3), lo = fm(fm(fm(r.lo, f1), f2), f3);
   return (long long)(((unsigned long long)__float_as_uint(lo) << 32) | __float_as_uint(hi));
 }
@@ -661,6 +666,8 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
           tc::mma(tm + d * ROWS, dx + (d - i) * XS, dw + i * WS, ID, (ks > 0 || i > 0) ? 1u : 0u);
 #pragma unroll
       for (int i = 0; i < 6; ++i) tc::mma(tm + 4 * ROWS, dx + (5 - i) * XS, dw + (5 + i) * WS, ID, 1u);
+#pragma unroll
+      for (int i = 1; i < 6; ++i) tc::mma(tm + 4 * ROWS, dx + (6 - i) * XS, dw + (10 + i) * WS, ID, 1u);
       tc::commit(&empty[s]);
       // refill the stage of k-step ks - 1 with the operator of k-step ks - 1 + S
       if (ks >= 1 && copied < ksteps) {

@@ -364,8 +364,13 @@ __global__ void k_tc_pack(const double* A, int P, int K, int ld, const int* rowe
     Z = (Z - lo) / 256;
   }
   d[0] = (int)Z;
-  float f = (float)(q < 5 ? d[q] : d[q - 5]);  // exact, |d| <= 128
-  if (q >= 5) f *= 0.00390625f;                 // 2^-8, exact
+  // slice q: digit q (q < 5), digit q - 5 times 2^-8 (q < 11), digit q - 10
+  // times 2^-16; all exact in BF16 (|d| <= 128)
+  float f = (float)(q < 5 ? d[q] : (q < 11 ? d[q - 5] : d[q - 10]));
+  if (q >= 11)
+    f *= 1.52587890625e-05f;  // 2^-16
+  else if (q >= 5)
+    f *= 0.00390625f;         // 2^-8
   w[t] = (unsigned short)(__float_as_uint(f) >> 16);
 }
 

@@ -1,0 +1,150 @@
+"""Parity at the full sizes of the benchmarked shells, through the C-ABI, in
+the launch configuration the bench times:
+
+* 33 x 48 x 96, 50 fields, L = 46 (the full-RK4 single-shell workload) and
+  65 x 96 x 192, 58 fields, L = 94, r in [1.8, 41] (the large extended-gauge
+  shell): Cartesian derivatives against the oracle everywhere; the
+  right-hand side (pointwise given the derivatives) and the Yn filter (which
+  acts on each sphere by itself) against the oracle on sampled radii,
+  including the outermost one with its boundary condition; several RK4 steps
+  of the mixed path against the FP64 GPU path (the oracle needs minutes per
+  stage at these sizes).
+* 9 x 12 x 24, L = 10: 100 RK4 steps of the mixed path against the oracle
+  (the accuracy target for fields after 100 steps).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ghg
+from paper_1104_3408_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-10}   # FP64, MIXED
+C3 = dict(n_r=33, n_theta=48, n_phi=96, r_in=1.8, r_out=11.0, L=46, nf=50, amp=1e-4, ell=4)
+C5 = dict(n_r=65, n_theta=96, n_phi=192, r_in=1.8, r_out=41.0, L=94, nf=58, amp=1e-4, ell=4)
+
+
+@pytest.fixture(scope="module")
+def cf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3408_gb300 import cffyn
+    return cffyn
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def rel_rows(got, ref):
+    d = np.abs(got - ref).reshape(ref.shape[0], -1).max(axis=1)
+    r = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1)
+    return (d / np.maximum(r, 1e-300)).max()
+
+
+def state(c, seed=0):
+    u = inputs.kerr_schild_state(c["n_r"], c["n_theta"], c["n_phi"], c["r_in"], c["r_out"],
+                                 n_fields=c["nf"], amp=c["amp"], ell=c["ell"], seed=seed)
+    if c["nf"] > 50:
+        u[50:54] = ghg.gauge_source_from_state(u[:50].reshape(50, -1)).reshape((4,) + u.shape[1:])
+    return u
+
+
+@pytest.mark.parametrize("c", [C3, C5], ids=["33x48x96", "65x96x192_58f"])
+def test_full_size_operators_and_rhs(cf, c):
+    n_r, N, J, L, nf = c["n_r"], c["n_theta"], c["n_phi"], c["L"], c["nf"]
+    u0 = state(c)
+    rs = oracle.OracleShell(n_r, N, J, c["r_in"], c["r_out"], L, n_fields=nf)
+    if nf == 50:
+        rs.init_gauge_from_state(u0)
+    du = rs.derivs(u0)                                   # [3, nf, J, N, n_r]
+    ks = [0, n_r // 2, n_r - 1]                          # sampled radii, the outer one last
+    u_s = np.ascontiguousarray(u0[..., ks])
+    du_s = np.ascontiguousarray(du[..., ks])
+    H, dH = (rs.H[..., ks], rs.dH[..., ks]) if nf == 50 else (u_s[50:54], du_s[:, 50:54])
+    rhs_ref = ghg.rhs_pointwise(u_s.reshape(nf, -1), du_s.reshape(3, nf, -1), H.reshape(4, -1),
+                                dH.reshape(3, 4, -1), nf).reshape(u_s.shape)
+    rhs_ref = ghg.apply_outer_bc(rhs_ref, u_s, rs.theta, rs.phi)
+    fs = oracle.OracleShell(3, N, J, c["r_in"], c["r_out"], L, n_fields=nf)
+    filt_ref = fs.filter(u_s)
+    scale = np.abs(du).max()
+    errs = {}
+    for prec in (1, 0):
+        sh = cf.Shell(n_r, N, J, c["r_in"], c["r_out"], L, n_fields=nf, precision=prec)
+        u = dev(u0)
+        if nf == 50:
+            sh.init_gauge_from_state(u)
+        out = torch.empty((3,) + u0.shape, dtype=torch.float64, device="cuda")
+        sh.derivs(u, out)
+        got = out.cpu().numpy()
+        del out
+        d = np.abs(got - du).reshape(3 * nf, -1).max(axis=1)
+        rmax = np.abs(du).reshape(3 * nf, -1).max(axis=1)
+        worst = int(np.argmax(d / np.maximum(rmax, 1e-300)))
+        loc = np.unravel_index(int(np.argmax(np.abs(got - du).reshape(3 * nf, -1)[worst])), u0.shape[1:])
+        errs[("derivs_row", prec)] = float((d / np.maximum(rmax, 1e-300)).max())
+        errs[("derivs_global", prec)] = float(d.max() / scale)
+        errs[("derivs_worst", prec)] = (worst // nf, worst % nf, tuple(int(x) for x in loc))
+        r = torch.empty_like(u)
+        sh.rhs(u, r)
+        got = r.cpu().numpy()[..., ks]
+        errs[("rhs", prec)] = float(np.abs(got - rhs_ref).max() / scale)
+        sh.filter(u, r)
+        got = r.cpu().numpy()[..., ks]
+        errs[("filter", prec)] = float(rel_rows(got, filt_ref))
+        sh.destroy()
+    print(c["n_r"], c["n_theta"], errs)
+    for (what, prec), e in errs.items():
+        if what != "derivs_worst":
+            assert e < TOL[prec], (what, prec, e)
+
+
+@pytest.mark.parametrize("c,steps", [(C3, 100), (C5, 5)], ids=["33x48x96", "65x96x192_58f"])
+def test_full_size_steps_mixed_vs_fp64_gpu(cf, c, steps):
+    n_r, N, J, L, nf = c["n_r"], c["n_theta"], c["n_phi"], c["L"], c["nf"]
+    u0 = state(c)
+    res = []
+    for prec in (1, 0):
+        sh = cf.Shell(n_r, N, J, c["r_in"], c["r_out"], L, n_fields=nf, precision=prec)
+        u = dev(u0)
+        sh.init_gauge_from_state(u)
+        v = torch.empty_like(u)
+        sh.filter(u, v)
+        sh.rk4_step(v, 0.0, steps)
+        res.append((v.cpu().numpy(), sh.constraint_norms(v)))
+        sh.destroy()
+    (a, ca), (b, cb) = res
+    assert np.isfinite(a).all()
+    assert np.abs(a - b).max() / np.abs(b).max() < 1e-8
+    # the motion of the fields is resolved (they moved by 1e-8..1e-5)
+    assert np.abs(a[:50] - b[:50]).max() / np.abs(b[:50] - u0[:50]).max() < 1e-3
+    # constraint norms: RMS of O(1) quantities computed from fields that agree
+    # to ~1e-13, so they agree to a small absolute amount
+    assert abs(ca[0] - cb[0]) <= 1e-6 * cb[0] + 1e-12 and abs(ca[1] - cb[1]) <= 1e-6 * cb[1] + 1e-12
+
+
+def test_hundred_steps_mixed_vs_oracle(cf):
+    n_r, N, J, L = 9, 12, 24, 10
+    u0 = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-6, ell=2, seed=0)
+    rs = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L)
+    rs.init_gauge_from_state(u0)
+    dt = 0.25 * rs.dx_min()
+    uf = rs.filter(u0)
+    ref = rs.rk4_step(uf, dt, 100)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=cf.MIXED)
+    u = dev(u0)
+    sh.init_gauge_from_state(u)
+    v = torch.empty_like(u)
+    sh.filter(u, v)
+    sh.rk4_step(v, dt, 100)
+    got = v.cpu().numpy()
+    sh.destroy()
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-8
+    # relative to how far the fields moved
+    assert np.abs(got - ref).max() / np.abs(ref - uf).max() < 1e-4
