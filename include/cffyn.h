@@ -72,6 +72,17 @@ extern "C" {
 #define CFFYN_FILTER_SUBSTEP 0 /* every stage right-hand side after the BC */
 #define CFFYN_FILTER_STEP 1    /* the state after each full RK4 step (paper) */
 
+/* Which filter (Sec. 3.5).  Only the tensor filter Yn is built; the
+ * component-wise Y and Yg filters return CFFYN_ENOTIMPL. */
+#define CFFYN_FILTER_YN 0
+#define CFFYN_FILTER_Y 1
+#define CFFYN_FILTER_YG 2
+
+/* cffyn_shell_desc.flags */
+#define CFFYN_DEFER_WORKSPACE 1 /* allocate no workspace at creation: attach one
+                                   with cffyn_attach_workspace before the first
+                                   call that computes (CFFYN_EINVAL before) */
+
 typedef struct cffyn_shell cffyn_shell;
 
 typedef struct cffyn_shell_desc {
@@ -86,6 +97,8 @@ typedef struct cffyn_shell_desc {
   int precision;    /* CFFYN_FP64 or CFFYN_MIXED */
   int filter_mode;  /* CFFYN_FILTER_SUBSTEP or CFFYN_FILTER_STEP */
   double courant;   /* lambda of dt = lambda * min dx (Sec. 4.1); <= 0 -> 0.25 */
+  int filter_kind;  /* CFFYN_FILTER_YN (0) */
+  int flags;        /* 0 or CFFYN_DEFER_WORKSPACE */
 } cffyn_shell_desc;
 
 /* Builds a shell: collocation grid (Sec. 2.1), differentiation matrices
@@ -95,8 +108,10 @@ typedef struct cffyn_shell_desc {
  * FP64 on the current CUDA device, plus the library's workspace.
  * Defaults of cffyn_create_shell: 50 fields, CFFYN_MIXED, CFFYN_FILTER_SUBSTEP,
  * courant 0.25.  Synchronous.  Returns CFFYN_EINVAL for sizes outside the
- * ranges above (or n_theta > 96, n_r > 96), CFFYN_ENOMEM / CFFYN_ECUDA on
- * device failures; *out is NULL on error. */
+ * ranges above (or n_theta > 96, n_r > 96) and for unknown flags,
+ * CFFYN_ENOTIMPL for a filter kind other than CFFYN_FILTER_YN, CFFYN_ENOMEM /
+ * CFFYN_ECUDA on device failures; *out is NULL on error.  cffyn_create_shell
+ * takes filter_kind 0 and flags 0. */
 CFFYN_API int cffyn_create_shell(int n_r, int n_theta, int n_phi, double r_in, double r_out, int L,
                        cffyn_shell** out);
 CFFYN_API int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out);
@@ -105,7 +120,27 @@ CFFYN_API int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** 
  * NULL is allowed. */
 CFFYN_API int cffyn_destroy(cffyn_shell* sh);
 
-/* Bytes of device memory the handle owns (matrices + workspace). */
+/* Workspace: the scratch arrays of one call (stage state, RK4 accumulator,
+ * spherical derivatives / DFT coefficients, right-hand side and its source
+ * terms, and on the mixed path the pair copy of the step's initial state);
+ * nothing in it survives from one call to the next.  cffyn_workspace_size is
+ * its size in bytes (8 or 7 arrays of n_fields x points doubles, each rounded
+ * up to 256 bytes).  By default the library allocates it at creation. */
+CFFYN_API size_t cffyn_workspace_size(const cffyn_shell* sh);
+
+/* Makes `ptr` (device memory of the shell's device, 256-byte aligned, at
+ * least cffyn_workspace_size bytes, caller-owned: the caller keeps it alive
+ * and unused by other work until the shell is destroyed or another workspace
+ * is attached) the shell's workspace, and frees the workspace the library
+ * allocated, if any.  ptr == NULL gives the shell a library-allocated
+ * workspace again.  Synchronises the device first (no call of this shell may
+ * be in flight); drops the captured step graph (the next cffyn_rk4_step
+ * recaptures; so does a batch holding the shell).  Not during a stream
+ * capture.  CFFYN_EINVAL for a misaligned or short buffer. */
+CFFYN_API int cffyn_attach_workspace(cffyn_shell* sh, void* ptr, size_t bytes);
+
+/* Bytes of device memory the handle owns (matrices, gauge, and the workspace
+ * while it is library-allocated). */
 CFFYN_API size_t cffyn_device_bytes(const cffyn_shell* sh);
 
 /* dt = courant * min(r_1 - r_0, 2 r_0 sin(theta_0) sin(dphi/2)) (Sec. 4.1). */

@@ -16,6 +16,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcffyn.so")
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTIMPL = 0, -1, -2, -3, -4, -5, -6
 FP64, MIXED = 0, 1
 FILTER_SUBSTEP, FILTER_STEP = 0, 1
+FILTER_YN, FILTER_Y, FILTER_YG = 0, 1, 2
+DEFER_WORKSPACE = 1
 STATIC_SCRATCH_BYTES = 8 * 1024 * 1024   # CFFYN_STATIC_SCRATCH_BYTES
 
 EXPORTED = [
@@ -25,6 +27,7 @@ EXPORTED = [
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
     "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch",
+    "cffyn_workspace_size", "cffyn_attach_workspace",
 ]
 PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
                   "dft_fwd", "project", "dft_inv", "reconstruct", "field_exp"]
@@ -35,7 +38,7 @@ class ShellDesc(ctypes.Structure):
         ("n_r", ctypes.c_int), ("n_theta", ctypes.c_int), ("n_phi", ctypes.c_int),
         ("r_in", ctypes.c_double), ("r_out", ctypes.c_double), ("L", ctypes.c_int),
         ("n_fields", ctypes.c_int), ("precision", ctypes.c_int), ("filter_mode", ctypes.c_int),
-        ("courant", ctypes.c_double),
+        ("courant", ctypes.c_double), ("filter_kind", ctypes.c_int), ("flags", ctypes.c_int),
     ]
 
 
@@ -63,6 +66,8 @@ def load(path=LIB_PATH):
         "cffyn_create_shell_ex": ([ctypes.POINTER(ShellDesc), ctypes.POINTER(vp)], i),
         "cffyn_destroy": ([vp], i),
         "cffyn_device_bytes": ([vp], ctypes.c_size_t),
+        "cffyn_workspace_size": ([vp], ctypes.c_size_t),
+        "cffyn_attach_workspace": ([vp, vp, ctypes.c_size_t], i),
         "cffyn_default_dt": ([vp], d),
         "cffyn_set_gauge": ([vp, dp, vp], i),
         "cffyn_init_gauge_from_state": ([vp, dp, vp], i),
@@ -118,10 +123,11 @@ class Shell:
     """One spherical shell (a cffyn_shell handle)."""
 
     def __init__(self, n_r, n_theta, n_phi, r_in, r_out, L, n_fields=50, precision=MIXED,
-                 filter_mode=FILTER_SUBSTEP, courant=0.25):
+                 filter_mode=FILTER_SUBSTEP, courant=0.25, filter_kind=FILTER_YN, flags=0):
         lib = load()
         desc = ShellDesc(n_r, n_theta, n_phi, r_in, r_out, L, n_fields, precision, filter_mode,
-                         courant)
+                         courant, filter_kind, flags)
+        self._workspace = None
         h = ctypes.c_void_p()
         _check(lib.cffyn_create_shell_ex(ctypes.byref(desc), ctypes.byref(h)))
         self.h = h
@@ -146,6 +152,23 @@ class Shell:
 
     def device_bytes(self):
         return load().cffyn_device_bytes(self.h)
+
+    def workspace_size(self):
+        return load().cffyn_workspace_size(self.h)
+
+    def attach_workspace(self, buf):
+        """Use `buf` (a contiguous CUDA tensor of at least workspace_size()
+        bytes, 256-byte aligned) as the shell's workspace; None returns to a
+        library-allocated one.  The Shell keeps a reference to buf."""
+        if buf is None:
+            _check(load().cffyn_attach_workspace(self.h, None, 0))
+        else:
+            import torch
+            if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
+                raise TypeError("workspace must be a contiguous CUDA tensor")
+            _check(load().cffyn_attach_workspace(self.h, ctypes.c_void_p(buf.data_ptr()),
+                                                 buf.numel() * buf.element_size()))
+        self._workspace = buf
 
     def default_dt(self):
         return load().cffyn_default_dt(self.h)

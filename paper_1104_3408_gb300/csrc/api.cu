@@ -77,6 +77,38 @@ int check_ptr(const void* p, const char* what) {
   return CFFYN_OK;
 }
 
+// Workspace layout: U, kacc, D (three arrays), S, Rsrc and on the mixed path
+// Uf, each nv x P doubles rounded up to 256 bytes, in this order.
+size_t ws_array_bytes(const cffyn_shell* sh) {
+  return ((size_t)sh->nv * sh->P * sizeof(double) + 255) / 256 * 256;
+}
+size_t ws_total_bytes(const cffyn_shell* sh) {
+  return ws_array_bytes(sh) * (sh->d.precision == CFFYN_MIXED ? 8 : 7);
+}
+void carve_workspace(cffyn_shell* sh, void* base) {
+  const size_t one = ws_array_bytes(sh);
+  char* p = static_cast<char*>(base);
+  auto take = [&](int n) {
+    double* q = base ? reinterpret_cast<double*>(p) : nullptr;
+    p += n * one;
+    return q;
+  };
+  sh->U = take(1);
+  sh->kacc = take(1);
+  sh->D = take(3);
+  sh->S = take(1);
+  sh->Rsrc = take(1);
+  sh->Uf = sh->d.precision == CFFYN_MIXED ? take(1) : nullptr;
+  sh->ws = base;
+}
+int check_ws(const cffyn_shell* sh) {
+  if (!sh->ws) {
+    set_error("no workspace attached (cffyn_attach_workspace)");
+    return CFFYN_EINVAL;
+  }
+  return CFFYN_OK;
+}
+
 // spherical derivatives of nf fields into D (internal storage); in_pairs: u is
 // a pair-stored internal buffer of the mixed path (else FP64)
 int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, bool in_pairs, cudaStream_t st) {
@@ -110,12 +142,12 @@ int filter_spin_slots(cffyn_shell* sh, double* spin, cudaStream_t st) {
 void free_shell(cffyn_shell* sh) {
   if (!sh) return;
   cudaDeviceSynchronize();
-  double** ptrs[] = {&sh->r,     &sh->sth,    &sh->cth,    &sh->sph, &sh->cph,  &sh->Dr,   &sh->Dth2,
-                     &sh->Dph,   &sh->Fan,    &sh->Fsy,    &sh->Fraw, &sh->Fproj0, &sh->FprojC,
-                     &sh->H,     &sh->dH,     &sh->U,      &sh->kacc, &sh->D,    &sh->S,
-                     &sh->Rsrc,  &sh->red,    &sh->triad, &sh->Uf};
+  double** ptrs[] = {&sh->r,   &sh->sth, &sh->cth,  &sh->sph,  &sh->cph,    &sh->Dr,     &sh->Dth2,
+                     &sh->Dph, &sh->Fan, &sh->Fsy,  &sh->Fraw, &sh->Fproj0, &sh->FprojC, &sh->H,
+                     &sh->dH,  &sh->red, &sh->triad};
   for (double** p : ptrs)
     if (*p) cudaFree(*p);
+  if (sh->ws_owned && sh->ws) cudaFree(sh->ws);
   TcOp* to[] = {&sh->tDr, &sh->tDth2, &sh->tDph, &sh->tFan, &sh->tFsy, &sh->tF0,
                 &sh->tFC[0], &sh->tFC[1], &sh->tFC[2]};
   for (TcOp* t : to) free_tc(*t);
@@ -167,6 +199,18 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     set_error("filter_mode must be CFFYN_FILTER_SUBSTEP or CFFYN_FILTER_STEP");
     return CFFYN_EINVAL;
   }
+  if (d.flags & ~CFFYN_DEFER_WORKSPACE) {
+    set_error("unknown flags 0x%x", d.flags);
+    return CFFYN_EINVAL;
+  }
+  if (d.filter_kind == CFFYN_FILTER_Y || d.filter_kind == CFFYN_FILTER_YG) {
+    set_error("filter kind %d: only the tensor filter Yn (CFFYN_FILTER_YN) is built", d.filter_kind);
+    return CFFYN_ENOTIMPL;
+  }
+  if (d.filter_kind != CFFYN_FILTER_YN) {
+    set_error("unknown filter kind %d", d.filter_kind);
+    return CFFYN_EINVAL;
+  }
   cffyn_shell* sh = new (std::nothrow) cffyn_shell();
   if (!sh) {
     set_error("host allocation failed");
@@ -212,14 +256,24 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     sh->bytes += n * sizeof(double);
     return CFFYN_OK;
   };
-  if ((rc = alloc(&sh->U, nvP)) || (rc = alloc(&sh->kacc, nvP)) || (rc = alloc(&sh->D, 3 * nvP)) ||
-      (rc = alloc(&sh->S, nvP)) || (rc = alloc(&sh->Rsrc, nvP)) || (rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, (sh->nv == 58 ? 16 : 12) * sh->P)) ||
+  if ((rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, (sh->nv == 58 ? 16 : 12) * sh->P)) ||
       (rc = alloc(&sh->red, 2)) || (rc = alloc(&sh->triad, (size_t)9 * sh->N * sh->J)))
     return fail(rc);
+  (void)nvP;
   if ((rc = pw_triad_table(sh))) return fail(rc);
-  if (d.precision == CFFYN_MIXED) {
-    if (cudaMalloc(&sh->exps, 64 * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
-    if ((rc = alloc(&sh->Uf, nvP))) return fail(rc);
+  if (d.precision == CFFYN_MIXED && cudaMalloc(&sh->exps, 64 * sizeof(int)) != cudaSuccess)
+    return fail(CFFYN_ENOMEM);
+  sh->ws_bytes = ws_total_bytes(sh);
+  if (!(d.flags & CFFYN_DEFER_WORKSPACE)) {
+    void* w = nullptr;
+    if (cudaMalloc(&w, sh->ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of %zu bytes (workspace) failed", sh->ws_bytes);
+      return fail(CFFYN_ENOMEM);
+    }
+    sh->ws_owned = true;
+    sh->bytes += sh->ws_bytes;
+    carve_workspace(sh, w);
   }
   {
     // R0: the 16 real slots of the 50 GHG fields, then H_t and H_r of every
@@ -266,6 +320,8 @@ int cffyn_create_shell(int n_r, int n_theta, int n_phi, double r_in, double r_ou
   d.precision = CFFYN_MIXED;
   d.filter_mode = CFFYN_FILTER_SUBSTEP;
   d.courant = 0.25;
+  d.filter_kind = CFFYN_FILTER_YN;
+  d.flags = 0;
   return cffyn_create_shell_ex(&d, out);
 }
 
@@ -276,11 +332,49 @@ int cffyn_destroy(cffyn_shell* sh) {
 
 size_t cffyn_device_bytes(const cffyn_shell* sh) { return sh ? sh->bytes : 0; }
 
+size_t cffyn_workspace_size(const cffyn_shell* sh) { return sh ? sh->ws_bytes : 0; }
+
+int cffyn_attach_workspace(cffyn_shell* sh, void* ptr, size_t bytes) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  if (ptr && (((uintptr_t)ptr) & 255)) {
+    set_error("workspace is not 256-byte aligned");
+    return CFFYN_EINVAL;
+  }
+  if (ptr && bytes < sh->ws_bytes) {
+    set_error("workspace of %zu bytes, %zu needed", bytes, sh->ws_bytes);
+    return CFFYN_EINVAL;
+  }
+  if (!ptr && sh->ws_owned) return CFFYN_OK;
+  CF_CUDA(cudaDeviceSynchronize());
+  void* fresh = nullptr;
+  if (!ptr) {
+    if (cudaMalloc(&fresh, sh->ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation of %zu bytes (workspace) failed", sh->ws_bytes);
+      return CFFYN_ENOMEM;
+    }
+  }
+  if (sh->ws_owned) {
+    cudaFree(sh->ws);
+    sh->bytes -= sh->ws_bytes;
+  }
+  sh->ws_owned = !ptr;
+  if (!ptr) sh->bytes += sh->ws_bytes;
+  carve_workspace(sh, ptr ? ptr : fresh);
+  if (sh->graph) {
+    cudaGraphExecDestroy(sh->graph);
+    sh->graph = nullptr;
+  }
+  ++sh->ws_gen;
+  return CFFYN_OK;
+}
+
 double cffyn_default_dt(const cffyn_shell* sh) { return sh ? sh->dt_default : 0.0; }
 
 static int gauge_derivs(cffyn_shell* sh, cudaStream_t st) {
   // d_i H_a with the shell's operators: spherical derivatives into D, chain rule into dH
   int rc;
+  if ((rc = check_ws(sh))) return rc;
   const bool pairs = sh->d.precision == CFFYN_MIXED;
   if ((rc = derivs_spherical(sh, sh->H, sh->D, 4, pairs, st))) return rc;
   if ((rc = pw_cart(sh, sh->D, sh->dH, 4, true, st))) return rc;
@@ -315,6 +409,7 @@ int cffyn_derivs(cffyn_shell* sh, const double* u, double* dxyz, void* stream) {
   if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
   int rc;
   if ((rc = check_ptr(u, "u")) || (rc = check_ptr(dxyz, "dxyz"))) return rc;
+  if ((rc = check_ws(sh))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, false, st))) return rc;
   return pw_cart(sh, sh->D, dxyz, sh->nv, false, st);
@@ -324,6 +419,7 @@ int cffyn_rhs(cffyn_shell* sh, const double* u, double* dudt, void* stream) {
   if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
   int rc;
   if ((rc = check_ptr(u, "u")) || (rc = check_ptr(dudt, "dudt"))) return rc;
+  if ((rc = check_ws(sh))) return rc;
   if (sh->nv == 50 && !sh->gauge_set) {
     set_error("gauge source not set (cffyn_set_gauge / cffyn_init_gauge_from_state)");
     return CFFYN_EINVAL;
@@ -337,6 +433,7 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
   if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
   int rc;
   if ((rc = check_ptr(u, "u")) || (rc = check_ptr(out, "out"))) return rc;
+  if ((rc = check_ws(sh))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if ((rc = pw_decompose(sh, u, sh->S, false, st))) return rc;
   if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
@@ -474,6 +571,8 @@ int step_flag_status(int flag) {
 }
 
 int check_step_ready(const cffyn_shell* sh) {
+  int rc;
+  if ((rc = check_ws(sh))) return rc;
   if (sh->nv == 50 && !sh->gauge_set) {
     set_error("gauge source not set (cffyn_set_gauge / cffyn_init_gauge_from_state)");
     return CFFYN_EINVAL;
@@ -567,6 +666,7 @@ int cffyn_constraint_norms(cffyn_shell* sh, const double* u, double out[2], void
   int rc;
   if ((rc = check_ptr(u, "u"))) return rc;
   if (!out) { set_error("out is NULL"); return CFFYN_EINVAL; }
+  if ((rc = check_ws(sh))) return rc;
   if (sh->nv == 50 && !sh->gauge_set) {
     set_error("gauge source not set");
     return CFFYN_EINVAL;
@@ -623,6 +723,7 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
   int rc;
   if ((rc = check_ptr(u, "u"))) return rc;
   if (!ms_out || !launches_out) { set_error("outputs are NULL"); return CFFYN_EINVAL; }
+  if ((rc = check_ws(sh))) return rc;
   if (sh->nv == 50 && !sh->gauge_set) { set_error("gauge source not set"); return CFFYN_EINVAL; }
   if (!(dt > 0)) dt = sh->dt_default;
   cudaStream_t st = (cudaStream_t)stream;

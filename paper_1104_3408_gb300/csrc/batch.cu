@@ -31,8 +31,9 @@ struct cffyn_batch {
   cudaEvent_t fork = nullptr;
   cudaStream_t origin = nullptr;
   cudaGraphExec_t pre = nullptr, step = nullptr, post = nullptr;
-  std::vector<double*> gu;  // state pointers and step sizes the graphs were captured with
-  std::vector<double> gdt;
+  std::vector<double*> gu;  // state pointers, step sizes and workspace generations
+  std::vector<double> gdt;  // the graphs were captured with
+  std::vector<unsigned> ggen;
   int* flags_host = nullptr;  // pinned, one word per shell
 };
 
@@ -177,14 +178,18 @@ int cffyn_batch_rk4_step(cffyn_batch* b, double* const* u, const double* dt, int
   for (int i = 0; i < b->n; ++i) {
     if ((rc = check_state_ptr(u[i], "u[i]"))) return rc;
     if ((rc = check_step_ready(b->sh[i]))) {
-      set_error("shell %d: gauge source not set", i);
+      char msg[512];
+      snprintf(msg, sizeof(msg), "%s", cffyn_last_error());
+      set_error("shell %d: %s", i, msg);
       return rc;
     }
     dts[i] = (dt && dt[i] > 0) ? dt[i] : b->sh[i]->dt_default;
   }
   if (n_steps == 0) return CFFYN_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const bool same = b->step && std::equal(b->gu.begin(), b->gu.end(), u) && b->gdt == dts;
+  std::vector<unsigned> gens(b->n);
+  for (int i = 0; i < b->n; ++i) gens[i] = b->sh[i]->ws_gen;
+  const bool same = b->step && std::equal(b->gu.begin(), b->gu.end(), u) && b->gdt == dts && b->ggen == gens;
   if (!same) {
     free_graphs(b);
     if ((rc = capture_branches(b, &b->pre, [&](int i, cudaStream_t s) {
@@ -206,6 +211,7 @@ int cffyn_batch_rk4_step(cffyn_batch* b, double* const* u, const double* dt, int
     }
     b->gu.assign(u, u + b->n);
     b->gdt = dts;
+    b->ggen = gens;
   }
   CF_CUDA(cudaGraphLaunch(b->pre, st));
   for (int k = 0; k < n_steps; ++k) CF_CUDA(cudaGraphLaunch(b->step, st));

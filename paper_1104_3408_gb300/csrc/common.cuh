@@ -94,7 +94,13 @@ struct cffyn_shell {
   double* dH = nullptr;   // [3][4][P] d_i H_a, + [4][P] d_t H_a for 58 fields
   bool gauge_set = false;
 
-  // workspace
+  // workspace: one block (ws, ws_bytes) carved into the arrays below; owned
+  // by the library (ws_owned) or attached by the caller; ws_gen counts
+  // attachments so that captured graphs can tell they are stale
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  unsigned ws_gen = 0;
   double* U = nullptr;     // stage state [nv][P]
   double* Uf = nullptr;    // mixed path: the step's initial state in internal storage [nv][P]
   double* kacc = nullptr;  // RK4 accumulator [nv][P]

@@ -89,3 +89,20 @@ def test_batch_arguments_are_checked_on_host(lib):
     assert lib.cffyn_batch_rk4_step(None, None, None, 1, None) == cffyn.EINVAL
     assert b"batch" in lib.cffyn_last_error()
     assert lib.cffyn_destroy_batch(None) == cffyn.OK
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("flags", 2, cffyn.EINVAL), ("filter_kind", cffyn.FILTER_Y, cffyn.ENOTIMPL),
+    ("filter_kind", cffyn.FILTER_YG, cffyn.ENOTIMPL), ("filter_kind", 7, cffyn.EINVAL),
+])
+def test_create_checks_filter_kind_and_flags_on_host(lib, field, value, code):
+    desc = cffyn.ShellDesc(9, 12, 24, 1.8, 11.0, 10, 50, cffyn.MIXED, cffyn.FILTER_SUBSTEP, 0.25)
+    setattr(desc, field, value)
+    h = ctypes.c_void_p(1)
+    assert lib.cffyn_create_shell_ex(ctypes.byref(desc), ctypes.byref(h)) == code
+    assert h.value is None
+
+
+def test_workspace_calls_reject_null_shell(lib):
+    assert lib.cffyn_workspace_size(None) == 0
+    assert lib.cffyn_attach_workspace(None, None, 0) == cffyn.EINVAL
