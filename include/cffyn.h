@@ -235,13 +235,14 @@ CFFYN_API int cffyn_get_operator(const cffyn_shell* sh, int which, double* host_
  * around every kernel group on `stream`, synchronising after each group, and
  * returns per group the device time in milliseconds summed over the step
  * (ms_out) and the number of kernel launches (launches_out).  Groups, in
- * order: d_r, d_theta, d_phi, right-hand-side sources with Christoffel symbols,
+ * order: d_r, d_theta and d_phi (one launch per stage on the CFFYN_MIXED
+ * path), right-hand-side sources with Christoffel symbols,
  * quadratic sources, principal parts + BC, spin decomposition, phi analysis,
  * projection, phi synthesis, reconstruction + RK4 update, and the per-field
  * exponent scans of the CFFYN_MIXED path in front of each operator group
  * (no launches on the FP64 path).  u is advanced by one step.  Both output
  * arrays hold CFFYN_PROFILE_PHASES entries (host memory). */
-#define CFFYN_PROFILE_PHASES 12
+#define CFFYN_PROFILE_PHASES 11
 CFFYN_API int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out,
                                  int* launches_out, void* stream);
 

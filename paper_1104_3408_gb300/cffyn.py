@@ -29,7 +29,7 @@ EXPORTED = [
     "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch",
     "cffyn_workspace_size", "cffyn_attach_workspace",
 ]
-PROFILE_PHASES = ["d_r", "d_theta", "d_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
+PROFILE_PHASES = ["d_r", "d_theta_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
                   "dft_fwd", "project", "dft_inv", "reconstruct", "field_exp"]
 
 

@@ -29,6 +29,7 @@ int set_op_smem_limits();
 int op_deriv_r(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int op_deriv_theta(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int op_deriv_phi(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
+int op_deriv_theta_phi(const cffyn_shell*, const double*, double*, double*, int, bool, cudaStream_t);
 int op_dft_fwd(const cffyn_shell*, const double*, double*, int, cudaStream_t);
 int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t);
 int op_project(const cffyn_shell*, const double*, double*, const int*, int, const int* const[3],
@@ -442,7 +443,7 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
 
 // The kernel groups of one RK4 step (Sec. 2.5) in order.  run(phase, fn)
 // enqueues fn() as part of `phase` (the groups of cffyn_profile_step; phase
-// 11 is the per-field exponent scan of the mixed path in front of each
+// 10 is the per-field exponent scan of the mixed path in front of each
 // operator group); tracing and profiling hooks live in run.
 extern "C++" {
 template <class Run>
@@ -454,18 +455,18 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
   const long long lc = (long long)sh->R * sh->N * sh->n_r;  // coefficient values per function
   int rc;
   auto prep = [&](const double* in, bool pairs, long long len, int pairing) {
-    return run(11, [&] { return op_prepare(sh, in, pairs, sh->nv, len, pairing, st); });
+    return run(10, [&] { return op_prepare(sh, in, pairs, sh->nv, len, pairing, st); });
   };
   // Yn filter of the spin slots in `spin` (in place through D and D + nvP)
   auto filter = [&](double* spin) -> int {
     int r;
     if ((r = prep(spin, true, P, 1))) return r;
-    if ((r = run(7, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return r;
+    if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return r;
     if ((r = prep(sh->D, true, lc, 1))) return r;
-    if ((r = run(8, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st); })))
+    if ((r = run(7, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st); })))
       return r;
     if ((r = prep(sh->D + nvP, true, lc, 1))) return r;
-    return run(9, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); });
+    return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); });
   };
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   for (int s = 0; s < 4; ++s) {
@@ -477,29 +478,29 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
     const bool xp = mixed;
     if ((rc = prep(X, xp, P, 0))) return rc;
     if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
-    if ((rc = run(1, [&] { return op_deriv_theta(sh, X, sh->D + nvP, sh->nv, xp, st); }))) return rc;
-    if ((rc = run(2, [&] { return op_deriv_phi(sh, X, sh->D + 2 * nvP, sh->nv, xp, st); }))) return rc;
-    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
-    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
-    if ((rc = run(5, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
+    if ((rc = run(1, [&] { return op_deriv_theta_phi(sh, X, sh->D + nvP, sh->D + 2 * nvP, sh->nv, xp, st); })))
+      return rc;
+    if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
+    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
+    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
     if (per_sub) {
-      if ((rc = run(6, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
+      if ((rc = run(5, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
       if ((rc = filter(spin))) return rc;
-      if ((rc = run(10, [&] {
+      if ((rc = run(9, [&] {
              return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
            })))
         return rc;
     } else {
-      if ((rc = run(10, [&] {
+      if ((rc = run(9, [&] {
              return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
            })))
         return rc;
     }
   }
   if (!per_sub) {
-    if ((rc = run(6, [&] { return pw_decompose(sh, mixed ? sh->Uf : u, sh->S, mixed, st); }))) return rc;
+    if ((rc = run(5, [&] { return pw_decompose(sh, mixed ? sh->Uf : u, sh->S, mixed, st); }))) return rc;
     if ((rc = filter(sh->S))) return rc;
-    if ((rc = run(10, [&] {
+    if ((rc = run(9, [&] {
            return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, sh->Uf, 0.0, sh->flag, st);
          })))
       return rc;

@@ -123,7 +123,7 @@ struct cffyn_shell {
 
   // tracing: event nodes at every phase boundary of the captured step
   int trace = 0;
-  static constexpr int kPhases = 12;
+  static constexpr int kPhases = 11;
   static constexpr int kMaxMarks = 64;
   cudaEvent_t marks[kMaxMarks] = {};
   int mark_phase[kMaxMarks] = {};   // phase that ends at mark i (-1: start)

@@ -877,6 +877,27 @@ int op_deriv_phi(const cffyn_shell* sh, const double* in, double* out, int nfiel
   return launch(sh, deriv_args(sh, 2, in, out, nfields), sh->Dph, &sh->tDph, dim3(1, 1), st, 0, in_pairs);
 }
 
+// d_theta and d_phi of nf fields (same input; both operators have 2N rows):
+// one launch of the tcgen05 core on the mixed path, so that the two share
+// the last, partly filled wave of CTAs; two launches on the FP64 path.
+int op_deriv_theta_phi(const cffyn_shell* sh, const double* in, double* out_th, double* out_ph, int nf,
+                       bool in_pairs, cudaStream_t st) {
+  if (sh->d.precision != CFFYN_MIXED || sh->tDth2.rows != sh->tDph.rows) {
+    int rc = op_deriv_theta(sh, in, out_th, nf, in_pairs, st);
+    return rc ? rc : op_deriv_phi(sh, in, out_ph, nf, in_pairs, st);
+  }
+  TcBatch b;
+  memset(&b, 0, sizeof(b));
+  b.a[0] = deriv_args(sh, 1, in, out_th, nf);
+  b.W[0] = sh->tDth2;
+  b.a[1] = deriv_args(sh, 2, in, out_ph, nf);
+  b.W[1] = sh->tDph;
+  for (int c = 0; c < 2; ++c) b.tiles[c] = (b.a[c].g.ncols + kTcCols - 1) / kTcCols;
+  b.nclass = 2;
+  b.nm = 1;
+  return launch_batch(sh, b, st, 0, in_pairs, sh->exps);
+}
+
 static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb, int K, int P,
                    long long in_bs, long long out_bs, const double* W, const TcOp* Wt, cudaStream_t st,
                    int pairing) {

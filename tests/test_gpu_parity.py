@@ -199,7 +199,7 @@ def test_trace_and_profile_report_every_kernel_group(cf):
     assert all(v > 0 for v in ms.values())
     # 4 stages; the mixed path scans the field exponents of the input of each
     # of the four operator groups of a stage
-    assert launches["d_theta"] == 4 and launches["d_phi"] == 4 and launches["rhs_pp"] == 4
+    assert launches["d_theta_phi"] == 4 and launches["rhs_pp"] == 4
     assert launches["project"] == 4 and launches["d_r"] == 4 and launches["field_exp"] == 16
     # tracing does not change the result
     v = dev(u0)
