@@ -106,6 +106,58 @@ __device__ __forceinline__ void unrot_mat(const Triad<T>& t, const T O[3][3], T 
     for (int b = 0; b < 3; ++b) Tm[a][b] = X[a][0] * t.R[0][b] + X[a][1] * t.R[1][b] + X[a][2] * t.R[2][b];
 }
 
+// symmetric 3x3 (only b <= c of Tm read, only B <= C of O written):
+// O_BC = R_Bb R_Cc T_bc
+template <class T>
+__device__ __forceinline__ void rot_sym(const Triad<T>& t, const T Tm[3][3], T O[3][3]) {
+  auto sym = [&](int i, int j) -> T { return i <= j ? Tm[i][j] : Tm[j][i]; };
+  T X[3][3];  // X[B][c] = R_Bb T_bc
+#pragma unroll
+  for (int B = 0; B < 3; ++B)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) X[B][c] = t.R[B][0] * sym(0, c) + t.R[B][1] * sym(1, c) + t.R[B][2] * sym(2, c);
+#pragma unroll
+  for (int B = 0; B < 3; ++B)
+#pragma unroll
+    for (int C = B; C < 3; ++C) O[B][C] = X[B][0] * t.R[C][0] + X[B][1] * t.R[C][1] + X[B][2] * t.R[C][2];
+}
+// inverse of rot_sym: T_bc = R_Bb R_Cc O_BC (B <= C read, b <= c written)
+template <class T>
+__device__ __forceinline__ void unrot_sym(const Triad<T>& t, const T O[3][3], T Tm[3][3]) {
+  auto sym = [&](int i, int j) -> T { return i <= j ? O[i][j] : O[j][i]; };
+  T X[3][3];  // X[b][C] = R_Bb O_BC
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int C = 0; C < 3; ++C) X[b][C] = t.R[0][b] * sym(0, C) + t.R[1][b] * sym(1, C) + t.R[2][b] * sym(2, C);
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = b; c < 3; ++c) Tm[b][c] = X[b][0] * t.R[0][c] + X[b][1] * t.R[1][c] + X[b][2] * t.R[2][c];
+}
+// R_Ab with A known only at run time, and R_Ab with b known only at run time
+// (selects, so that the triad stays in registers)
+template <class T>
+__device__ __forceinline__ T triad_row_el(const Triad<T>& t, int A, int b) {
+  return A == 0 ? t.R[0][b] : (A == 1 ? t.R[1][b] : t.R[2][b]);
+}
+template <class T>
+__device__ __forceinline__ T triad_col_el(const Triad<T>& t, int A, int b) {
+  return b == 0 ? t.R[A][0] : (b == 1 ? t.R[A][1] : t.R[A][2]);
+}
+
+// Per-thread scratch in shared memory, [slot][thread] for blocks of 128
+// threads (consecutive threads, consecutive words): the rank-3 group keeps
+// its intermediates there so that its loops over the legs stay rolled (fully
+// unrolled, its double-float rotations overflow the instruction caches).
+template <class T>
+struct Scratch {
+  T* s;
+  __device__ __forceinline__ T& operator()(int v) const { return s[v * 128 + (int)threadIdx.x]; }
+};
+constexpr int kDecSlots = 26;  // Trot_a (3 x 6) | (P_rm, P_mm) of legs 1, 2 (2 x 4)
+constexpr int kRecSlots = 36;  // Trot_A (3 x 6) | X_A (3 x 6)
+
 // Slot assignment: 16 real spin-0 slots, then (re, im) pairs of spin 1 from
 // slot 16, of spin 2 from slot 38 and of spin 3 at slot 48; the numbers
 // below are the slots written by k_decompose and read back by k_reconstruct.
@@ -138,7 +190,7 @@ constexpr int kGroups = 8;
 constexpr int kMaxNv = 58;
 
 template <class T, bool FI>
-__device__ __forceinline__ void decompose_group(int grp, const double* __restrict__ in,
+__device__ __forceinline__ void decompose_group(int grp, Scratch<T> sc, const double* __restrict__ in,
                                                 double* __restrict__ out, long long P, long long p,
                                                 const Triad<T>& t) {
   const T two = S<T>::c(2.0);
@@ -212,54 +264,59 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
       break;
     }
     default: {
-      T Pr[3], Pmb[3], Prm[3][2], Pmm[3][2];
-      T Trot[3][3][3];
-#pragma unroll
+      // T_ijk (leg i: fields 20 + 10 i; jk symmetric): the pair jk into the
+      // triad for each i, then the leg i; slots 6 a + q hold Trot_a, q the
+      // index of (rr, r1, r2, 11, 12, 22)
+#pragma unroll 1
       for (int a = 0; a < 3; ++a) {
-        T Tm[3][3];
+        T Tm[3][3], O[3][3];
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) Tm[b][c] = ld<T, FI>(in, P, p, 20 + 10 * a + SI(b + 1, c + 1));
-        rot_mat(t, Tm, Trot[a]);
-      }
-#pragma unroll
-      for (int A = 0; A < 3; ++A) {
-        T O[3][3];
+          for (int c = b; c < 3; ++c) Tm[b][c] = ld<T, FI>(in, P, p, 20 + 10 * a + SI(b + 1, c + 1));
+        rot_sym(t, Tm, O);
 #pragma unroll
         for (int B = 0; B < 3; ++B)
 #pragma unroll
-          for (int C = 0; C < 3; ++C)
-            O[B][C] = t.R[A][0] * Trot[0][B][C] + t.R[A][1] * Trot[1][B][C] + t.R[A][2] * Trot[2][B][C];
-        Pr[A] = O[0][0];
-        Pmb[A] = O[1][1] + O[2][2];
-        Prm[A][0] = O[0][1];
-        Prm[A][1] = O[0][2];
-        Pmm[A][0] = O[1][1] - O[2][2];
-        Pmm[A][1] = two * O[1][2];
+          for (int C = B; C < 3; ++C) sc(6 * a + SI(B + 1, C + 1) - 4) = O[B][C];
       }
-      st<kIn<T>>(out, P, p, SLOT_R0(10), Pr[0]);
-      st<kIn<T>>(out, P, p, SLOT_R0(11), Pmb[0]);
-      st<kIn<T>>(out, P, p, SLOT_C1(7), Prm[0][0]);
-      st<kIn<T>>(out, P, p, SLOT_C1(7) + 1, Prm[0][1]);
-      st<kIn<T>>(out, P, p, SLOT_C2(3), Pmm[0][0]);
-      st<kIn<T>>(out, P, p, SLOT_C2(3) + 1, Pmm[0][1]);
-      st<kIn<T>>(out, P, p, SLOT_C1(8), Pr[1]);
-      st<kIn<T>>(out, P, p, SLOT_C1(8) + 1, Pr[2]);
-      st<kIn<T>>(out, P, p, SLOT_C1(9), Pmb[1]);
-      st<kIn<T>>(out, P, p, SLOT_C1(9) + 1, Pmb[2]);
+#pragma unroll 1
+      for (int A = 0; A < 3; ++A) {
+        const T r0 = triad_row_el(t, A, 0), r1 = triad_row_el(t, A, 1), r2 = triad_row_el(t, A, 2);
+        T O[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) O[q] = r0 * sc(q) + r1 * sc(6 + q) + r2 * sc(12 + q);
+        const T pr = O[0], pmb = O[3] + O[5], prm0 = O[1], prm1 = O[2], pmm0 = O[3] - O[5], pmm1 = two * O[4];
+        if (A == 0) {
+          st<kIn<T>>(out, P, p, SLOT_R0(10), pr);
+          st<kIn<T>>(out, P, p, SLOT_R0(11), pmb);
+          st<kIn<T>>(out, P, p, SLOT_C1(7), prm0);
+          st<kIn<T>>(out, P, p, SLOT_C1(7) + 1, prm1);
+          st<kIn<T>>(out, P, p, SLOT_C2(3), pmm0);
+          st<kIn<T>>(out, P, p, SLOT_C2(3) + 1, pmm1);
+        } else {
+          st<kIn<T>>(out, P, p, SLOT_C1(8) + A - 1, pr);
+          st<kIn<T>>(out, P, p, SLOT_C1(9) + A - 1, pmb);
+          sc(18 + 4 * (A - 1)) = prm0;
+          sc(19 + 4 * (A - 1)) = prm1;
+          sc(20 + 4 * (A - 1)) = pmm0;
+          sc(21 + 4 * (A - 1)) = pmm1;
+        }
+      }
+      const T prm10 = sc(18), prm11 = sc(19), pmm10 = sc(20), pmm11 = sc(21);
+      const T prm20 = sc(22), prm21 = sc(23), pmm20 = sc(24), pmm21 = sc(25);
       // (mbar; mm) = P_mm^theta - i P_mm^phi
-      st<kIn<T>>(out, P, p, SLOT_C1(10), Pmm[1][0] + Pmm[2][1]);
-      st<kIn<T>>(out, P, p, SLOT_C1(10) + 1, Pmm[1][1] - Pmm[2][0]);
+      st<kIn<T>>(out, P, p, SLOT_C1(10), pmm10 + pmm21);
+      st<kIn<T>>(out, P, p, SLOT_C1(10) + 1, pmm11 - pmm20);
       // (m; rm) = P_rm^theta + i P_rm^phi
-      st<kIn<T>>(out, P, p, SLOT_C2(4), Prm[1][0] - Prm[2][1]);
-      st<kIn<T>>(out, P, p, SLOT_C2(4) + 1, Prm[1][1] + Prm[2][0]);
+      st<kIn<T>>(out, P, p, SLOT_C2(4), prm10 - prm21);
+      st<kIn<T>>(out, P, p, SLOT_C2(4) + 1, prm11 + prm20);
       // (m; r mbar) = conj(P_rm^theta) + i conj(P_rm^phi)   (spin 0)
-      st<kIn<T>>(out, P, p, SLOT_R0(14), Prm[1][0] + Prm[2][1]);
-      st<kIn<T>>(out, P, p, SLOT_R0(15), Prm[2][0] - Prm[1][1]);
+      st<kIn<T>>(out, P, p, SLOT_R0(14), prm10 + prm21);
+      st<kIn<T>>(out, P, p, SLOT_R0(15), prm20 - prm11);
       // (m; mm) = P_mm^theta + i P_mm^phi
-      st<kIn<T>>(out, P, p, SLOT_C3, Pmm[1][0] - Pmm[2][1]);
-      st<kIn<T>>(out, P, p, SLOT_C3 + 1, Pmm[1][1] + Pmm[2][0]);
+      st<kIn<T>>(out, P, p, SLOT_C3, pmm10 - pmm21);
+      st<kIn<T>>(out, P, p, SLOT_C3 + 1, pmm11 + pmm20);
     }
   }
 }
@@ -267,7 +324,7 @@ __device__ __forceinline__ void decompose_group(int grp, const double* __restric
 // Inverse of decompose_group: the group's spin slots -> its Cartesian
 // components, each handed to emit(field, value).
 template <class T, class Emit>
-__device__ __forceinline__ void reconstruct_group(int grp, const double* __restrict__ sp, long long P,
+__device__ __forceinline__ void reconstruct_group(int grp, Scratch<T> sc, const double* __restrict__ sp, long long P,
                                                   long long p, const Triad<T>& t, Emit&& emit) {
   const T half = S<T>::c(0.5);
   switch (grp) {
@@ -374,39 +431,64 @@ __device__ __forceinline__ void reconstruct_group(int grp, const double* __restr
         Pmm[2][0] = half * (xi - zi);
         Pmm[2][1] = half * (zr - xr);
       }
-      T X[3][3][3];  // [A][b][c]: pair back in Cartesian, first leg in the triad
+      // slots 6 A + q: the pair part Trot_A of triad leg A (q: rr, r1, r2,
+      // 11, 12, 22); slots 18 + 6 A + q: X_A, the pair back in Cartesian
 #pragma unroll
       for (int A = 0; A < 3; ++A) {
-        T Trot[3][3];
-        Trot[0][0] = Pr[A];
-        Trot[0][1] = Trot[1][0] = Prm[A][0];
-        Trot[0][2] = Trot[2][0] = Prm[A][1];
-        Trot[1][1] = half * (Pmb[A] + Pmm[A][0]);
-        Trot[2][2] = half * (Pmb[A] - Pmm[A][0]);
-        Trot[1][2] = Trot[2][1] = half * Pmm[A][1];
-        unrot_mat(t, Trot, X[A]);
+        sc(6 * A + 0) = Pr[A];
+        sc(6 * A + 1) = Prm[A][0];
+        sc(6 * A + 2) = Prm[A][1];
+        sc(6 * A + 3) = half * (Pmb[A] + Pmm[A][0]);
+        sc(6 * A + 4) = half * Pmm[A][1];
+        sc(6 * A + 5) = half * (Pmb[A] - Pmm[A][0]);
       }
+#pragma unroll 1
+      for (int A = 0; A < 3; ++A) {
+        T Trot[3][3], X[3][3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
+        for (int B = 0; B < 3; ++B)
+#pragma unroll
+          for (int C = B; C < 3; ++C) Trot[B][C] = sc(6 * A + SI(B + 1, C + 1) - 4);
+        unrot_sym(t, Trot, X);
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-          for (int c = b; c < 3; ++c)
-            emit(20 + 10 * a + SI(b + 1, c + 1),
-                 t.R[0][a] * X[0][b][c] + t.R[1][a] * X[1][b][c] + t.R[2][a] * X[2][b][c]);
+          for (int c = b; c < 3; ++c) sc(18 + 6 * A + SI(b + 1, c + 1) - 4) = X[b][c];
+      }
+#pragma unroll 1
+      for (int a = 0; a < 3; ++a) {
+        const T r0 = triad_col_el(t, 0, a), r1 = triad_col_el(t, 1, a), r2 = triad_col_el(t, 2, a);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const int f = 20 + 10 * a + 4 + q;  // SI(b + 1, c + 1) = 4 + q
+          emit(f, r0 * sc(18 + q) + r1 * sc(24 + q) + r2 * sc(30 + q));
+        }
+      }
     }
   }
+}
+
+// Tensor group of blockIdx.y, the groups with the most components first
+// (7: 18, 6: 9, 4 and 5: 6, the gauge groups: 4, 1..3: 3, 0: 2), so that the
+// light ones fill the last wave of a launch; ng gauge groups.
+__device__ __forceinline__ int group_of(int y, int ng) {
+  if (y < 4) return y == 0 ? 7 : (y == 1 ? 6 : (y == 2 ? 4 : 5));
+  y -= 4;
+  if (y < ng) return 8 + y;
+  y -= ng;
+  return y < 3 ? 1 + y : 0;
 }
 
 template <class T, bool FI>
 __global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in, double* __restrict__ out,
                                                    Geo geo) {
+  __shared__ T sm[kDecSlots * 128];
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= geo.P) return;
   const int i = (int)((p / geo.n_r) % geo.N);
   const int jj = (int)(p / ((long long)geo.n_r * geo.N));
   const Triad<T> t = triad_at<T>(geo, i, jj);
-  decompose_group<T, FI>((int)blockIdx.y, in, out, geo.P, p, t);
+  decompose_group<T, FI>(group_of((int)blockIdx.y, (geo.nv - 50) / 4), Scratch<T>{sm}, in, out, geo.P, p, t);
 }
 
 // Output fields of each tensor group (see kGroups).
@@ -436,69 +518,45 @@ __host__ __device__ constexpr bool in_group(int G, int f) {
 // registers first, then the state words of all its fields are loaded at once
 // and updated.
 template <class T, bool FD, int G, int KIND>
-__device__ __forceinline__ void reconstruct_update(const double* __restrict__ sp, double* __restrict__ dst,
-                                                   const Geo& geo, int mode, double* __restrict__ u,
-                                                   double* __restrict__ U, double* __restrict__ kacc,
-                                                   double* __restrict__ uf, double dt, long long p,
-                                                   bool& bad) {
+__device__ __forceinline__ void reconstruct_update(Scratch<T> sc, const double* __restrict__ sp,
+                                                   double* __restrict__ dst, const Geo& geo, int mode,
+                                                   double* __restrict__ u, double* __restrict__ U,
+                                                   double* __restrict__ kacc, double* __restrict__ uf, double dt,
+                                                   long long p, bool& bad) {
   const long long P = geo.P;
   using SI_ = Store<T, kIn<T>>;
-  T kv[kMaxNv];
+  constexpr bool kPair = kIn<T>;  // mixed path: the step's initial state also as pairs in uf
+  const int stage = KIND == 0 ? 0 : (mode - 1) % 4;  // 0..3 for modes 1..8; KIND 2 is stage 3
+  const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
+  const T sixth = S<T>::c(dt / 6.0);
+  // the update of field f with its right-hand side k, as each k is formed
+  auto update = [&](int f, T k) {
+    const long long o = (long long)f * P + p;
+    if (KIND == 0) {
+      Store<T, FD>::st(dst, o, k);
+      if (kPair && uf) SI_::st(uf, o, k);
+    } else if (KIND == 1) {
+      bad |= !finite_s(k);
+      // stage state: FP64 sum on the FP64 path, double-float on the mixed path
+      const T base = kPair ? SI_::ld(uf, o) : S<T>::c(u[o]);
+      SI_::st(kacc, o, stage == 0 ? k : SI_::ld(kacc, o) + (k + k));
+      SI_::st(U, o, base + cU * k);
+    } else {
+      bad |= !finite_s(k);
+      const double un = u[o] + S<T>::to_double(sixth * (SI_::ld(kacc, o) + k));
+      u[o] = un;
+      if (kPair && uf) SI_::st(uf, o, S<T>::c(un));
+    }
+  };
   if (mode <= 4) {
     const int i = (int)((p / geo.n_r) % geo.N);
     const int jj = (int)(p / ((long long)geo.n_r * geo.N));
     const Triad<T> t = triad_at<T>(geo, i, jj);
-    reconstruct_group<T>(G, sp, P, p, t, [&](int f, T v) { kv[f] = v; });
+    reconstruct_group<T>(G, sc, sp, P, p, t, update);
   } else {
 #pragma unroll
     for (int f = 0; f < kMaxNv; ++f)
-      if (in_group(G, f)) kv[f] = ld<T, kIn<T>>(sp, P, p, f);
-  }
-  constexpr bool kPair = kIn<T>;  // mixed path: the step's initial state also as pairs in uf
-  if (KIND == 0) {
-#pragma unroll
-    for (int f = 0; f < kMaxNv; ++f)
-      if (in_group(G, f)) {
-        Store<T, FD>::st(dst, (long long)f * P + p, kv[f]);
-        if (kPair && uf) SI_::st(uf, (long long)f * P + p, kv[f]);
-      }
-    return;
-  }
-  const int stage = (mode - 1) % 4;  // 0..3 for modes 1..8; KIND 2 is stage 3
-  double uv[kMaxNv];
-  T ub[kMaxNv], ka[kMaxNv];
-#pragma unroll
-  for (int f = 0; f < kMaxNv; ++f)
-    if (in_group(G, f)) {
-      const long long o = (long long)f * P + p;
-      if (kPair && KIND == 1)
-        ub[f] = SI_::ld(uf, o);
-      else
-        uv[f] = u[o];
-      if (KIND == 2 || stage > 0) ka[f] = SI_::ld(kacc, o);
-    }
-  if (KIND == 1) {
-    const T cU = S<T>::c(stage == 2 ? dt : 0.5 * dt);
-#pragma unroll
-    for (int f = 0; f < kMaxNv; ++f)
-      if (in_group(G, f)) {
-        const long long o = (long long)f * P + p;
-        bad |= !finite_s(kv[f]);
-        SI_::st(kacc, o, stage == 0 ? kv[f] : ka[f] + (kv[f] + kv[f]));
-        // stage state: FP64 sum on the FP64 path, double-float on the mixed path
-        SI_::st(U, o, (kPair ? ub[f] : S<T>::c(uv[f])) + cU * kv[f]);
-      }
-  } else {
-    const T sixth = S<T>::c(dt / 6.0);
-#pragma unroll
-    for (int f = 0; f < kMaxNv; ++f)
-      if (in_group(G, f)) {
-        const long long o = (long long)f * P + p;
-        bad |= !finite_s(kv[f]);
-        const double un = uv[f] + S<T>::to_double(sixth * (ka[f] + kv[f]));
-        u[o] = un;
-        if (kPair && uf) SI_::st(uf, o, S<T>::c(un));
-      }
+      if (in_group(G, f)) update(f, ld<T, kIn<T>>(sp, P, p, f));
   }
 }
 
@@ -508,11 +566,13 @@ __global__ void __launch_bounds__(128, 4) k_reconstruct(const double* __restrict
                                                      double* __restrict__ U, double* __restrict__ kacc,
                                                      double* __restrict__ uf, double dt,
                                                      int* __restrict__ flag) {
+  __shared__ T sm[kRecSlots * 128];
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= geo.P) return;
   bool bad = false;
-#define CFFYN_RECON(G) reconstruct_update<T, FD, G, KIND>(sp, dst, geo, mode, u, U, kacc, uf, dt, p, bad)
-  switch (blockIdx.y) {
+  const Scratch<T> sc{sm};
+#define CFFYN_RECON(G) reconstruct_update<T, FD, G, KIND>(sc, sp, dst, geo, mode, u, U, kacc, uf, dt, p, bad)
+  switch (group_of((int)blockIdx.y, (geo.nv - 50) / 4)) {
     case 0: CFFYN_RECON(0); break;
     case 1: CFFYN_RECON(1); break;
     case 2: CFFYN_RECON(2); break;
