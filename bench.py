@@ -162,6 +162,10 @@ FAMILIES = {
     "k_field_exp": ["field_exp"],
 }
 PAIRS = 26  # BF16 digit-pair products per operator product (i + j <= 6 of 6 x 6)
+# DRAM bytes per step of all k_op_tc launches, from the ncu launch list of the
+# same command (profiles/launch_list_ks_33x48x96_mixed.md); None where no
+# capture of the current kernel exists.
+OP_TRAFFIC_PER_STEP = {"ks_33x48x96": 2.03e9}
 
 
 def _op_flops(w, phase):
@@ -209,7 +213,9 @@ def _roofline(w, per_step, launches, hbm, bf16s, peak_kind):
                               "tensor_frac": PAIRS * 4 * _op_flops(w, ph) / tl / 1e12 / bf16s}
         return {"bound": "tensor", "kernel": "k_op_tc (all operator launches of the step)",
                 "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
-                "traffic": None, "peak_source": f"bf16_tflops_sustained ({peak_kind})",
+                "traffic": OP_TRAFFIC_PER_STEP.get(w["name"]),
+                "traffic_scope": "DRAM bytes per step, all k_op_tc launches (ncu launch list)",
+                "peak_source": f"bf16_tflops_sustained ({peak_kind})",
                 "work": "26 BF16 digit-pair products x method FP64 operator flops "
                         "(2n_r + 16N + 2(L+1) per pt-field per substep)",
                 "fp64_equiv_tflops": fl / t / 1e12,
