@@ -24,7 +24,8 @@ swsh     normalised associated Legendre functions, spin-weighted recursion
          pseudo-inverse (eq. forwardL) and filter matrices F = P f P^+
          (eq. FasPfQ).
 ynfilter triad decomposition of Cartesian tensors (Sec. 3.4, eqs. tetrad,
-         tensorexpansion) and the Yn tensor filter (Sec. 3.5).
+         tensorexpansion), the Yn tensor filter (Sec. 3.5), and the
+         component-wise Y and graded Yg filters (Sec. 3.5, eq. nfofmu).
 ghg      first-order GHG right-hand side (App. A.1, eqs. gdot, Phidot, Pidot),
          freeze-incoming outer boundary condition (App. A.2), gauge source
          initialisation (eq. gauge) and constraint norms.

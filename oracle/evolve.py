@@ -25,9 +25,12 @@ class OracleShell:
     """All precomputed matrices of one shell plus the static gauge source."""
 
     def __init__(self, n_r, n_theta, n_phi, r_in, r_out, L, n_fields=50,
-                 filter_mode="substep"):
+                 filter_mode="substep", filter_kind="yn"):
         assert n_phi == 2 * n_theta
         assert n_fields in (50, 54, 58)
+        assert filter_kind in ("yn", "y", "yg")
+        self.filter_kind = filter_kind
+        self._sf_at = {}
         self.n_r, self.N, self.J = n_r, n_theta, n_phi
         self.r_in, self.r_out, self.L = r_in, r_out, L
         self.n_fields = n_fields
@@ -84,8 +87,24 @@ class OracleShell:
         del shp
         return ghg.apply_outer_bc(out, u, self.theta, self.phi)
 
+    def sf_at(self, L_keep):
+        """SpinFilter of another retained degree (the graded filter's)."""
+        if L_keep == self.L:
+            return self.sf
+        if L_keep not in self._sf_at:
+            self._sf_at[L_keep] = ynfilter.SpinFilter(self.theta, self.phi, L_keep)
+        return self._sf_at[L_keep]
+
     def filter(self, u):
-        return ynfilter.filter_state(u, self.sf, self.n_fields)
+        """Yn tensor filter (Sec. 3.5), or the component-wise Y / Yg filters."""
+        if self.filter_kind == "yn":
+            return ynfilter.filter_state(u, self.sf, self.n_fields)
+        sfs = {None: self.sf}
+        if self.filter_kind == "yg":
+            for d in range(1, 4):
+                Lk = min(self.L + d, self.N - 1)
+                sfs[Lk] = self.sf_at(Lk)
+        return ynfilter.filter_state_scalar(u, sfs, self.n_fields, graded=self.filter_kind == "yg")
 
     def stage(self, u):
         k = self.rhs(u)

@@ -169,3 +169,32 @@ def filter_state(u, sf, n_fields=50, return_imag=False):
     if return_imag:
         return out, imag_max
     return out
+
+
+def spatial_degree(mu):
+    """d(u^mu) of Sec. 3.5: the number of spatial indices of field mu in the
+    field order of this project (g_ab 0..9, Pi_ab 10..19, Phi_iab 20..49 with
+    i the derivative leg, H_a 50..53, dH_a/dt 54..57; pairs in the order
+    tt, tx, ty, tz, xx, xy, xz, yy, yz, zz)."""
+    if mu >= 50:
+        return 0 if (mu - 50) % 4 == 0 else 1
+    s = mu % 10
+    pair = SYM_PAIRS[s]
+    d = sum(1 for x in pair if x > 0)
+    return d + (1 if mu >= 20 else 0)
+
+
+def filter_state_scalar(u, sfs, n_fields=50, graded=False):
+    """The component-wise filters of Sec. 3.5: every field u^mu filtered as a
+    scalar (spin 0) function.  Y filter (graded=False): retained degree L for
+    every field.  Yg filter (graded=True, eq. nfofmu): n_f(mu) = n_f - d(u^mu)
+    top modes zeroed, i.e. retained degree L + d(u^mu) (at most N - 1).
+    sfs maps a retained degree to a SpinFilter; sfs[None] is the one of L."""
+    out = np.array(u, copy=True)
+    base = sfs[None].L_keep
+    N = sfs[None].N
+    for mu in range(n_fields):
+        Lk = min(base + spatial_degree(mu), N - 1) if graded else base
+        sf = sfs[Lk] if Lk != base else sfs[None]
+        out[mu] = sf.filter_function(u[mu][None].astype(complex), 0)[0].real
+    return out
