@@ -40,6 +40,8 @@ def _args():
     ap.add_argument("--workload", default="ks_33x48x96")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--filter", default="yn", choices=["yn", "y", "yg"],
+                    help="filter of the single-shell workloads: tensor Yn (default), scalar Y, graded Yg")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one eager RK4 step with per-group device times and print them "
                          "(the fixed launch sequence used for profiler captures)")
@@ -243,8 +245,9 @@ def run_ours(args, rank, local_rank, ws, dist):
     units_per_step = P * w["n_fields"]
     u0 = _state(w)
 
+    fk = {"yn": cffyn.FILTER_YN, "y": cffyn.FILTER_Y, "yg": cffyn.FILTER_YG}[args.filter]
     sh = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, n_fields=w["n_fields"],
-                     precision=cffyn.MIXED)
+                     precision=cffyn.MIXED, filter_kind=fk)
     dt = w["lam"] * sh.default_dt() / 0.25
     u = torch.from_numpy(u0).cuda()
     sh.init_gauge_from_state(u)
@@ -295,7 +298,7 @@ def run_ours(args, rank, local_rank, ws, dist):
     fp64 = None
     if not args.no_fp64:
         s64 = cffyn.Shell(n_r, N, J, w["r_in"], w["r_out"], L, n_fields=w["n_fields"],
-                          precision=cffyn.FP64)
+                          precision=cffyn.FP64, filter_kind=fk)
         v = torch.from_numpy(u0).cuda()
         s64.init_gauge_from_state(v)
         vf = torch.empty_like(v)
@@ -358,7 +361,8 @@ def run_ours(args, rank, local_rank, ws, dist):
         "data": "synthetic (seeded Kerr-Schild + l<=4 perturbation, amplitude 1e-4)",
         "config": {"workload": w["name"], "n_r": n_r, "n_theta": N, "n_phi": J,
                    "n_fields": w["n_fields"], "L": L, "r": [w["r_in"], w["r_out"]],
-                   "dt": dt, "filter": "Yn on every stage rhs", "precision": "mixed",
+                   "dt": dt, "filter": {"yn": "Yn", "y": "Y", "yg": "Yg"}[args.filter] + " on every stage rhs",
+                   "precision": "mixed",
                    "parallelism": f"replicas x{ws}",
                    "l2": "flushed (256 MiB write) before every timed step"},
         "roofline": roof,

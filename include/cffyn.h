@@ -72,8 +72,12 @@ extern "C" {
 #define CFFYN_FILTER_SUBSTEP 0 /* every stage right-hand side after the BC */
 #define CFFYN_FILTER_STEP 1    /* the state after each full RK4 step (paper) */
 
-/* Which filter (Sec. 3.5).  Only the tensor filter Yn is built; the
- * component-wise Y and Yg filters return CFFYN_ENOTIMPL. */
+/* Which filter (Sec. 3.5).  Yn: the tensor filter (triad decomposition,
+ * projection of every spin-weight component with F^n_m).  Y: every field
+ * projected as a scalar with F^0_m at the retained degree L.  Yg: the graded
+ * Y filter of eq. nfofmu, n_f(mu) = n_f - d(u^mu): a field with d spatial
+ * indices (g_tt 0, g_ti 1, g_ij 2, Phi_ijk 3, H_t 0, H_i 1) keeps
+ * l <= min(L + d, n_theta - 1). */
 #define CFFYN_FILTER_YN 0
 #define CFFYN_FILTER_Y 1
 #define CFFYN_FILTER_YG 2
@@ -97,7 +101,7 @@ typedef struct cffyn_shell_desc {
   int precision;    /* CFFYN_FP64 or CFFYN_MIXED */
   int filter_mode;  /* CFFYN_FILTER_SUBSTEP or CFFYN_FILTER_STEP */
   double courant;   /* lambda of dt = lambda * min dx (Sec. 4.1); <= 0 -> 0.25 */
-  int filter_kind;  /* CFFYN_FILTER_YN (0) */
+  int filter_kind;  /* CFFYN_FILTER_YN (0), CFFYN_FILTER_Y or CFFYN_FILTER_YG */
   int flags;        /* 0 or CFFYN_DEFER_WORKSPACE */
 } cffyn_shell_desc;
 
@@ -108,10 +112,9 @@ typedef struct cffyn_shell_desc {
  * FP64 on the current CUDA device, plus the library's workspace.
  * Defaults of cffyn_create_shell: 50 fields, CFFYN_MIXED, CFFYN_FILTER_SUBSTEP,
  * courant 0.25.  Synchronous.  Returns CFFYN_EINVAL for sizes outside the
- * ranges above (or n_theta > 96, n_r > 96) and for unknown flags,
- * CFFYN_ENOTIMPL for a filter kind other than CFFYN_FILTER_YN, CFFYN_ENOMEM /
- * CFFYN_ECUDA on device failures; *out is NULL on error.  cffyn_create_shell
- * takes filter_kind 0 and flags 0. */
+ * ranges above (or n_theta > 96, n_r > 96), for an unknown filter kind or
+ * flags, CFFYN_ENOMEM / CFFYN_ECUDA on device failures; *out is NULL on
+ * error.  cffyn_create_shell takes filter_kind CFFYN_FILTER_YN and flags 0. */
 CFFYN_API int cffyn_create_shell(int n_r, int n_theta, int n_phi, double r_in, double r_out, int L,
                        cffyn_shell** out);
 CFFYN_API int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out);
@@ -168,9 +171,11 @@ CFFYN_API int cffyn_derivs(cffyn_shell* sh, const double* u, double* dxyz, void*
  * outermost sphere; no filter.  Requires the gauge for 50 fields. */
 CFFYN_API int cffyn_rhs(cffyn_shell* sh, const double* u, double* dudt, void* stream);
 
-/* Yn tensor filter of Secs. 3.4-3.5: per tensor group, triad decomposition
- * (eq. tensorexpansion), phi DFT (eq. forwardF), projection with F^n_m per spin
- * n and azimuthal m (eq. FasPfQ), inverse DFT, recombination.  out may alias u. */
+/* The shell's filter (Secs. 3.4-3.5).  Yn: per tensor group, triad
+ * decomposition (eq. tensorexpansion), phi DFT (eq. forwardF), projection with
+ * F^n_m per spin n and azimuthal m (eq. FasPfQ), inverse DFT, recombination.
+ * Y / Yg: phi DFT, projection with F^0_m at each field's retained degree,
+ * inverse DFT.  out may alias u. */
 CFFYN_API int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream);
 
 /* n_steps classical RK4 steps of the method of lines (Sec. 2.5) in place on u

@@ -3,6 +3,7 @@
 // out of the operator kernels (ops.cu) and the pointwise kernels
 // (pointwise.cu).  One RK4 step is captured once into a CUDA graph and
 // replayed.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -30,8 +31,9 @@ int op_deriv_r(const cffyn_shell*, const double*, double*, int, bool, cudaStream
 int op_deriv_theta(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int op_deriv_phi(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int op_deriv_theta_phi(const cffyn_shell*, const double*, double*, double*, int, bool, cudaStream_t);
-int op_dft_fwd(const cffyn_shell*, const double*, double*, int, cudaStream_t);
-int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t);
+int op_dft_fwd(const cffyn_shell*, const double*, double*, int, cudaStream_t, int);
+int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t, int);
+int op_project_scalar(const cffyn_shell*, const double*, double*, cudaStream_t);
 int op_project(const cffyn_shell*, const double*, double*, const int*, int, const int* const[3],
                const int[3], cudaStream_t);
 int op_prepare(const cffyn_shell*, const double*, bool, int, long long, int, cudaStream_t);
@@ -122,21 +124,27 @@ int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, bool i
   return CFFYN_OK;
 }
 
-// spin slots in `spin` (nv x P) -> filtered spin slots back in `spin`;
-// scratch: D (2 nv P)
+// Filter of the functions in `spin` (nv x P), in place, scratch D (2 nv P):
+// Yn: the spin slots of the triad decomposition, projected per spin class;
+// Y / Yg: the Cartesian fields themselves, each with F^0_m (Sec. 3.5).
+bool yn_filter(const cffyn_shell* sh) { return sh->d.filter_kind == CFFYN_FILTER_YN; }
+
 int filter_spin_slots(cffyn_shell* sh, double* spin, cudaStream_t st) {
   const size_t nvP = (size_t)sh->nv * sh->P;
   int rc;
   double* C = sh->D;
   double* C2 = sh->D + nvP;
   const long long lc = (long long)sh->R * sh->N * sh->n_r;  // coefficient values per function
-  if ((rc = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, 1, st))) return rc;
-  if ((rc = op_dft_fwd(sh, spin, C, sh->nv, st))) return rc;
+  const int pairing = yn_filter(sh) ? 1 : 0;
+  if ((rc = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, pairing, st))) return rc;
+  if ((rc = op_dft_fwd(sh, spin, C, sh->nv, st, pairing))) return rc;
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
-  if ((rc = op_prepare(sh, C, true, sh->nv, lc, 1, st))) return rc;
-  if ((rc = op_project(sh, C, C2, slots_r0(sh), sh->nR0, cl, sh->nC, st))) return rc;
-  if ((rc = op_prepare(sh, C2, true, sh->nv, lc, 1, st))) return rc;
-  if ((rc = op_dft_inv(sh, C2, spin, sh->nv, st))) return rc;
+  if ((rc = op_prepare(sh, C, true, sh->nv, lc, pairing, st))) return rc;
+  if ((rc = yn_filter(sh) ? op_project(sh, C, C2, slots_r0(sh), sh->nR0, cl, sh->nC, st)
+                          : op_project_scalar(sh, C, C2, st)))
+    return rc;
+  if ((rc = op_prepare(sh, C2, true, sh->nv, lc, pairing, st))) return rc;
+  if ((rc = op_dft_inv(sh, C2, spin, sh->nv, st, pairing))) return rc;
   return CFFYN_OK;
 }
 
@@ -144,15 +152,16 @@ void free_shell(cffyn_shell* sh) {
   if (!sh) return;
   cudaDeviceSynchronize();
   double** ptrs[] = {&sh->r,   &sh->sth, &sh->cth,  &sh->sph,  &sh->cph,    &sh->Dr,     &sh->Dth2,
-                     &sh->Dph, &sh->Fan, &sh->Fsy,  &sh->Fraw, &sh->Fproj0, &sh->FprojC, &sh->H,
+                     &sh->Dph, &sh->Fan, &sh->Fsy,  &sh->Fraw, &sh->Fproj0, &sh->FprojC, &sh->F0g, &sh->H,
                      &sh->dH,  &sh->red, &sh->triad};
   for (double** p : ptrs)
     if (*p) cudaFree(*p);
   if (sh->ws_owned && sh->ws) cudaFree(sh->ws);
   TcOp* to[] = {&sh->tDr, &sh->tDth2, &sh->tDph, &sh->tFan, &sh->tFsy, &sh->tF0,
-                &sh->tFC[0], &sh->tFC[1], &sh->tFC[2]};
+                &sh->tFC[0], &sh->tFC[1], &sh->tFC[2], &sh->tF0g[0], &sh->tF0g[1], &sh->tF0g[2], &sh->tF0g[3]};
   for (TcOp* t : to) free_tc(*t);
   if (sh->slots) cudaFree(sh->slots);
+  if (sh->yslots) cudaFree(sh->yslots);
   if (sh->exps) cudaFree(sh->exps);
   if (sh->cap_stream) cudaStreamDestroy(sh->cap_stream);
   if (sh->flag_host) cudaFreeHost(sh->flag_host);
@@ -204,11 +213,7 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     set_error("unknown flags 0x%x", d.flags);
     return CFFYN_EINVAL;
   }
-  if (d.filter_kind == CFFYN_FILTER_Y || d.filter_kind == CFFYN_FILTER_YG) {
-    set_error("filter kind %d: only the tensor filter Yn (CFFYN_FILTER_YN) is built", d.filter_kind);
-    return CFFYN_ENOTIMPL;
-  }
-  if (d.filter_kind != CFFYN_FILTER_YN) {
+  if (d.filter_kind != CFFYN_FILTER_YN && d.filter_kind != CFFYN_FILTER_Y && d.filter_kind != CFFYN_FILTER_YG) {
     set_error("unknown filter kind %d", d.filter_kind);
     return CFFYN_EINVAL;
   }
@@ -222,7 +227,8 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
   sh->N = d.n_theta;
   sh->J = d.n_phi;
   sh->L = d.L;
-  sh->R = 2 * d.L + 1;
+  sh->Lrows = d.filter_kind == CFFYN_FILTER_YG ? std::min(d.L + 3, d.n_theta - 1) : d.L;
+  sh->R = 2 * sh->Lrows + 1;
   sh->nv = d.n_fields;
   sh->ng = (d.n_fields - 50) / 4;
   sh->nR0 = 16 + 2 * sh->ng;
@@ -293,6 +299,28 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     host[n++] = 48;
     if (cudaMalloc(&sh->slots, n * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
     if (cudaMemcpy(sh->slots, host, n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(CFFYN_ECUDA);
+  }
+  if (d.filter_kind != CFFYN_FILTER_YN) {
+    // component-wise filters: the fields, by spatial degree d(u^mu) for Yg
+    // (Sec. 3.5: pairs tt, ti, ij of g_ab and Pi_ab have 0, 1, 2 spatial
+    // indices, Phi_iab one more, H_t 0 and H_i 1), all in one list for Y
+    auto degree = [](int mu) {
+      if (mu >= 50) return (mu - 50) % 4 == 0 ? 0 : 1;
+      const int s = mu % 10;
+      return (s == 0 ? 0 : (s < 4 ? 1 : 2)) + (mu >= 20 ? 1 : 0);
+    };
+    const bool graded = d.filter_kind == CFFYN_FILTER_YG;
+    int host[64];
+    int n = 0;
+    for (int dd = 0; dd < 4; ++dd) {
+      const int n0 = n;
+      for (int mu = 0; mu < sh->nv; ++mu)
+        if (graded ? degree(mu) == dd : dd == 0) host[n++] = mu;
+      sh->ny[dd] = n - n0;
+    }
+    if (cudaMalloc(&sh->yslots, n * sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
+    if (cudaMemcpy(sh->yslots, host, n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(CFFYN_ECUDA);
   }
   if (cudaMalloc(&sh->flag, 64) != cudaSuccess) return fail(CFFYN_ENOMEM);
@@ -436,9 +464,14 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
   if ((rc = check_ptr(u, "u")) || (rc = check_ptr(out, "out"))) return rc;
   if ((rc = check_ws(sh))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = pw_decompose(sh, u, sh->S, false, st))) return rc;
+  if (yn_filter(sh)) {
+    if ((rc = pw_decompose(sh, u, sh->S, false, st))) return rc;
+    if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
+    return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+  }
+  if ((rc = pw_to_internal(sh, u, sh->S, (long long)sh->nv * sh->P, st))) return rc;
   if ((rc = filter_spin_slots(sh, sh->S, st))) return rc;
-  return pw_reconstruct(sh, sh->S, out, 0, nullptr, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
+  return pw_reconstruct(sh, sh->S, out, 9, nullptr, nullptr, nullptr, nullptr, 0.0, sh->flag, st);
 }
 
 // The kernel groups of one RK4 step (Sec. 2.5) in order.  run(phase, fn)
@@ -457,16 +490,22 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
   auto prep = [&](const double* in, bool pairs, long long len, int pairing) {
     return run(10, [&] { return op_prepare(sh, in, pairs, sh->nv, len, pairing, st); });
   };
-  // Yn filter of the spin slots in `spin` (in place through D and D + nvP)
+  // filter of the functions in `spin` (in place through D and D + nvP): the
+  // spin slots for Yn, the Cartesian fields for Y / Yg
+  const bool yn = yn_filter(sh);
+  const int pairing = yn ? 1 : 0;
   auto filter = [&](double* spin) -> int {
     int r;
-    if ((r = prep(spin, true, P, 1))) return r;
-    if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st); }))) return r;
-    if ((r = prep(sh->D, true, lc, 1))) return r;
-    if ((r = run(7, [&] { return op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st); })))
+    if ((r = prep(spin, true, P, pairing))) return r;
+    if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st, pairing); }))) return r;
+    if ((r = prep(sh->D, true, lc, pairing))) return r;
+    if ((r = run(7, [&] {
+           return yn ? op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st)
+                     : op_project_scalar(sh, sh->D, sh->D + nvP, st);
+         })))
       return r;
-    if ((r = prep(sh->D + nvP, true, lc, 1))) return r;
-    return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st); });
+    if ((r = prep(sh->D + nvP, true, lc, pairing))) return r;
+    return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st, pairing); });
   };
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   for (int s = 0; s < 4; ++s) {
@@ -483,7 +522,7 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
     if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
     if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
     if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
-    if (per_sub) {
+    if (per_sub && yn) {
       if ((rc = run(5, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
       if ((rc = filter(spin))) return rc;
       if ((rc = run(9, [&] {
@@ -491,6 +530,9 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
            })))
         return rc;
     } else {
+      // unfiltered stage rhs (per-step placement), or the component-wise
+      // filter applied to the Cartesian rhs in place
+      if (per_sub && (rc = filter(sh->S))) return rc;
       if ((rc = run(9, [&] {
              return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
            })))
@@ -498,10 +540,19 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
     }
   }
   if (!per_sub) {
-    if ((rc = run(5, [&] { return pw_decompose(sh, mixed ? sh->Uf : u, sh->S, mixed, st); }))) return rc;
+    if (yn) {
+      if ((rc = run(5, [&] { return pw_decompose(sh, mixed ? sh->Uf : u, sh->S, mixed, st); }))) return rc;
+    } else {
+      // the Cartesian state itself (pairs on the mixed path)
+      if ((rc = run(5, [&] {
+             CF_CUDA(cudaMemcpyAsync(sh->S, mixed ? sh->Uf : u, nvP * sizeof(double), cudaMemcpyDeviceToDevice, st));
+             return CFFYN_OK;
+           })))
+        return rc;
+    }
     if ((rc = filter(sh->S))) return rc;
     if ((rc = run(9, [&] {
-           return pw_reconstruct(sh, sh->S, u, 0, nullptr, nullptr, nullptr, sh->Uf, 0.0, sh->flag, st);
+           return pw_reconstruct(sh, sh->S, u, yn ? 0 : 9, nullptr, nullptr, nullptr, sh->Uf, 0.0, sh->flag, st);
          })))
       return rc;
   }

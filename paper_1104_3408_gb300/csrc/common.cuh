@@ -56,7 +56,8 @@ struct cffyn_shell_impl;
 
 struct cffyn_shell {
   cffyn_shell_desc d;
-  int n_r, N, J, L, nv, R;      // R = 2L + 1 Fourier rows kept
+  int n_r, N, J, L, nv, R;      // R = 2 Lrows + 1 Fourier rows kept
+  int Lrows;                    // azimuthal modes kept by the phi DFT: L, or L + 3 (at most N - 1) for Yg
   size_t P;                     // points per field
   double dt_default;
   size_t bytes = 0;
@@ -75,10 +76,11 @@ struct cffyn_shell {
   double* Fraw = nullptr;   // [7][L+1] N x N : F^n_m, n = -3..3
   double* Fproj0 = nullptr; // [L+1] N x N : F^0_m
   double* FprojC = nullptr; // [3][L+1] N x 2N : [F_s | F_d] for spin 1..3
+  double* F0g = nullptr;    // graded filter: [4][Lrows+1] N x N : F^0_m at retained degree L + d
 
   // split-precision operators (tcgen05 core); tF0 and tFC are batched over
   // m = 0..L, tFC per spin 1..3
-  cffyn::TcOp tDr, tDth2, tDph, tFan, tFsy, tF0, tFC[3];
+  cffyn::TcOp tDr, tDth2, tDph, tFan, tFsy, tF0, tFC[3], tF0g[4];
 
   // spin slots of the filter (one real slot per Cartesian field): nR0 real
   // functions filtered with F^0_m (spin 0, including the real and imaginary
@@ -88,6 +90,10 @@ struct cffyn_shell {
   // real slots (H_t, H_r) and one spin-1 pair.
   int ng = 0;                    // gauge groups: (nv - 50) / 4
   int nR0 = 16, nC[3] = {11, 5, 1};
+  // component-wise filters: fields by spatial degree d (Yg: 4 lists; Y: one
+  // list of every field) in yslots, ny[d] entries each
+  int* yslots = nullptr;
+  int ny[4] = {0, 0, 0, 0};
 
   // gauge
   double* H = nullptr;    // [4][P]

@@ -829,7 +829,7 @@ static OpArgs base_args(const cffyn_shell* sh) {
   a.N = sh->N;
   a.J = sh->J;
   a.R = sh->R;
-  a.L = sh->L;
+  a.L = sh->Lrows;  // row of b_1 minus 1 in the DFT coefficient layout
   return a;
 }
 
@@ -915,17 +915,68 @@ static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb,
   return launch(sh, a, W, Wt, dim3(1, 1), st, pairing, true);
 }
 
-// phi analysis: S[f][j][i][k] -> C[f][row][i][k] (pair-stored input on the mixed path)
-int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
+// phi analysis: S[f][j][i][k] -> C[f][row][i][k] (pair-stored input on the
+// mixed path); pairing: the exponents of slot pairs (f, f ^ 1) are shared
+// (the complex slots of the Yn filter)
+int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st, int pairing) {
   long long Q = (long long)sh->N * sh->n_r;
   return op_rows(sh, in, out, nf, sh->J, sh->R, (long long)sh->J * Q, (long long)sh->R * Q, sh->Fan,
-                 &sh->tFan, st, 1);
+                 &sh->tFan, st, pairing);
 }
 
-int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st) {
+int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st, int pairing) {
   long long Q = (long long)sh->N * sh->n_r;
   return op_rows(sh, in, out, nf, sh->R, sh->J, (long long)sh->R * Q, (long long)sh->J * Q, sh->Fsy,
-                 &sh->tFsy, st, 1);
+                 &sh->tFsy, st, pairing);
+}
+
+// Component-wise filters (Sec. 3.5): every field's coefficients projected
+// with F^0_m, C -> C2: the Y filter at the retained degree L (one class), the
+// graded Yg filter at L + d for the fields of spatial degree d (eq. nfofmu;
+// one class per d), m = 0..Lrows; one launch on the mixed path.
+int op_project_scalar(const cffyn_shell* sh, const double* C, double* C2, cudaStream_t st) {
+  const int N = sh->N;
+  const bool graded = sh->d.filter_kind == CFFYN_FILTER_YG;
+  const int nm = sh->Lrows + 1;
+  OpArgs cls[4];
+  const double* W64[4];
+  const TcOp* Wt[4];
+  int ncls = 0, off = 0;
+  for (int d = 0; d < 4; ++d) {
+    if (sh->ny[d] <= 0) continue;
+    OpArgs a = base_args(sh);
+    a.in = C;
+    a.out = C2;
+    a.kind = OP_PROJ0;
+    a.slots = sh->yslots + off;
+    a.nslots = sh->ny[d];
+    a.batched_m = 1;
+    a.w_stride = (long long)N * N;
+    a.g.K = a.g.K0 = a.g.P = a.g.P0 = N;
+    a.g.in_rs = a.g.out_rs = sh->n_r;
+    a.g.ncols = (long long)sh->ny[d] * 2 * sh->n_r;
+    off += sh->ny[d];
+    cls[ncls] = a;
+    W64[ncls] = graded ? sh->F0g + (size_t)d * nm * N * N : sh->Fproj0;
+    Wt[ncls++] = graded ? &sh->tF0g[d] : &sh->tF0;
+  }
+  if (sh->d.precision == CFFYN_MIXED) {
+    TcBatch bt;
+    memset(&bt, 0, sizeof(bt));
+    for (int c = 0; c < ncls; ++c) {
+      bt.a[c] = cls[c];
+      bt.W[c] = *Wt[c];
+      bt.tiles[c] = (cls[c].g.ncols + kTcCols - 1) / kTcCols;
+    }
+    bt.nclass = ncls;
+    bt.nm = nm;
+    return launch_batch(sh, bt, st, 0, true, sh->exps);
+  }
+  for (int c = 0; c < ncls; ++c) {
+    int rc = launch(sh, cls[c], W64[c], Wt[c], dim3(1, nm), st, 0, true);
+    if (rc) return rc;
+  }
+  return CFFYN_OK;
 }
 
 // Projection of all spin classes, coefficients C -> C2 (same layout): every

@@ -505,7 +505,8 @@ __host__ __device__ constexpr bool in_group(int G, int f) {
                 : (f >= 54 && f < 58);
 }
 
-// mode: 0 = write filtered tensor to `dst`;
+// mode: 0 = write filtered tensor to `dst`; 9 = the same from Cartesian
+//       values in sp (component-wise filters);
 //       1..4 = RK4 stage s (1-based) with filtered rhs k_s = reconstruct(sp);
 //       5..8 = RK4 stage without filter: k_s read as Cartesian from sp.
 // Stage updates: k_1: acc = k, U = u + dt/2 k; k_2: acc += 2k, U = u + dt/2 k;
@@ -713,7 +714,7 @@ int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mod
   Geo g = geo_of(sh);
   const dim3 grid(blocks_for(g.P, 128), kGroups + sh->ng);
   // kernel instance by stage kind: 0 filtered result, 1 stages 1-3, 2 last stage
-  const int kind = mode == 0 ? 0 : ((mode - 1) % 4 == 3 ? 2 : 1);
+  const int kind = (mode == 0 || mode == 9) ? 0 : ((mode - 1) % 4 == 3 ? 2 : 1);
   if (sh->d.precision == CFFYN_MIXED) {
     if (kind == 0)
       k_reconstruct<ff, false, 0><<<grid, 128, 0, st>>>(sp, dst, g, mode, u, U, kacc, uf, dt, flag);

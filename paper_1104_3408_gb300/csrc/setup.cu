@@ -408,7 +408,7 @@ void free_tc(TcOp& s) {
 
 // Builds every operator of the shell.  Called from cffyn_create_shell_ex.
 int build_operators(cffyn_shell* sh) {
-  const int n_r = sh->n_r, N = sh->N, J = sh->J, L = sh->L, R = sh->R;
+  const int n_r = sh->n_r, N = sh->N, J = sh->J, L = sh->L, R = sh->R, Lrows = sh->Lrows;
   size_t& B = sh->bytes;
   auto alloc = [&](double** p, size_t n) -> int {
     CF_CUDA(cudaMalloc(p, n * sizeof(double)));
@@ -427,7 +427,7 @@ int build_operators(cffyn_shell* sh) {
   if ((rc = alloc(&sh->Dph, (size_t)J * J)) || (rc = alloc(&sh->Dth2, (size_t)4 * N * N))) return rc;
   k_fourier_ops<<<(J * J + 255) / 256, 256>>>(sh->Dph, J, sh->Dth2, N);
   if ((rc = alloc(&sh->Fan, (size_t)R * J)) || (rc = alloc(&sh->Fsy, (size_t)J * R))) return rc;
-  k_dft<<<(R * J + 255) / 256, 256>>>(sh->Fan, sh->Fsy, J, L);
+  k_dft<<<(R * J + 255) / 256, 256>>>(sh->Fan, sh->Fsy, J, Lrows);
   CF_CUDA(cudaGetLastError());
 
   // spin-weighted Legendre and filter matrices for m = 0..L
@@ -450,6 +450,32 @@ int build_operators(cffyn_shell* sh) {
   cudaFree(tmp);
   cudaFree(scratch);
 
+  // graded filter (eq. nfofmu): F^0_m at the retained degrees L + d,
+  // d = 0..3 (at most N - 1), for m = 0..Lrows
+  if (sh->d.filter_kind == CFFYN_FILTER_YG) {
+    const int nmg = Lrows + 1;
+    double *Pg = nullptr, *tg = nullptr, *sg = nullptr, *Fg = nullptr;
+    CF_CUDA(cudaMalloc(&Pg, (size_t)7 * nmg * N * N * sizeof(double)));
+    CF_CUDA(cudaMalloc(&tg, (size_t)N * nmg * 8 * N * sizeof(double)));
+    CF_CUDA(cudaMalloc(&sg, (size_t)7 * nmg * 4 * N * N * sizeof(double)));
+    CF_CUDA(cudaMalloc(&Fg, (size_t)7 * nmg * N * N * sizeof(double)));
+    if ((rc = alloc(&sh->F0g, (size_t)4 * nmg * N * N))) return rc;
+    k_spin_legendre<<<(N * nmg + 63) / 64, 64>>>(Pg, tg, N, Lrows);
+    for (int d = 0; d < 4; ++d) {
+      const int cut = L + d < N - 1 ? L + d : N - 1;
+      k_filter_qr<<<dim3(nmg, 7), 128>>>(Pg, Fg, sg, N, Lrows, cut);
+      // the n = 0 matrices
+      CF_CUDA(cudaMemcpyAsync(sh->F0g + (size_t)d * nmg * N * N, Fg + (size_t)3 * nmg * N * N,
+                              (size_t)nmg * N * N * sizeof(double), cudaMemcpyDeviceToDevice));
+    }
+    CF_CUDA(cudaGetLastError());
+    CF_CUDA(cudaDeviceSynchronize());
+    cudaFree(Pg);
+    cudaFree(tg);
+    cudaFree(sg);
+    cudaFree(Fg);
+  }
+
   // split-precision digits of every operator (used by the mixed path)
   if (sh->d.precision == CFFYN_MIXED) {
     if ((rc = build_tc(sh->tDr, sh->Dr, n_r, n_r, n_r, B))) return rc;
@@ -462,6 +488,11 @@ int build_operators(cffyn_shell* sh) {
       if ((rc = build_tc(sh->tFC[s], sh->FprojC + (size_t)s * nm * N * 2 * N, N, 2 * N, 2 * N, B, nm,
                          (size_t)N * 2 * N)))
         return rc;
+    if (sh->F0g)
+      for (int d = 0; d < 4; ++d)
+        if ((rc = build_tc(sh->tF0g[d], sh->F0g + (size_t)d * (Lrows + 1) * N * N, N, N, N, B, Lrows + 1,
+                           (size_t)N * N)))
+          return rc;
     CF_CUDA(cudaDeviceSynchronize());
   }
   return CFFYN_OK;
