@@ -188,7 +188,7 @@ def _pointwise_bytes(w, phase):
     P8 = n_r * N * J * 8.0
     vals = {"rhs_gamma": 96, "rhs_quad": 100, "rhs_pp": 240, "decompose": 2 * nv,
             "reconstruct": 4.5 * nv,
-            "field_exp": nv * (1 + 2 * (2 * L + 1) / J + 1) / 4}[phase]
+            "field_exp": nv}[phase]
     return vals * P8
 
 

@@ -32,10 +32,10 @@ int op_deriv_theta(const cffyn_shell*, const double*, double*, int, bool, cudaSt
 int op_deriv_phi(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
 int op_deriv_theta_phi(const cffyn_shell*, const double*, double*, double*, int, bool, cudaStream_t);
 int op_dft_fwd(const cffyn_shell*, const double*, double*, int, cudaStream_t, int);
-int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t, int);
-int op_project_scalar(const cffyn_shell*, const double*, double*, cudaStream_t);
+int op_dft_inv(const cffyn_shell*, const double*, double*, int, cudaStream_t, int, int);
+int op_project_scalar(const cffyn_shell*, const double*, double*, cudaStream_t, int);
 int op_project(const cffyn_shell*, const double*, double*, const int*, int, const int* const[3],
-               const int[3], cudaStream_t);
+               const int[3], cudaStream_t, int);
 int op_prepare(const cffyn_shell*, const double*, bool, int, long long, int, cudaStream_t);
 // setup.cu
 int build_operators(cffyn_shell*);
@@ -129,22 +129,23 @@ int derivs_spherical(cffyn_shell* sh, const double* u, double* D, int nf, bool i
 // Y / Yg: the Cartesian fields themselves, each with F^0_m (Sec. 3.5).
 bool yn_filter(const cffyn_shell* sh) { return sh->d.filter_kind == CFFYN_FILTER_YN; }
 
+// One exponent scan of the filter's input; the coefficients and the projected
+// coefficients take bounds from it (exponent + the operators' gains) instead
+// of scans of their own.
 int filter_spin_slots(cffyn_shell* sh, double* spin, cudaStream_t st) {
   const size_t nvP = (size_t)sh->nv * sh->P;
   int rc;
   double* C = sh->D;
   double* C2 = sh->D + nvP;
-  const long long lc = (long long)sh->R * sh->N * sh->n_r;  // coefficient values per function
   const int pairing = yn_filter(sh) ? 1 : 0;
+  const int e1 = sh->gain_dft, e2 = sh->gain_dft + sh->gain_proj;
   if ((rc = op_prepare(sh, spin, true, sh->nv, (long long)sh->P, pairing, st))) return rc;
   if ((rc = op_dft_fwd(sh, spin, C, sh->nv, st, pairing))) return rc;
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
-  if ((rc = op_prepare(sh, C, true, sh->nv, lc, pairing, st))) return rc;
-  if ((rc = yn_filter(sh) ? op_project(sh, C, C2, slots_r0(sh), sh->nR0, cl, sh->nC, st)
-                          : op_project_scalar(sh, C, C2, st)))
+  if ((rc = yn_filter(sh) ? op_project(sh, C, C2, slots_r0(sh), sh->nR0, cl, sh->nC, st, e1)
+                          : op_project_scalar(sh, C, C2, st, e1)))
     return rc;
-  if ((rc = op_prepare(sh, C2, true, sh->nv, lc, pairing, st))) return rc;
-  if ((rc = op_dft_inv(sh, C2, spin, sh->nv, st, pairing))) return rc;
+  if ((rc = op_dft_inv(sh, C2, spin, sh->nv, st, pairing, e2))) return rc;
   return CFFYN_OK;
 }
 
@@ -485,7 +486,6 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
   const long long P = (long long)sh->P;
   const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
-  const long long lc = (long long)sh->R * sh->N * sh->n_r;  // coefficient values per function
   int rc;
   auto prep = [&](const double* in, bool pairs, long long len, int pairing) {
     return run(10, [&] { return op_prepare(sh, in, pairs, sh->nv, len, pairing, st); });
@@ -494,18 +494,19 @@ static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st,
   // spin slots for Yn, the Cartesian fields for Y / Yg
   const bool yn = yn_filter(sh);
   const int pairing = yn ? 1 : 0;
+  // one exponent scan per filter: the coefficients and the projected ones
+  // take bounds (the scan's exponents + the operators' gains)
+  const int e1 = sh->gain_dft, e2 = sh->gain_dft + sh->gain_proj;
   auto filter = [&](double* spin) -> int {
     int r;
     if ((r = prep(spin, true, P, pairing))) return r;
     if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st, pairing); }))) return r;
-    if ((r = prep(sh->D, true, lc, pairing))) return r;
     if ((r = run(7, [&] {
-           return yn ? op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st)
-                     : op_project_scalar(sh, sh->D, sh->D + nvP, st);
+           return yn ? op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st, e1)
+                     : op_project_scalar(sh, sh->D, sh->D + nvP, st, e1);
          })))
       return r;
-    if ((r = prep(sh->D + nvP, true, lc, pairing))) return r;
-    return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st, pairing); });
+    return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st, pairing, e2); });
   };
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   for (int s = 0; s < 4; ++s) {

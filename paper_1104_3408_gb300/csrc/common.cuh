@@ -94,6 +94,11 @@ struct cffyn_shell {
   // list of every field) in yslots, ny[d] entries each
   int* yslots = nullptr;
   int ny[4] = {0, 0, 0, 0};
+  // exponent gains of the filter's operators: ceil(log2) of the largest row
+  // sum of |entries| of the phi analysis and of the projection matrices, so
+  // that |coefficients| < 2^(E_input + gain_dft) and |projected| <
+  // 2^(E_input + gain_dft + gain_proj) bound the next operators' inputs
+  int gain_dft = 1, gain_proj = 0;
 
   // gauge
   double* H = nullptr;    // [4][P]

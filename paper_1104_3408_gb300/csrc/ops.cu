@@ -438,6 +438,7 @@ struct TcBatch {
   TcOp W[kMaxBatch];
   long long tiles[kMaxBatch];  // column tiles of each class
   int nclass, nm;
+  int eoff;  // added to every column exponent: a bound from an earlier scan times the operator gain
 };
 
 template <int ROWS>
@@ -568,7 +569,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
   const ColDesc col = make_col(a, tile * kTcCols + ctile);
   int ce = exps[col.fld];
   if (pairing && col.fld >= kPairedFrom) ce = max(ce, exps[col.fld ^ 1]);
-  const int E = ce - 1022;
+  const int E = ce - 1022 + B.eoff;
   if (tid < ROWS) rowF[tid] = pow2f(W.rowexp[grp * ROWS + tid]);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -768,7 +769,7 @@ static int launch_batch(const cffyn_shell* sh, const TcBatch& b, cudaStream_t st
 // exponents of the input at exps (op_prepare fills sh->exps); in_pairs: the
 // input is pair-stored.  Mixed-path outputs are pair-stored.
 static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const TcOp* Wt, dim3 extra,
-                  cudaStream_t st, int pairing, bool in_pairs, const int* exps = nullptr) {
+                  cudaStream_t st, int pairing, bool in_pairs, const int* exps = nullptr, int eoff = 0) {
   if (a.g.ncols <= 0) return CFFYN_OK;
   if (sh->d.precision == CFFYN_FP64 || Wt == nullptr) {
     unsigned gx = (unsigned)((a.g.ncols + F64_QT - 1) / F64_QT);
@@ -786,6 +787,7 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
   b.tiles[0] = (a.g.ncols + kTcCols - 1) / kTcCols;
   b.nclass = 1;
   b.nm = (int)extra.y;
+  b.eoff = eoff;
   return launch_batch(sh, b, st, pairing, in_pairs, exps ? exps : sh->exps);
 }
 
@@ -900,7 +902,7 @@ int op_deriv_theta_phi(const cffyn_shell* sh, const double* in, double* out_th, 
 
 static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb, int K, int P,
                    long long in_bs, long long out_bs, const double* W, const TcOp* Wt, cudaStream_t st,
-                   int pairing) {
+                   int pairing, int eoff = 0) {
   OpArgs a = base_args(sh);
   a.kind = OP_ROWS;
   a.in = in;
@@ -912,7 +914,7 @@ static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb,
   a.g.P = a.g.P0 = P;
   a.g.in_rs = a.g.out_rs = a.Q;
   a.g.ncols = (long long)nb * a.Q;
-  return launch(sh, a, W, Wt, dim3(1, 1), st, pairing, true);
+  return launch(sh, a, W, Wt, dim3(1, 1), st, pairing, true, nullptr, eoff);
 }
 
 // phi analysis: S[f][j][i][k] -> C[f][row][i][k] (pair-stored input on the
@@ -924,17 +926,19 @@ int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cud
                  &sh->tFan, st, pairing);
 }
 
-int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st, int pairing) {
+// eoff: see TcBatch (the coefficients' exponents are bounds, not a scan)
+int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st, int pairing,
+               int eoff) {
   long long Q = (long long)sh->N * sh->n_r;
   return op_rows(sh, in, out, nf, sh->R, sh->J, (long long)sh->R * Q, (long long)sh->J * Q, sh->Fsy,
-                 &sh->tFsy, st, pairing);
+                 &sh->tFsy, st, pairing, eoff);
 }
 
 // Component-wise filters (Sec. 3.5): every field's coefficients projected
 // with F^0_m, C -> C2: the Y filter at the retained degree L (one class), the
 // graded Yg filter at L + d for the fields of spatial degree d (eq. nfofmu;
 // one class per d), m = 0..Lrows; one launch on the mixed path.
-int op_project_scalar(const cffyn_shell* sh, const double* C, double* C2, cudaStream_t st) {
+int op_project_scalar(const cffyn_shell* sh, const double* C, double* C2, cudaStream_t st, int eoff) {
   const int N = sh->N;
   const bool graded = sh->d.filter_kind == CFFYN_FILTER_YG;
   const int nm = sh->Lrows + 1;
@@ -970,6 +974,7 @@ int op_project_scalar(const cffyn_shell* sh, const double* C, double* C2, cudaSt
     }
     bt.nclass = ncls;
     bt.nm = nm;
+    bt.eoff = eoff;
     return launch_batch(sh, bt, st, 0, true, sh->exps);
   }
   for (int c = 0; c < ncls; ++c) {
@@ -983,7 +988,7 @@ int op_project_scalar(const cffyn_shell* sh, const double* C, double* C2, cudaSt
 // class and every m = 0..L in one launch on the mixed path, one launch per
 // class on the FP64 path.
 int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* slots_r0, int n_r0,
-               const int* const slots_c[3], const int n_c[3], cudaStream_t st) {
+               const int* const slots_c[3], const int n_c[3], cudaStream_t st, int eoff) {
   const int N = sh->N;
   const int nm = sh->L + 1;
   OpArgs cls[4];
@@ -1036,6 +1041,7 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     }
     bt.nclass = ncls;
     bt.nm = nm;
+    bt.eoff = eoff;
     return launch_batch(sh, bt, st, 1, true, sh->exps);
   }
   for (int c = 0; c < ncls; ++c) {

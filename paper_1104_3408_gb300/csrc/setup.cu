@@ -15,6 +15,7 @@
 //                             mma.m16n8k16 A-fragment order.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -337,6 +338,17 @@ __global__ void k_slice_rows(const double* A, int P, int K, int ld, int* rowexp)
   rowexp[p] = (E == -2000) ? 0 : E;
 }
 
+// Largest row sum of |entries| over nmat row-major matrices of rows x cols
+// (contiguous), as the bit pattern of a non-negative double in *out.
+__global__ void k_max_row_sum(const double* A, int rows, int cols, long long nmat, unsigned long long* out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nmat * rows) return;
+  const double* a = A + t * cols;
+  double s = 0.0;
+  for (int k = 0; k < cols; ++k) s += fabs(a[k]);
+  atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
 // One thread per BF16 value of the tcgen05 operator layout (see TcOp).
 __global__ void k_tc_pack(const double* A, int P, int K, int ld, const int* rowexp, unsigned short* w,
                           int rows, int ksteps, size_t total) {
@@ -474,6 +486,34 @@ int build_operators(cffyn_shell* sh) {
     cudaFree(tg);
     cudaFree(sg);
     cudaFree(Fg);
+  }
+
+  // exponent gains of the filter operators (see cffyn_shell::gain_dft)
+  {
+    unsigned long long* g = nullptr;
+    CF_CUDA(cudaMalloc(&g, 2 * sizeof(unsigned long long)));
+    CF_CUDA(cudaMemset(g, 0, 2 * sizeof(unsigned long long)));
+    auto rows = [&](const double* A, int r, int c, long long n, unsigned long long* o) {
+      const long long t = n * r;
+      k_max_row_sum<<<(unsigned)((t + 127) / 128), 128>>>(A, r, c, n, o);
+    };
+    rows(sh->Fan, R, J, 1, g);
+    rows(sh->Fproj0, N, N, nm, g + 1);
+    rows(sh->FprojC, N, 2 * N, 3LL * nm, g + 1);
+    if (sh->F0g) rows(sh->F0g, N, N, 4LL * (Lrows + 1), g + 1);
+    unsigned long long h[2];
+    CF_CUDA(cudaMemcpy(h, g, sizeof(h), cudaMemcpyDeviceToHost));
+    cudaFree(g);
+    double mx[2];
+    memcpy(mx, h, sizeof(h));
+    int e[2];
+    for (int i = 0; i < 2; ++i) {
+      frexp(mx[i], &e[i]);  // mx < 2^e
+      if (!(mx[i] > 0.0)) e[i] = 0;
+      if (e[i] < 0) e[i] = 0;
+    }
+    sh->gain_dft = e[0];
+    sh->gain_proj = e[1];
   }
 
   // split-precision digits of every operator (used by the mixed path)

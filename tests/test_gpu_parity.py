@@ -197,10 +197,10 @@ def test_trace_and_profile_report_every_kernel_group(cf):
     ms, launches, steps = sh.get_trace()
     assert steps == 3
     assert all(v > 0 for v in ms.values())
-    # 4 stages; the mixed path scans the field exponents of the input of each
-    # of the four operator groups of a stage
+    # 4 stages; the mixed path scans the field exponents of each stage's input
+    # and of its filter's input (the filter's later operators take bounds)
     assert launches["d_theta_phi"] == 4 and launches["rhs_pp"] == 4
-    assert launches["project"] == 4 and launches["d_r"] == 4 and launches["field_exp"] == 16
+    assert launches["project"] == 4 and launches["d_r"] == 4 and launches["field_exp"] == 8
     # tracing does not change the result
     v = dev(u0)
     w = dev(u0)
