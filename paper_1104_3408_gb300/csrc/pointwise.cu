@@ -562,7 +562,7 @@ __device__ __forceinline__ void reconstruct_update(Scratch<T> sc, const double* 
 }
 
 template <class T, bool FD, int KIND>
-__global__ void __launch_bounds__(128, 5) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
+__global__ void __launch_bounds__(128, 6) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
                                                      Geo geo, int mode, double* __restrict__ u,
                                                      double* __restrict__ U, double* __restrict__ kacc,
                                                      double* __restrict__ uf, double dt,
