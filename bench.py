@@ -163,7 +163,9 @@ FAMILIES = {
     "k_decompose": ["decompose"],
     "k_field_exp": ["field_exp"],
 }
-PAIRS = 26  # BF16 digit-pair products per operator product (i + j <= 6 of 6 x 6)
+# BF16 digit-pair products per operator product: i + j <= 6 of 6 x 6 digits
+# for the derivatives, i + j <= 5 for the filter's DFTs and projections
+PAIRS = {"d_r": 26, "d_theta_phi": 26, "dft_fwd": 21, "project": 21, "dft_inv": 21}
 # DRAM bytes per step of all k_op_tc launches, from the ncu launch list of the
 # same command (profiles/launch_list_ks_33x48x96_mixed.md); None where no
 # capture of the current kernel exists.
@@ -205,20 +207,20 @@ def _roofline(w, per_step, launches, hbm, bf16s, peak_kind):
     nl = sum(launches.get(ph, 0) for ph in FAMILIES[dom])
     if dom == "k_op_tc":
         fl = sum(4 * _op_flops(w, ph) for ph in FAMILIES[dom])  # 4 stages
-        achieved = PAIRS * fl / t / 1e12
+        achieved = sum(PAIRS[ph] * 4 * _op_flops(w, ph) for ph in FAMILIES[dom]) / t / 1e12
         byts = 4 * 8.0 * w["n_fields"] * w["n_r"] * w["n_theta"] * w["n_phi"] * (
             6 + 2 + 4 * (2 * w["L"] + 1) / w["n_phi"])
         per_launch = {}
         for ph in FAMILIES[dom]:
             tl = per_step[ph] * 1e-3
             per_launch[ph] = {"ms_per_step": per_step[ph], "launches_per_step": launches[ph],
-                              "tensor_frac": PAIRS * 4 * _op_flops(w, ph) / tl / 1e12 / bf16s}
+                              "tensor_frac": PAIRS[ph] * 4 * _op_flops(w, ph) / tl / 1e12 / bf16s}
         return {"bound": "tensor", "kernel": "k_op_tc (all operator launches of the step)",
                 "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
                 "traffic": OP_TRAFFIC_PER_STEP.get(w["name"]),
                 "traffic_scope": "DRAM bytes per step, all k_op_tc launches (ncu launch list)",
                 "peak_source": f"bf16_tflops_sustained ({peak_kind})",
-                "work": "26 BF16 digit-pair products x method FP64 operator flops "
+                "work": "26 (derivatives) or 21 (filter) BF16 digit-pair products x method FP64 operator flops "
                         "(2n_r + 16N + 2(L+1) per pt-field per substep)",
                 "fp64_equiv_tflops": fl / t / 1e12,
                 "hbm_view": {"algorithmic_GBps": byts / t / 1e9, "frac": byts / t / 1e9 / hbm},
@@ -538,9 +540,10 @@ def run_batch(args, rank, local_rank, ws, dist):
     fl = 0.0
     for i in mine:
         d = descs[i]
-        per = 2 * d["n_r"] + 16 * d["n_theta"] + 2 * (d["L"] + 1)
-        fl += 4.0 * per * _shell_units(d)
-    achieved = PAIRS * fl * args.steps / (t_ms * 1e-3) / 1e12
+        deriv = 2 * d["n_r"] + 8 * d["n_theta"]
+        filt = 8 * d["n_theta"] + 2 * (d["L"] + 1)
+        fl += 4.0 * (26 * deriv + 21 * filt) * _shell_units(d)
+    achieved = fl * args.steps / (t_ms * 1e-3) / 1e12
     roof = {"bound": "tensor", "kernel": "k_op_tc (operator work over the whole batch step time)",
             "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
             "traffic": None, "peak_source": f"bf16_tflops_sustained ({peak_kind})",

@@ -411,11 +411,18 @@ __global__ void __launch_bounds__(kExpThreads) k_field_exp(const long long* __re
 //     words prefetched one k-step ahead) into the stage, then arrive on its
 //     `xfull` barrier; after the last k-step they run the epilogue;
 //   one MMA warp: bulk-copies (TMA) the operator's sixteen slices of each
-//     k-step (see TcOp) a stage ahead and, once a stage is full, issues the 26
+//     k-step (see TcOp) a stage ahead and, once a stage is full, issues the
 //     digit-pair MMAs into five FP32 accumulators in TMEM and commits them to
 //     the stage's `empty` barrier:
 //   acc_d = sum_{i+j=d} W_i X_j                            d = 0..3
 //   acc_4 = sum_{i+j=4} W_i X_j + 2^-8 sum_{i+j=5} W_i X_j + 2^-16 sum_{i+j=6} W_i X_j
+// The digit-sum <= 4 pairs of one input slice X_j go out as one MMA of up to
+// 256 rows over adjacent operator slices into adjacent accumulators: the
+// MMAs' shared-memory operand reads are the kernel's limit (a 128 x 96 x 16
+// MMA reads 7 KB for 196 608 MACs), and the wider MMAs re-read X_j less.
+// The digit-sum-6 pairs are issued for the derivatives only (TcBatch::sum6);
+// the filter's DFTs and projections stop at digit sum 5 (21 pairs) and copy
+// eleven operator slices per k-step.
 // acc_0..acc_3 are exact integers (below 4 * 192 * 2^14 < 2^24).  acc_4 is
 // not exact; its rounding is below 2^-24 of a term of weight 256^-4 relative
 // to the leading one, about 2^-56 of the result's scale, at the level of the
@@ -439,6 +446,7 @@ struct TcBatch {
   long long tiles[kMaxBatch];  // column tiles of each class
   int nclass, nm;
   int eoff;  // added to every column exponent: a bound from an earlier scan times the operator gain
+  int sum6;  // issue the digit-sum-6 pairs (derivatives); the filter's operators stop at digit sum 5
 };
 
 template <int ROWS>
@@ -644,10 +652,13 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     // MMA thread
     const unsigned char* wsrc =
         reinterpret_cast<const unsigned char*>(W.w) + (size_t)grp * ksteps * C::kWBytes;
+    // the operator slices of a k-step; without the digit-sum-6 pairs the
+    // last five (digits 1..5 times 2^-16) stay in global memory
+    const uint32_t wcopy = B.sum6 ? C::kWBytes : (kTcWSlices - 5) * C::kWSlice;
     const uint32_t sbase = tc::smem_addr(smtc);
     for (int ks = 0; ks < S && ks < ksteps; ++ks) {
-      tc::bar_expect_tx(&wfull[ks], C::kWBytes);
-      tc::bulk_g2s(smtc + ks * C::kStage + kTcXBytes, wsrc + (size_t)ks * C::kWBytes, C::kWBytes, &wfull[ks]);
+      tc::bar_expect_tx(&wfull[ks], wcopy);
+      tc::bulk_g2s(smtc + ks * C::kStage + kTcXBytes, wsrc + (size_t)ks * C::kWBytes, wcopy, &wfull[ks]);
     }
     int copied = S < ksteps ? S : ksteps;  // operator k-steps whose copy has been issued
     for (int ks = 0; ks < ksteps && ok; ++ks) {
@@ -660,23 +671,33 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
       const uint64_t dw = tc::desc_kmajor(xa + kTcXBytes, 128, 256);
       constexpr uint32_t ID = tc::idesc_bf16_f32(kTcCols, ROWS);
       constexpr uint64_t XS = kTcXSlice >> 4, WS = C::kWSlice >> 4;  // slice strides, descriptor units
+      // digit-sum <= 4 pairs of input slice j: the operator slices 0..4-j
+      // are adjacent in shared memory and their accumulators acc_j..acc_4
+      // adjacent in TMEM, so up to 256 / ROWS of them go into one MMA of
+      // N = n ROWS (fewer re-reads of the input slice)
+      constexpr int kMerge = 256 / ROWS;
 #pragma unroll
-      for (int d = 0; d < 5; ++d)
+      for (int j = 0; j < 5; ++j)
 #pragma unroll
-        for (int i = 0; i <= d; ++i)
-          tc::mma(tm + d * ROWS, dx + (d - i) * XS, dw + i * WS, ID, (ks > 0 || i > 0) ? 1u : 0u);
+        for (int i = 0; i + j <= 4; i += kMerge) {
+          const int n = (5 - j - i) < kMerge ? (5 - j - i) : kMerge;
+          const uint32_t idn = tc::idesc_bf16_f32(kTcCols, n * ROWS);
+          tc::mma(tm + (i + j) * ROWS, dx + j * XS, dw + i * WS, idn, (ks > 0 || j > 0) ? 1u : 0u);
+        }
 #pragma unroll
       for (int i = 0; i < 6; ++i) tc::mma(tm + 4 * ROWS, dx + (5 - i) * XS, dw + (5 + i) * WS, ID, 1u);
+      if (B.sum6) {
 #pragma unroll
-      for (int i = 1; i < 6; ++i) tc::mma(tm + 4 * ROWS, dx + (6 - i) * XS, dw + (10 + i) * WS, ID, 1u);
+        for (int i = 1; i < 6; ++i) tc::mma(tm + 4 * ROWS, dx + (6 - i) * XS, dw + (10 + i) * WS, ID, 1u);
+      }
       tc::commit(&empty[s]);
       // refill the stage of k-step ks - 1 with the operator of k-step ks - 1 + S
       if (ks >= 1 && copied < ksteps) {
         const int sp = (ks - 1) % S;
         ok = tc::bar_wait(&empty[sp], ((ks - 1) / S) & 1, kTcWaitNs);
         if (!ok) break;
-        tc::bar_expect_tx(&wfull[sp], C::kWBytes);
-        tc::bulk_g2s(smtc + sp * C::kStage + kTcXBytes, wsrc + (size_t)copied * C::kWBytes, C::kWBytes,
+        tc::bar_expect_tx(&wfull[sp], wcopy);
+        tc::bulk_g2s(smtc + sp * C::kStage + kTcXBytes, wsrc + (size_t)copied * C::kWBytes, wcopy,
                      &wfull[sp]);
         ++copied;
       }
@@ -769,7 +790,8 @@ static int launch_batch(const cffyn_shell* sh, const TcBatch& b, cudaStream_t st
 // exponents of the input at exps (op_prepare fills sh->exps); in_pairs: the
 // input is pair-stored.  Mixed-path outputs are pair-stored.
 static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const TcOp* Wt, dim3 extra,
-                  cudaStream_t st, int pairing, bool in_pairs, const int* exps = nullptr, int eoff = 0) {
+                  cudaStream_t st, int pairing, bool in_pairs, const int* exps = nullptr, int eoff = 0,
+                  int sum6 = 1) {
   if (a.g.ncols <= 0) return CFFYN_OK;
   if (sh->d.precision == CFFYN_FP64 || Wt == nullptr) {
     unsigned gx = (unsigned)((a.g.ncols + F64_QT - 1) / F64_QT);
@@ -788,6 +810,7 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
   b.nclass = 1;
   b.nm = (int)extra.y;
   b.eoff = eoff;
+  b.sum6 = sum6;
   return launch_batch(sh, b, st, pairing, in_pairs, exps ? exps : sh->exps);
 }
 
@@ -897,6 +920,7 @@ int op_deriv_theta_phi(const cffyn_shell* sh, const double* in, double* out_th, 
   for (int c = 0; c < 2; ++c) b.tiles[c] = (b.a[c].g.ncols + kTcCols - 1) / kTcCols;
   b.nclass = 2;
   b.nm = 1;
+  b.sum6 = 1;
   return launch_batch(sh, b, st, 0, in_pairs, sh->exps);
 }
 
@@ -914,7 +938,9 @@ static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb,
   a.g.P = a.g.P0 = P;
   a.g.in_rs = a.g.out_rs = a.Q;
   a.g.ncols = (long long)nb * a.Q;
-  return launch(sh, a, W, Wt, dim3(1, 1), st, pairing, true, nullptr, eoff);
+  // the phi DFTs of the filter: digit sums up to 5 suffice (filter errors
+  // stay near 1e-12 relative)
+  return launch(sh, a, W, Wt, dim3(1, 1), st, pairing, true, nullptr, eoff, 0);
 }
 
 // phi analysis: S[f][j][i][k] -> C[f][row][i][k] (pair-stored input on the
@@ -975,6 +1001,7 @@ int op_project_scalar(const cffyn_shell* sh, const double* C, double* C2, cudaSt
     bt.nclass = ncls;
     bt.nm = nm;
     bt.eoff = eoff;
+    bt.sum6 = 0;
     return launch_batch(sh, bt, st, 0, true, sh->exps);
   }
   for (int c = 0; c < ncls; ++c) {
@@ -1042,6 +1069,7 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     bt.nclass = ncls;
     bt.nm = nm;
     bt.eoff = eoff;
+    bt.sum6 = 0;
     return launch_batch(sh, bt, st, 1, true, sh->exps);
   }
   for (int c = 0; c < ncls; ++c) {

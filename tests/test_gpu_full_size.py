@@ -124,9 +124,12 @@ def test_full_size_steps_mixed_vs_fp64_gpu(cf, c, steps):
     assert np.abs(a - b).max() / np.abs(b).max() < 1e-8
     # the motion of the fields is resolved (they moved by 1e-8..1e-5)
     assert np.abs(a[:50] - b[:50]).max() / np.abs(b[:50] - u0[:50]).max() < 1e-3
-    # constraint norms: RMS of O(1) quantities computed from fields that agree
-    # to ~1e-13, so they agree to a small absolute amount
-    assert abs(ca[0] - cb[0]) <= 1e-6 * cb[0] + 1e-12 and abs(ca[1] - cb[1]) <= 1e-6 * cb[1] + 1e-12
+    # constraint norms: C_iab = d_i g_ab - Phi_iab takes the shell's own
+    # derivatives of g, whose mixed-path error is bounded by the derivative
+    # target (1e-10 relative, |d g| = O(1)); C_a = H_a + Gamma_a has no
+    # derivatives and follows the fields (~1e-13)
+    assert abs(ca[0] - cb[0]) <= 1e-10
+    assert abs(ca[1] - cb[1]) <= 1e-6 * cb[1] + 1e-12
 
 
 def test_hundred_steps_mixed_vs_oracle(cf):
