@@ -169,7 +169,7 @@ PAIRS = {"d_r": 26, "d_theta_phi": 26, "dft_fwd": 21, "project": 21, "dft_inv": 
 # DRAM bytes per step of all k_op_tc launches, from the ncu launch list of the
 # same command (profiles/launch_list_ks_33x48x96_mixed.md); None where no
 # capture of the current kernel exists.
-OP_TRAFFIC_PER_STEP = {"ks_33x48x96": 2.03e9}
+OP_TRAFFIC_PER_STEP = {"ks_33x48x96": 1.99e9}
 
 
 def _op_flops(w, phase):
