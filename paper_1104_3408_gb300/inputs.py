@@ -24,6 +24,10 @@ Recipes
     random centre e) times a Chebyshev series in r with N(0,1) coefficients
     scaled by 10^(-q/4).  Cartesian components of such fields carry every
     spin weight; their angular spectra decay exponentially.
+``kerr_schild_pi_from_phi``
+    Pi_ab of unperturbed Kerr-Schild data from a given Phi_iab (the paper's
+    R10 runs take Phi as the numerical derivative of g_ab), with the
+    closed-form lapse and shift of App. A.3.
 ``shell_batch``
     The uneven-shell batch: n_theta from {16, 24, 32, 48}, n_phi = 2 n_theta,
     n_r from {17, 25, 33}, amplitude log-uniform in [1e-6, 1e-3].
@@ -123,6 +127,22 @@ def kerr_schild_state(n_r, n_theta, n_phi, r_in=1.8, r_out=11.0, n_fields=50,
         for i in range(3):
             u[20 + 10 * i + s] = dg[i, a, b]
     return np.ascontiguousarray(u)
+
+
+def kerr_schild_pi_from_phi(Phi, n_r, n_theta, n_phi, r_in=1.8, r_out=11.0, mass=1.0):
+    """Pi_ab = beta^k Phi_kab / alpha for unperturbed Kerr-Schild data
+    (eq. defPiPhi with d_t g_ab = 0), with the closed-form lapse
+    alpha = (1 + f)^(-1/2) and shift beta^k = f/(1 + f) x^k/r of App. A.3.
+
+    Phi: [3, 10, n_phi, n_theta, n_r] in the symmetric-pair order of
+    SYM_PAIRS, any approximation of d_k g_ab (the paper's runs take the
+    numerical derivative of eq. KSmetric).  Returns Pi[10, n_phi, n_theta, n_r].
+    """
+    X, R = _cartesian(n_r, n_theta, n_phi, r_in, r_out)
+    f = 2.0 * mass / R
+    alpha = 1.0 / np.sqrt(1.0 + f)
+    beta = X / R[None] * (f / (1.0 + f))[None]
+    return np.ascontiguousarray(np.einsum("k...,kf...->f...", beta, np.asarray(Phi)) / alpha[None])
 
 
 def band_limited_fields(n_r, n_theta, n_phi, r_in=1.8, r_out=11.0, n_fields=50, seed=0,
