@@ -88,7 +88,10 @@ def test_initial_truncation_error_converges_with_n_r(r10, prec):
         ref.init_gauge_from_state(u0)
         want.append(np.abs(ref.rhs(u0)).max())
         scale = np.abs(ref.derivs(u0)).max()
-        tol = 1e-12 if prec == 0 else 1e-10
+        # near the inner sphere the right-hand side sums derivative terms
+        # weighted by metric factors up to 1 + 2M/r_in = 2.1, so FP64
+        # summation order alone moves it by a few 1e-12 of max |d_k u|
+        tol = 4e-12 if prec == 0 else 1e-10
         assert abs(got[-1] - want[-1]) < tol * scale, (n_r, got[-1], want[-1])
     assert all(a > 30.0 * b for a, b in zip(got, got[1:])), got
 
