@@ -42,6 +42,9 @@ def _args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--filter", default="yn", choices=["yn", "y", "yg"],
                     help="filter of the single-shell workloads: tensor Yn (default), scalar Y, graded Yg")
+    ap.add_argument("--sweep", default=None,
+                    help="comma list of n: time the Cartesian derivatives of 50 fields on n x n x 2n shells "
+                         "by the mixed and FP64 matrix paths and the FFT path, print one JSON line and exit")
     ap.add_argument("--profile-step", action="store_true",
                     help="run one eager RK4 step with per-group device times and print them "
                          "(the fixed launch sequence used for profiler captures)")
@@ -672,10 +675,76 @@ def run_profile_step(args):
             "launches": {k: n for k, (t, n) in prof.items()}}
 
 
+def run_derivs_sweep(args):
+    """Cartesian derivatives of 50 fields on shells n_r x n x 2n (n_r = n) by
+    three methods: the split-precision matrices on the tensor cores (MIXED),
+    the FP64 matrices, and FP64 FFTs (cuFFT; cffyn_derivs_fft): the GB300
+    analogue of the paper's matrix-vs-FFT comparison (Sec. 5, Fig. mmfft), for
+    the whole derivative rather than one transform.  CUDA events on the
+    launching stream, median of 5 calls after 2 warm-up calls, L2 flushed
+    before each call."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3408_gb300 import cffyn, inputs
+
+    st = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    nv = 50
+    rows = []
+    for n in [int(x) for x in args.sweep.split(",")]:
+        base = inputs.band_limited_fields(n, n, 2 * n, 1.8, 11.0, n_fields=5, seed=n)
+        u = torch.from_numpy(np.ascontiguousarray(np.tile(base, (nv // 5, 1, 1, 1)))).cuda()
+        shells = {"matrix_mixed": cffyn.Shell(n, n, 2 * n, 1.8, 11.0, n - 2, precision=cffyn.MIXED),
+                  "matrix_fp64": cffyn.Shell(n, n, 2 * n, 1.8, 11.0, n - 2, precision=cffyn.FP64)}
+        calls = {"matrix_mixed": lambda o: shells["matrix_mixed"].derivs(u, o),
+                 "matrix_fp64": lambda o: shells["matrix_fp64"].derivs(u, o),
+                 "fft_fp64": lambda o: shells["matrix_fp64"].derivs_fft(u, o)}
+        outs, ms = {}, {}
+        for name, fn in calls.items():
+            o = torch.empty((3,) + tuple(u.shape), dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                fn(o)
+            times = []
+            for _ in range(5):
+                flush.fill_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                fn(o)
+                b.record(st)
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+            ms[name] = statistics.median(times)
+            outs[name] = o
+        ref = outs["matrix_fp64"]
+        scale = float(ref.abs().max())
+        units = float(n * n * 2 * n * nv)
+        rows.append({"n_r": n, "n_theta": n, "n_phi": 2 * n, "ms": ms,
+                     "pt_field_per_s": {k: units / (v * 1e-3) for k, v in ms.items()},
+                     "rel_diff_vs_matrix_fp64": {k: float((outs[k] - ref).abs().max()) / scale
+                                                 for k in ("matrix_mixed", "fft_fp64")}})
+        for sh in shells.values():
+            sh.destroy()
+        del outs, u
+        torch.cuda.empty_cache()
+    return {"mode": "derivs_sweep", "fields": nv, "method_note":
+            "matrix_mixed: split-precision BF16 digit products on tcgen05 (k_op_tc); matrix_fp64: "
+            "FP64 matrices (k_op_fp64); fft_fp64: cuFFT D2Z/Z2D with the library's own extension, "
+            "recurrence and transpose kernels; all followed by the same chain-rule kernel",
+            "timing": "median of 5 calls after 2 warm-ups, CUDA events, L2 flushed before each call",
+            "rows": rows}
+
+
 def main():
     args = _args()
     if args.profile_step:
         print(json.dumps(run_profile_step(args)), flush=True)
+        return
+    if args.sweep:
+        print(json.dumps(run_derivs_sweep(args)), flush=True)
         return
     rank, local_rank, ws, dist = _dist()
     batch = "n_shells" in _workload(args.workload)

@@ -314,6 +314,28 @@ CFFYN_API int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launch
 CFFYN_API int cffyn_derivs_static(const cffyn_shell* sh, const double* u, int n_f, double* dxyz,
                                   void* stream);
 
+/* Cartesian derivatives of every field, like cffyn_derivs (same output
+ * layout and meaning), computed with fast Fourier transforms instead of the
+ * differentiation matrices: the alternative the paper weighs against the
+ * matrix method in Sec. 5 (Fig. mmfft).  FP64 on either precision path:
+ * Chebyshev coefficients by a real FFT of the even extension in r (DCT-I),
+ * the derivative's coefficients by the recurrence
+ * c_k b_k = b_{k+2} + 2 (k + 1) a_{k+1}, and an inverse FFT; the theta
+ * derivative over the double cover of Sec. 2.1 (2 n_theta points per line)
+ * and the phi derivative by FFTs with the Nyquist mode set to zero, as the
+ * matrices of eq. FD do.  Results agree with cffyn_derivs on an FP64 shell to
+ * rounding.  Uses cuFFT (library code) for the transforms and the shell's
+ * workspace for the spherical derivatives (like cffyn_derivs).
+ *
+ * The first call on a shell creates six cuFFT plans and allocates FFT scratch
+ * (cudaMalloc, about 4 x n_fields x P doubles, plus cuFFT's own work area):
+ * make it before any stream capture.  cffyn_destroy frees them.
+ * Errors: CFFYN_EINVAL for a NULL shell or NULL / unaligned arrays, no
+ * workspace, or a current device other than the shell's; CFFYN_ENOMEM or
+ * CFFYN_ECUDA if a plan, the scratch or a launch fails.  Asynchronous after
+ * the first call. */
+CFFYN_API int cffyn_derivs_fft(cffyn_shell* sh, const double* u, double* dxyz, void* stream);
+
 /* Message of the last failing call on this thread (never NULL). */
 CFFYN_API const char* cffyn_last_error(void);
 

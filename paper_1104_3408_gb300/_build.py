@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libcffyn.so")
-SOURCES = ["setup.cu", "ops.cu", "pointwise.cu", "rhs.cu", "api.cu", "static_scratch.cu", "batch.cu"]
+SOURCES = ["setup.cu", "ops.cu", "pointwise.cu", "rhs.cu", "api.cu", "static_scratch.cu", "batch.cu", "fft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-diag-suppress", "177"]
@@ -71,7 +71,12 @@ def build(force=False, verbose=False):
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
+    # cuFFT (the FFT derivative path) from the toolkit next to nvcc, found at run
+    # time through the rpath
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + [
+        "-L", cuda_lib, "-lcufft", "-Xlinker", "-rpath", "-Xlinker", cuda_lib,
+        "-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))

@@ -27,7 +27,7 @@ EXPORTED = [
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
     "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch",
-    "cffyn_workspace_size", "cffyn_attach_workspace",
+    "cffyn_workspace_size", "cffyn_attach_workspace", "cffyn_derivs_fft",
 ]
 PROFILE_PHASES = ["d_r", "d_theta_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
                   "dft_fwd", "project", "dft_inv", "reconstruct", "field_exp"]
@@ -73,6 +73,7 @@ def load(path=LIB_PATH):
         "cffyn_init_gauge_from_state": ([vp, dp, vp], i),
         "cffyn_derivs": ([vp, dp, dp, vp], i),
         "cffyn_derivs_static": ([vp, dp, i, dp, vp], i),
+        "cffyn_derivs_fft": ([vp, dp, dp, vp], i),
         "cffyn_rhs": ([vp, dp, dp, vp], i),
         "cffyn_filter": ([vp, dp, dp, vp], i),
         "cffyn_rk4_step": ([vp, dp, d, i, vp], i),
@@ -181,6 +182,12 @@ class Shell:
 
     def derivs(self, u, out, stream=None):
         _check(load().cffyn_derivs(self.h, _ptr(u, "u"), _ptr(out, "dxyz"), _stream(stream)))
+        return out
+
+    def derivs_fft(self, u, out, stream=None):
+        """Cartesian derivatives like derivs(), by FFTs (cuFFT, FP64); the
+        first call makes the plans and allocates their scratch."""
+        _check(load().cffyn_derivs_fft(self.h, _ptr(u, "u"), _ptr(out, "dxyz"), _stream(stream)))
         return out
 
     def derivs_static(self, u, n_f, out, stream=None):
@@ -297,6 +304,10 @@ def rk4_step(sh, u, dt=0.0, n_steps=1, stream=None):
 
 def derivs(sh, u, out, stream=None):
     return sh.derivs(u, out, stream)
+
+
+def derivs_fft(sh, u, out, stream=None):
+    return sh.derivs_fft(u, out, stream)
 
 
 def create_batch(shells):

@@ -170,6 +170,7 @@ void free_shell(cffyn_shell* sh) {
   if (sh->graph) cudaGraphExecDestroy(sh->graph);
   for (int i = 0; i < cffyn_shell::kMaxMarks; ++i)
     if (sh->marks[i]) cudaEventDestroy(sh->marks[i]);
+  fft_release(sh);
   delete sh;
 }
 

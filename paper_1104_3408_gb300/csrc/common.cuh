@@ -51,6 +51,7 @@ struct TcOp {
 };
 
 struct cffyn_shell_impl;
+struct FftPath;  // fft.cu: plans and scratch of cffyn_derivs_fft
 
 }  // namespace cffyn
 
@@ -120,6 +121,7 @@ struct cffyn_shell {
   double* Rsrc = nullptr;  // right-hand-side source terms [nv][P]
   int* exps = nullptr;     // per-field exponents of the next operator input (64 entries)
   double* red = nullptr;   // device reduction words (2 doubles)
+  cffyn::FftPath* fft = nullptr;  // FFT derivative path, made by its first call
   int* flag = nullptr;     // device non-finite flag
   int* flag_host = nullptr;  // pinned host copy of the flag
   int* slots = nullptr;    // device slot lists: R0 (nR0) | C1 (nC[0]) | C2 (nC[1]) | C3 (nC[2])
@@ -143,3 +145,8 @@ struct cffyn_shell {
   double trace_ms[kPhases] = {};
   long long trace_steps = 0;
 };
+
+namespace cffyn {
+// fft.cu: frees the FFT derivative path's plans and scratch (no-op without)
+void fft_release(cffyn_shell*);
+}  // namespace cffyn

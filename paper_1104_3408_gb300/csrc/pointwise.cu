@@ -751,6 +751,16 @@ int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, bool ou
   return CFFYN_OK;
 }
 
+// FP64 spherical derivatives D (not internal storage) -> FP64 Cartesian out,
+// on either path (the FFT derivative path writes FP64 into the workspace)
+int pw_cart_fp64(const cffyn_shell* sh, const double* D, double* out, int nf, cudaStream_t st) {
+  Geo g = geo_of(sh);
+  k_cart<false, false><<<blocks_for(g.P * nf, 256), 256, 0, st>>>(D, out, nf, g);
+  count_launch();
+  CF_CUDA(cudaGetLastError());
+  return CFFYN_OK;
+}
+
 // Table of the real triad rows at every (theta_i, phi_j) (set-up).
 int pw_triad_table(const cffyn_shell* sh) {
   Geo g = geo_of(sh);

@@ -182,7 +182,7 @@ def study_dtfac(a, emit):
         for prec in _precisions(a.precision):
             stable, unstable, runs = None, None, []
             for lam in ladder:
-                r = run_one(n_r, n_theta, a.t_end or 1000.0, courant=lam, precision=prec,
+                r = run_one(n_r, n_theta, a.t_end or 500.0, courant=lam, precision=prec,
                             sample_steps=10)
                 runs.append(dict(courant=lam, failed_at=r["failed_at"], t=r["t"],
                                  rhs_gtt_final=r["rhs_gtt_final"], seconds=r["seconds"]))
@@ -193,7 +193,7 @@ def study_dtfac(a, emit):
                     break                      # larger factors fail sooner
             emit("dtfac", dict(grid=f"{n_r}x{n_theta}x{2 * n_theta}",
                                precision="fp64" if prec == cffyn.FP64 else "mixed",
-                               t_end=a.t_end or 1000.0, largest_stable=stable,
+                               t_end=a.t_end or 500.0, largest_stable=stable,
                                smallest_unstable=unstable, paper_lambda_max=lam_paper, runs=runs))
 
 

@@ -104,3 +104,22 @@ def test_filter_strength_decides_stability_as_in_fig_r10_nf(r10):
     for nf in (3, 4):
         assert runs[nf]["failed_at"] is None, runs[nf]
         assert runs[nf]["rhs_gtt_max"] < 1e-3
+
+
+def test_courant_limit_brackets_tab_dtfac(r10):
+    # Tab. dtfac gives lambda_max = 6.1 on 25 x 9 x 18 (its Delta t_stab
+    # 0.2651 and Delta t_unst 0.2666 over min dx = 0.0428): 6.0 runs, 6.5 fails
+    ok = r10.run_one(25, 9, 500.0, courant=6.0, sample_steps=10)
+    bad = r10.run_one(25, 9, 500.0, courant=6.5, sample_steps=10)
+    assert ok["failed_at"] is None and ok["rhs_gtt_final"] < 1e-9
+    assert bad["failed_at"] is not None and bad["failed_at"] < 500.0
+
+
+def test_scalar_y_filter_fails_where_yn_settles_as_in_fig_r10_f0(r10):
+    # Fig. r10_f0: with the scalar Y filter (n_f = 4) the run fails within a
+    # few thousand; with the Yn filter it settles at round-off level
+    cf = r10.cffyn
+    y = r10.run_one(25, 9, 4000.0, filter_kind=cf.FILTER_Y, sample_steps=50)
+    yn = r10.run_one(25, 9, 4000.0, filter_kind=cf.FILTER_YN, sample_steps=50)
+    assert y["failed_at"] is not None and y["failed_at"] < 4000.0
+    assert yn["failed_at"] is None and yn["rhs_gtt_late_max"] < 1e-10
