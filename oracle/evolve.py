@@ -39,6 +39,10 @@ class OracleShell:
         self._sf = None
         self.H = None
         self.dH = None
+        # constraint-damping factors of App. A.1 (the paper's values; tests of
+        # the damping change them)
+        self.gamma0 = 1.0
+        self.gamma2 = 1.0
 
     @property
     def sf(self):
@@ -82,7 +86,8 @@ class OracleShell:
         mu = u.shape[0]
         shp = u.shape[1:]
         out = ghg.rhs_pointwise(u.reshape(mu, -1), du.reshape(3, mu, -1),
-                                H.reshape(4, -1), dH.reshape(3, 4, -1), self.n_fields)
+                                H.reshape(4, -1), dH.reshape(3, 4, -1), self.n_fields,
+                                self.gamma0, self.gamma2)
         out = out.reshape(u.shape)
         del shp
         return ghg.apply_outer_bc(out, u, self.theta, self.phi)

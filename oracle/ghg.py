@@ -99,11 +99,17 @@ def gauge_source_from_state(u):
     return (-Gam_c).reshape((4,) + shp)
 
 
-def rhs_pointwise(u, du, H, dH, n_fields=50):
+def rhs_pointwise(u, du, H, dH, n_fields=50, gamma0=1.0, gamma2=1.0):
     """Right-hand side of eqs. gdot, Phidot, Pidot for every point.
 
     u[mu, P], du[3, mu, P] (numerical Cartesian derivatives of every field),
-    H[4, P] and dH[3, 4, P] (d_i H_a).  Returns rhs[mu, P]."""
+    H[4, P] and dH[3, 4, P] (d_i H_a).  Returns rhs[mu, P].
+
+    gamma0 and gamma2 are the constraint-damping factors of App. A.1, which
+    the printed equations take as 1 (with gamma1 = -1, gamma3 = gamma1
+    gamma2): gamma2 multiplies alpha (d_i g_ab - Phi_iab) in eq. Phidot and
+    -beta^k (d_k g_ab - Phi_kab) in eq. Pidot, gamma0 the gauge-constraint
+    term of eq. Pidot.  Other values exist only for tests of the damping."""
     g, Pi, Phi = split_state(u)
     dg = np.stack([unpack_sym(du[i, 0:10]) for i in range(3)])            # d_i g_ab
     dPi = np.stack([unpack_sym(du[i, 10:20]) for i in range(3)])          # d_i Pi_ab
@@ -126,11 +132,11 @@ def rhs_pointwise(u, du, H, dH, n_fields=50):
     nnPhi = np.einsum("cP,dP,icdP->iP", n_up, n_up, Phi, optimize=True)
     dt_Phi = (np.einsum("kP,kiabP->iabP", beta_up, dPhi)
               - alpha[None, None, None] * dPi
-              + alpha[None, None, None] * dg
+              + gamma2 * alpha[None, None, None] * dg
               + 0.5 * alpha[None, None, None] * nnPhi[:, None, None] * Pi[None]
               + alpha[None, None, None] * np.einsum("jkP,cP,ijcP,kabP->iabP", gamma_inv, n_up,
                                                     Phi[:, 1:], Phi, optimize=True)
-              - alpha[None, None, None] * Phi)
+              - gamma2 * alpha[None, None, None] * Phi)
 
     Q1 = np.einsum("cdP,ijP,iacP,jbdP->abP", ginv, gamma_inv, Phi, Phi, optimize=True)
     Q2 = np.einsum("cdP,acP,bdP->abP", ginv, Pi, Pi, optimize=True)
@@ -139,14 +145,14 @@ def rhs_pointwise(u, du, H, dH, n_fields=50):
     nC = np.einsum("cP,cP->P", n_up, C)
     dt_Pi = (np.einsum("kP,kabP->abP", beta_up, dPi)
              - al * np.einsum("ikP,kiabP->abP", gamma_inv, dPhi)
-             - np.einsum("kP,kabP->abP", beta_up, dg)
+             - gamma2 * np.einsum("kP,kabP->abP", beta_up, dg)
              + 2.0 * al * (Q1 - Q2 - Q3)
              - al * (DH + np.einsum("abP->baP", DH))
              - 0.5 * al * nnPi[None, None] * Pi
              - al * np.einsum("cP,ciP,ijP,jabP->abP", n_up, Pi[:, 1:], gamma_inv, Phi, optimize=True)
-             + al * (np.einsum("bP,aP->abP", n_lo, C) + np.einsum("aP,bP->abP", n_lo, C)
-                     - g * nC[None, None])
-             + np.einsum("iP,iabP->abP", beta_up, Phi))
+             + gamma0 * al * (np.einsum("bP,aP->abP", n_lo, C) + np.einsum("aP,bP->abP", n_lo, C)
+                              - g * nC[None, None])
+             + gamma2 * np.einsum("iP,iabP->abP", beta_up, Phi))
 
     out = np.zeros_like(u)
     out[0:10] = pack_sym(dt_g)

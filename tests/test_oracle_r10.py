@@ -21,11 +21,12 @@ def r10_initial(n_r, N):
     return u
 
 
-def run(n_r, N, n_f, lam, t_end, every=5, blowup=1e-2):
+def run(n_r, N, n_f, lam, t_end, every=5, blowup=1e-2, gamma0=1.0, gamma2=1.0):
     """PER_STEP Yn run (Sec. 2.5) with n_f top modes removed; returns the
     time of failure (or None) and the sampled max |d_t g_tt| at r = r_in."""
     u = r10_initial(n_r, N)
     sh = oracle.OracleShell(n_r, N, 2 * N, R_IN, R_OUT, N - 1 - n_f, filter_mode="step")
+    sh.gamma0, sh.gamma2 = gamma0, gamma2
     sh.init_gauge_from_state(u)
     dt = lam * sh.dx_min()
     n = int(round(t_end / dt))
@@ -59,6 +60,18 @@ def test_filter_strength_decides_stability_as_in_fig_r10_nf():
     # Fig. r10_nf: with n_f = 0 the run fails within t = 110 (here long
     # before t = 40); with the default n_f = 4 it settles
     t_fail0, _ = run(13, 9, 0, 4.0, 40.0)
-    t_fail4, vals4 = run(13, 9, 4, 4.0, 40.0)
+    t_fail4, vals4 = run(13, 9, 4, 4.0, 50.0)
     assert t_fail0 is not None and t_fail0 < 40.0
     assert t_fail4 is None and max(vals4) < 1e-3
+
+
+def test_constraint_damping_terms_keep_the_run_stable():
+    # The damping terms of App. A.1 (gamma0 on the gauge constraint in
+    # eq. Pidot, gamma2 on C_iab in eqs. Phidot and Pidot) vanish on exact
+    # data, so rhs parity alone does not pin them; the R10 run does.  With the
+    # paper's gamma0 = gamma2 = 1 it settles (previous test, to t = 50);
+    # without either term it fails well before t = 50.
+    t_no_g2, _ = run(13, 9, 4, 4.0, 50.0, gamma2=0.0)
+    t_no_g0, _ = run(13, 9, 4, 4.0, 50.0, gamma0=0.0)
+    assert t_no_g2 is not None and t_no_g2 < 50.0
+    assert t_no_g0 is not None and t_no_g0 < 50.0
