@@ -75,3 +75,14 @@ def test_constraint_damping_terms_keep_the_run_stable():
     t_no_g0, _ = run(13, 9, 4, 4.0, 50.0, gamma0=0.0)
     assert t_no_g2 is not None and t_no_g2 < 50.0
     assert t_no_g0 is not None and t_no_g0 < 50.0
+
+
+def test_courant_limit_brackets_tab_dtfac():
+    # Tab. dtfac: on 25 x 9 x 18 the largest stable step is 0.2651 and the
+    # smallest unstable one 0.2666, i.e. lambda = 6.20 and 6.23 over
+    # min dx = r_1 - r_0 = 0.04278 (the radial spacing limits this grid).
+    # lambda = 6.0 runs on; 6.5 fails within a few tens of time units.
+    t_fail, _ = run(25, 9, 4, 6.5, 30.0)
+    t_ok, vals = run(25, 9, 4, 6.0, 30.0)
+    assert t_fail is not None and t_fail < 30.0
+    assert t_ok is None and max(vals) < 1e-6
