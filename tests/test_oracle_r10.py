@@ -2,7 +2,12 @@
 initial data with a numerical Phi (App. A.3) and the filter-strength result of
 Fig. r10_nf.  CPU only."""
 
+import concurrent.futures
+import multiprocessing
+import os
+
 import numpy as np
+import pytest
 
 import oracle
 from paper_1104_3408_gb300 import inputs
@@ -56,33 +61,68 @@ def test_numerical_phi_data_is_static_in_g():
     assert c3 < 1e-15 and c4 < 1e-14
 
 
-def test_filter_strength_decides_stability_as_in_fig_r10_nf():
+# The PER_STEP runs the tests below read: (n_r, N, n_f, lambda, t_end, options)
+RUNS = {
+    "nf0": (13, 9, 0, 4.0, 40.0, {}),
+    "nf4": (13, 9, 4, 4.0, 50.0, {}),
+    "no_gamma2": (13, 9, 4, 4.0, 50.0, {"gamma2": 0.0}),
+    "no_gamma0": (13, 9, 4, 4.0, 50.0, {"gamma0": 0.0}),
+    "lambda_6.5": (25, 9, 4, 6.5, 30.0, {}),
+    "lambda_6.0": (25, 9, 4, 6.0, 30.0, {}),
+}
+
+
+def _run_named(item):
+    name, (n_r, N, n_f, lam, t_end, kw) = item
+    return name, run(n_r, N, n_f, lam, t_end, **kw)
+
+
+@pytest.fixture(scope="module")
+def runs():
+    """All runs at once in spawned worker processes (one BLAS thread each)."""
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        workers = max(1, min(len(RUNS), os.cpu_count() or 1))
+        with concurrent.futures.ProcessPoolExecutor(
+                max_workers=workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+            return dict(ex.map(_run_named, RUNS.items()))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def test_filter_strength_decides_stability_as_in_fig_r10_nf(runs):
     # Fig. r10_nf: with n_f = 0 the run fails within t = 110 (here long
     # before t = 40); with the default n_f = 4 it settles
-    t_fail0, _ = run(13, 9, 0, 4.0, 40.0)
-    t_fail4, vals4 = run(13, 9, 4, 4.0, 50.0)
+    t_fail0, _ = runs["nf0"]
+    t_fail4, vals4 = runs["nf4"]
     assert t_fail0 is not None and t_fail0 < 40.0
     assert t_fail4 is None and max(vals4) < 1e-3
 
 
-def test_constraint_damping_terms_keep_the_run_stable():
+def test_constraint_damping_terms_keep_the_run_stable(runs):
     # The damping terms of App. A.1 (gamma0 on the gauge constraint in
     # eq. Pidot, gamma2 on C_iab in eqs. Phidot and Pidot) vanish on exact
     # data, so rhs parity alone does not pin them; the R10 run does.  With the
     # paper's gamma0 = gamma2 = 1 it settles (previous test, to t = 50);
     # without either term it fails well before t = 50.
-    t_no_g2, _ = run(13, 9, 4, 4.0, 50.0, gamma2=0.0)
-    t_no_g0, _ = run(13, 9, 4, 4.0, 50.0, gamma0=0.0)
+    t_no_g2, _ = runs["no_gamma2"]
+    t_no_g0, _ = runs["no_gamma0"]
     assert t_no_g2 is not None and t_no_g2 < 50.0
     assert t_no_g0 is not None and t_no_g0 < 50.0
 
 
-def test_courant_limit_brackets_tab_dtfac():
+def test_courant_limit_brackets_tab_dtfac(runs):
     # Tab. dtfac: on 25 x 9 x 18 the largest stable step is 0.2651 and the
     # smallest unstable one 0.2666, i.e. lambda = 6.20 and 6.23 over
     # min dx = r_1 - r_0 = 0.04278 (the radial spacing limits this grid).
     # lambda = 6.0 runs on; 6.5 fails within a few tens of time units.
-    t_fail, _ = run(25, 9, 4, 6.5, 30.0)
-    t_ok, vals = run(25, 9, 4, 6.0, 30.0)
+    t_fail, _ = runs["lambda_6.5"]
+    t_ok, vals = runs["lambda_6.0"]
     assert t_fail is not None and t_fail < 30.0
     assert t_ok is None and max(vals) < 1e-6
