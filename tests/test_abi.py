@@ -65,6 +65,8 @@ def test_null_handles_are_rejected(lib):
     assert lib.cffyn_filter(None, None, None, None) == cffyn.EINVAL
     assert lib.cffyn_rk4_step(None, None, 0.1, 1, None) == cffyn.EINVAL
     assert lib.cffyn_create_shell_ex(None, None) == cffyn.EINVAL
+    assert lib.cffyn_derivs_fft(None, None, None, None) == cffyn.EINVAL
+    assert b"NULL" in lib.cffyn_last_error()
 
 
 def test_static_scratch_limit_and_null_shell(lib):
