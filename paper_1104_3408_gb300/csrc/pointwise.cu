@@ -591,23 +591,27 @@ __global__ void __launch_bounds__(128, 6) k_reconstruct(const double* __restrict
 
 // Spherical -> Cartesian derivatives: D[3][nf][P] -> out[3][nf][P] (FP64
 // arithmetic; D and out in the given storages).  Setup and API paths only.
+// One thread per point: the Jacobian (FP64 divisions) is formed once and
+// applied to every field, whose values are coalesced across the threads.
 template <bool FI, bool FO>
 __global__ void k_cart(const double* __restrict__ D, double* __restrict__ out, int nf, Geo geo) {
   const long long P = geo.P;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= P * nf) return;
-  const long long p = t % P;
-  const int mu = (int)(t / P);
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= P) return;
   const int k = (int)(p % geo.n_r);
   const int i = (int)((p / geo.n_r) % geo.N);
   const int jj = (int)(p / ((long long)geo.n_r * geo.N));
   const Jac<double> J = jacobian<double>(geo, k, i, jj);
-  const double dr = Store<double, FI>::ld(D, (long long)mu * P + p);
-  const double dt = Store<double, FI>::ld(D, ((long long)nf + mu) * P + p);
-  const double dp = Store<double, FI>::ld(D, ((long long)2 * nf + mu) * P + p);
+#pragma unroll 2
+  for (int mu = 0; mu < nf; ++mu) {
+    const double dr = Store<double, FI>::ld(D, (long long)mu * P + p);
+    const double dt = Store<double, FI>::ld(D, ((long long)nf + mu) * P + p);
+    const double dp = Store<double, FI>::ld(D, ((long long)2 * nf + mu) * P + p);
 #pragma unroll
-  for (int x = 0; x < 3; ++x)
-    Store<double, FO>::st(out, ((long long)x * nf + mu) * P + p, J.j[x][0] * dr + J.j[x][1] * dt + J.j[x][2] * dp);
+    for (int x = 0; x < 3; ++x)
+      Store<double, FO>::st(out, ((long long)x * nf + mu) * P + p,
+                            J.j[x][0] * dr + J.j[x][1] * dt + J.j[x][2] * dp);
+  }
 }
 
 // H_a = -Gamma_a(u), pointwise (FP64); H in storage FO
@@ -739,7 +743,7 @@ int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mod
 int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, bool out_pairs, cudaStream_t st) {
   Geo g = geo_of(sh);
   const bool in_pairs = sh->d.precision == CFFYN_MIXED;
-  const unsigned nb = blocks_for(g.P * nf, 256);
+  const unsigned nb = blocks_for(g.P, 256);
   if (in_pairs && out_pairs)
     k_cart<true, true><<<nb, 256, 0, st>>>(D, out, nf, g);
   else if (in_pairs)
@@ -755,7 +759,7 @@ int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, bool ou
 // on either path (the FFT derivative path writes FP64 into the workspace)
 int pw_cart_fp64(const cffyn_shell* sh, const double* D, double* out, int nf, cudaStream_t st) {
   Geo g = geo_of(sh);
-  k_cart<false, false><<<blocks_for(g.P * nf, 256), 256, 0, st>>>(D, out, nf, g);
+  k_cart<false, false><<<blocks_for(g.P, 256), 256, 0, st>>>(D, out, nf, g);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
