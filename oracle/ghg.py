@@ -31,6 +31,9 @@ is a projection that keeps the outgoing characteristic field, C_a(0) = 0 after
 the gauge initialisation, exact Kerr-Schild data give a right-hand side at
 truncation level converging with n_r (Sec. 4.1), and a complex-step
 derivative of every evolution equation against an independent linearisation.
+The constraint-damping terms (gamma0, gamma2), which vanish on exact data, are
+pinned by the R10 runs of Sec. 4.1 (tests/test_oracle_r10.py): with them the
+run settles, without either it fails (presence and sign, not magnitude).
 """
 
 import numpy as np
