@@ -58,3 +58,14 @@ def test_two_gloo_ranks_share_the_batch_and_the_slowest_time():
     assert sorted(out[0][3] + out[1][3]) == list(range(16))
     assert not set(out[0][3]) & set(out[1][3])
     assert all(o[4] == 11.0 for o in out)
+
+
+def test_operator_work_is_the_method_count():
+    # the roofline's algorithmic work per pt-field per substep is the method's
+    # 2 n_r + 16 N + 2 (L + 1) FP64 flops (d_r, d_theta + d_phi, and the
+    # filter's DFT, projection and inverse DFT)
+    w = dict(inputs.WORKLOADS["ks_33x48x96"], name="ks_33x48x96")
+    P = w["n_r"] * w["n_theta"] * w["n_phi"] * w["n_fields"]
+    total = sum(bench._op_flops(w, ph) for ph in bench.PAIRS)
+    assert total == (2 * 33 + 16 * 48 + 2 * (46 + 1)) * P == 928 * P
+    assert set(bench.PAIRS) == set(bench.FAMILIES["k_op_tc"])
