@@ -111,6 +111,17 @@ def synthesis_matrix(sl, n, m, N):
     return P, ls
 
 
+def synthesis_condition(sl, n, m, N):
+    """2-norm condition number sigma_max / sigma_min of P^n_m (the synthesis
+    matrix of eq. forwardL without its zero columns); inf if rank deficient,
+    0 for an empty matrix."""
+    P, _ = synthesis_matrix(sl, n, m, N)
+    if P.shape[1] == 0:
+        return 0.0
+    S = np.linalg.svd(P, compute_uv=False)
+    return float(S[0] / S[-1]) if S[-1] > 0 else float("inf")
+
+
 def pinv_svd(A):
     """Moore-Penrose pseudo-inverse by the SVD A = U S V^T: A^+ = V S^+ U^T."""
     if A.shape[1] == 0:
