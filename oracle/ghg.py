@@ -25,15 +25,20 @@ Outer boundary (App. A.2, freeze-incoming, the B = E^{-1} Z E formulas at the
 end of A.2) at the largest radius only; s_i = l_i / sqrt(gamma^ij l_i l_j),
 l_i = x_i / r, s^k = gamma^kl s_l with the current metric.
 
-Parity pins (tests/test_oracle_ghg.py): closed-form Kerr-Schild 3+1
-quantities (App. A.3), the characteristic speeds printed in App. A.3, the BC
-is a projection that keeps the outgoing characteristic field, C_a(0) = 0 after
-the gauge initialisation, exact Kerr-Schild data give a right-hand side at
-truncation level converging with n_r (Sec. 4.1), and a complex-step
-derivative of every evolution equation against an independent linearisation.
-The constraint-damping terms (gamma0, gamma2), which vanish on exact data, are
-pinned by the R10 runs of Sec. 4.1 (tests/test_oracle_r10.py): with them the
-run settles, without either it fails (presence and sign, not magnitude).
+Parity pins (tests/test_oracle_ghg.py, tests/test_oracle_constraints.py):
+closed-form Kerr-Schild 3+1 quantities (App. A.3); the characteristic speeds
+printed in App. A.3; the linear part of the rhs in d_k u against the printed
+characteristic matrix of App. A.2 (this fixes every derivative term,
+including the gamma_2 d_i g_ab terms); the BC is a projection that keeps the
+outgoing characteristic field; exact Kerr-Schild data give a right-hand side
+at truncation level converging with n_r (Sec. 4.1); Gamma_a of exact
+Kerr-Schild data equals its closed form (2M/r^2) l_a; the constraint norms of
+data with a known violation (one of the 30 C_iab components, or C_a = h)
+equal the RMS over points and components; the gamma_2 terms drop out when
+C_iab = 0; and on spatially constant perturbations of flat space the
+constraints decay at the rates the damping terms give at linear order
+(C_iab at gamma_2, C_t at 2 gamma_0, C_i at gamma_0).  The R10 runs of
+Sec. 4.1 (tests/test_oracle_r10.py) also need both damping terms to settle.
 """
 
 import numpy as np
