@@ -40,6 +40,9 @@ def _args():
     ap.add_argument("--workload", default="ks_33x48x96")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the shorter measurements of the 58-field 65x96x192 shell and of the "
+                         "256-shell batch that a default run adds to its line")
     ap.add_argument("--filter", default="yn", choices=["yn", "y", "yg"],
                     help="filter of the single-shell workloads: tensor Yn (default), scalar Y, graded Yg")
     ap.add_argument("--sweep", default=None,
@@ -169,10 +172,20 @@ FAMILIES = {
 # BF16 digit-pair products per operator product: i + j <= 6 of 6 x 6 digits
 # for the derivatives, i + j <= 5 for the filter's DFTs and projections
 PAIRS = {"d_r": 26, "d_theta_phi": 26, "dft_fwd": 21, "project": 21, "dft_inv": 21}
-# DRAM bytes per step of all k_op_tc launches, from the ncu launch list of the
-# same command (profiles/launch_list_ks_33x48x96_mixed.md); None where no
-# capture of the current kernel exists.
-OP_TRAFFIC_PER_STEP = {"ks_33x48x96": 1.99e9}
+# FP64 operations of one evaluation of the pointwise right-hand side per point
+# (eqs. gdot, Phidot, Pidot with their 3+1 quantities and Christoffel
+# symbols), counted on the oracle's own formulation by oracle/flops.py
+# (tests/test_oracle_flops.py checks this figure); the chain rule adds
+# 15 per pt-field (eq. dvdx).
+RHS_OPS_PER_POINT = 6418.0
+# FP32 instructions per FP64-equivalent operation of the double-float
+# arithmetic of the mixed path's pointwise kernels: an addition is TwoSum
+# (6) + 2 + a fast renormalisation (3) = 11, a product is 1 + 1 FMA + 2 + 1
+# + 3 = 8; the whole-step bound takes the mean, 9.5.
+FF_INSTR_PER_OP = 9.5
+# SM count and FP32 lanes per SM of the GB300 (the FP32 pipe's instruction
+# peak is SMs x lanes x SM clock).
+SMS, FP32_LANES = 152, 128
 
 
 def _op_flops(w, phase):
@@ -197,35 +210,96 @@ def _pointwise_bytes(w, phase):
     return vals * P8
 
 
+def _op_sources_sha():
+    """sha256 of the sources that define the operator kernel k_op_tc."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("ops.cu", "tc.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1104_3408_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _op_traffic(w):
+    """DRAM bytes per step of the operator family from the committed
+    single-kernel capture summary profiles/k_op_tc_dram_<workload>.md, or
+    None when there is none or it was taken on other kernel sources."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"k_op_tc_dram_{w['name']}.md")
+    if not os.path.exists(path):
+        return None, "no single-kernel DRAM capture of k_op_tc for this workload"
+    with open(path) as fh:
+        text = fh.read()
+    sha = re.search(r"sources_sha256:\s*([0-9a-f]{64})", text)
+    val = re.search(r"dram_bytes_per_step:\s*([0-9.eE+]+)", text)
+    if not sha or not val:
+        return None, "capture summary without sources_sha256 / dram_bytes_per_step"
+    if sha.group(1) != _op_sources_sha():
+        return None, "capture taken on other k_op_tc sources (stale)"
+    return float(val.group(1)), f"profiles/k_op_tc_dram_{w['name']}.md"
+
+
+def _whole_step_bound(w, ms_step, hbm, bf16s, sm_mhz):
+    """The whole-step roofline of the method: T_bound = max(operator work /
+    tensor peak, algorithmic bytes / HBM peak) + right-hand-side work / ALU
+    peak, per RK4 step (four substeps).  Operator work: the method's FP64
+    flops 2n_r + 16N + 2(L+1) per pt-field per substep (no emulation
+    overhead).  Bytes: 40 per pt-field per substep (read the stage state and
+    u_n, read and write the accumulator, write the next stage).  Right-hand
+    side: RHS_OPS_PER_POINT + 15 n_v (chain rule) FP64-equivalent operations
+    per point, each FF_INSTR_PER_OP FP32 instructions on the FP32 pipe
+    (SMS x FP32_LANES x the measured median SM clock)."""
+    n_r, N, J, L, nv = w["n_r"], w["n_theta"], w["n_phi"], w["L"], w["n_fields"]
+    P = n_r * N * J
+    units = 4.0 * P * nv
+    t_tensor = (2 * n_r + 16 * N + 2 * (L + 1)) * units / (bf16s * 1e12)
+    t_hbm = 40.0 * units / (hbm * 1e9)
+    clk = (sm_mhz or 2070.0) * 1e6
+    t_alu = 4.0 * P * (RHS_OPS_PER_POINT + 15 * nv) * FF_INSTR_PER_OP / (SMS * FP32_LANES * clk)
+    t_bound = max(t_tensor, t_hbm) + t_alu
+    return {"t_tensor_ms": t_tensor * 1e3, "t_hbm_ms": t_hbm * 1e3, "t_rhs_alu_ms": t_alu * 1e3,
+            "t_bound_ms": t_bound * 1e3, "ms_per_step": ms_step, "frac": t_bound * 1e3 / ms_step,
+            "rhs_ops_per_point": RHS_OPS_PER_POINT + 15 * nv, "ff_instr_per_op": FF_INSTR_PER_OP,
+            "sm_mhz": clk / 1e6}
+
+
 def _roofline(w, per_step, launches, hbm, bf16s, peak_kind):
     """Roofline of the dominant kernel family of the traced step (largest device
     time per step).  The operator family is a dense contraction on the tensor
-    cores: its algorithmic work is the method's FP64 operator flops times the
-    26 BF16 digit-pair products each one takes; it is timed inside the step, so
-    the peak is the sustained BF16 figure.  Pointwise families are compared with
-    HBM on their algorithmic bytes."""
+    cores: achieved = the method's own FP64 operator flops (2n_r + 16N +
+    2(L+1) per pt-field per substep) / the family's traced time, against the
+    sustained BF16 peak (it runs inside a long step).  The split-precision
+    scheme issues 26 (derivatives) or 21 (filter) BF16 digit-pair products per
+    such flop: that utilisation of the tensor pipe is reported beside it as
+    tensor_pipe_frac.  Pointwise families are compared with HBM on their
+    algorithmic bytes."""
     fam_ms = {f: sum(per_step.get(ph, 0.0) for ph in phs) for f, phs in FAMILIES.items()}
     dom = max(fam_ms, key=fam_ms.get)
     t = fam_ms[dom] * 1e-3
     nl = sum(launches.get(ph, 0) for ph in FAMILIES[dom])
     if dom == "k_op_tc":
         fl = sum(4 * _op_flops(w, ph) for ph in FAMILIES[dom])  # 4 stages
-        achieved = sum(PAIRS[ph] * 4 * _op_flops(w, ph) for ph in FAMILIES[dom]) / t / 1e12
+        achieved = fl / t / 1e12
+        issued = sum(PAIRS[ph] * 4 * _op_flops(w, ph) for ph in FAMILIES[dom]) / t / 1e12
         byts = 4 * 8.0 * w["n_fields"] * w["n_r"] * w["n_theta"] * w["n_phi"] * (
             6 + 2 + 4 * (2 * w["L"] + 1) / w["n_phi"])
         per_launch = {}
         for ph in FAMILIES[dom]:
             tl = per_step[ph] * 1e-3
             per_launch[ph] = {"ms_per_step": per_step[ph], "launches_per_step": launches[ph],
-                              "tensor_frac": PAIRS[ph] * 4 * _op_flops(w, ph) / tl / 1e12 / bf16s}
+                              "method_tflops": 4 * _op_flops(w, ph) / tl / 1e12,
+                              "tensor_pipe_frac": PAIRS[ph] * 4 * _op_flops(w, ph) / tl / 1e12 / bf16s}
+        traffic, tsrc = _op_traffic(w)
         return {"bound": "tensor", "kernel": "k_op_tc (all operator launches of the step)",
                 "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
-                "traffic": OP_TRAFFIC_PER_STEP.get(w["name"]),
-                "traffic_scope": "DRAM bytes per step, all k_op_tc launches (ncu launch list)",
+                "traffic": traffic, "traffic_source": tsrc,
+                "traffic_scope": "DRAM bytes per step, all k_op_tc launches",
                 "peak_source": f"bf16_tflops_sustained ({peak_kind})",
-                "work": "26 (derivatives) or 21 (filter) BF16 digit-pair products x method FP64 operator flops "
-                        "(2n_r + 16N + 2(L+1) per pt-field per substep)",
-                "fp64_equiv_tflops": fl / t / 1e12,
+                "work": "the method's FP64 operator flops, 2n_r + 16N + 2(L+1) per pt-field per substep "
+                        "(no emulation overhead)",
+                "tensor_pipe_frac": issued / bf16s,
+                "issued_bf16_tflops": issued,
+                "issued_work": "26 (derivatives) or 21 (filter) BF16 digit-pair products per method flop",
                 "hbm_view": {"algorithmic_GBps": byts / t / 1e9, "frac": byts / t / 1e9 / hbm},
                 "ms_per_step": fam_ms[dom], "launches_per_step": nl, "per_phase": per_launch}
     byts = sum(launches[ph] * _pointwise_bytes(w, ph) for ph in FAMILIES[dom])
@@ -235,7 +309,7 @@ def _roofline(w, per_step, launches, hbm, bf16s, peak_kind):
             "ms_per_step": fam_ms[dom], "launches_per_step": nl}
 
 
-def run_ours(args, rank, local_rank, ws, dist):
+def run_ours(args, rank, local_rank, ws, dist, acc_steps=100):
     import numpy as np
     import torch
 
@@ -298,6 +372,8 @@ def run_ours(args, rank, local_rank, ws, dist):
     hbm, bf16s, peak_kind = _peaks()
     per_step = {k: v / max(tsteps, 1) for k, v in trace_ms.items()}
     roof = _roofline(w, per_step, launches, hbm, bf16s, peak_kind)
+    roof["whole_step"] = _whole_step_bound(w, t_max / args.steps, hbm, bf16s,
+                                           clk.get("sm_mhz") if clk else None)
 
     # ---- plain FP64 GPU path on the same workload
     fp64 = None
@@ -314,18 +390,18 @@ def run_ours(args, rank, local_rank, ws, dist):
         k64 = max(2, min(args.steps, 5))
         t64 = _time_steps(s64, v, dt, k64, flush, torch)
         fp64_value = units_per_step * k64 / (t64 * 1e-3)
-        # accuracy: 100 steps of both paths from the same filtered state
+        # accuracy: acc_steps steps of both paths from the same filtered state
         a = torch.from_numpy(u0).cuda()
         sh.init_gauge_from_state(a)
         sh.filter(a, uf)
         a.copy_(uf)
         b = a.clone()
-        sh.rk4_step(a, dt, 100)
-        s64.rk4_step(b, dt, 100)
+        sh.rk4_step(a, dt, acc_steps)
+        s64.rk4_step(b, dt, acc_steps)
         err = float((a - b).abs().max() / b.abs().max())
         s64.destroy()
         fp64 = {"value": fp64_value, "steps": k64, "mixed_over_fp64": value / ws / fp64_value,
-                "err_fields_100_steps_vs_fp64_gpu": err}
+                f"err_fields_{acc_steps}_steps_vs_fp64_gpu": err}
 
     # ---- end to end through the C-ABI with host buffers
     hu = torch.from_numpy(u0).pin_memory()
@@ -540,16 +616,20 @@ def run_batch(args, rank, local_rank, ws, dist):
 
     # ---- whole-step tensor roofline (a lower bound of the operator family's share)
     hbm, bf16s, peak_kind = _peaks()
-    fl = 0.0
+    fl = issued = 0.0
     for i in mine:
         d = descs[i]
         deriv = 2 * d["n_r"] + 8 * d["n_theta"]
         filt = 8 * d["n_theta"] + 2 * (d["L"] + 1)
-        fl += 4.0 * (26 * deriv + 21 * filt) * _shell_units(d)
+        fl += 4.0 * (deriv + filt) * _shell_units(d)
+        issued += 4.0 * (26 * deriv + 21 * filt) * _shell_units(d)
     achieved = fl * args.steps / (t_ms * 1e-3) / 1e12
     roof = {"bound": "tensor", "kernel": "k_op_tc (operator work over the whole batch step time)",
             "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
-            "traffic": None, "peak_source": f"bf16_tflops_sustained ({peak_kind})",
+            "traffic": None, "traffic_source": "no single-kernel capture of the batch",
+            "peak_source": f"bf16_tflops_sustained ({peak_kind})",
+            "work": "the method's FP64 operator flops, 2n_r + 16N + 2(L+1) per pt-field per substep",
+            "tensor_pipe_frac": issued * args.steps / (t_ms * 1e-3) / 1e12 / bf16s,
             "scope": "divides by the whole step (all kernel families), so it is a lower bound "
                      "of the operator kernels' own fraction"}
     cpu = None
@@ -738,6 +818,32 @@ def run_derivs_sweep(args):
             "rows": rows}
 
 
+def run_other_workloads(args, local_rank):
+    """Shorter measurements of the other two throughput configurations on the
+    same GPU, after the main line: the 58-field 65 x 96 x 192 shell (5 timed
+    steps, FP64 path beside it, fields compared after 10 steps) and the batch
+    of 256 uneven shells (5 timed batch steps, per-shell loops beside it).
+    Same timing rules as the main line; no CPU baseline."""
+    import copy
+
+    import torch
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "roofline", "fp64_gpu", "e2e",
+            "clocks", "gpu_launches", "mixed_per_shell_loop_value", "batch_over_mixed_loop")
+    res = {}
+    for name, fn in (("ks_65x96x192_58f", lambda a: run_ours(a, 0, local_rank, 1, None, acc_steps=10)),
+                     ("batch_256", lambda a: run_batch(a, 0, local_rank, 1, None))):
+        a = copy.copy(args)
+        a.workload, a.steps, a.warmup, a.no_cpu_baseline = name, 5, 3, True
+        try:
+            r = fn(a)
+            res[name] = {k: r[k] for k in keep if k in r}
+        except Exception as e:  # recorded in the line, never hides the main value
+            res[name] = {"error": repr(e)}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return res
+
+
 def main():
     args = _args()
     if args.profile_step:
@@ -756,6 +862,8 @@ def main():
         out = run_batch(args, rank, local_rank, ws, dist)
     else:
         out = run_ours(args, rank, local_rank, ws, dist)
+        if ws == 1 and not args.no_other_workloads and args.workload == "ks_33x48x96":
+            out["other_workloads"] = run_other_workloads(args, local_rank)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if dist:

@@ -251,6 +251,21 @@ CFFYN_API int cffyn_get_operator(const cffyn_shell* sh, int which, double* host_
 CFFYN_API int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out,
                                  int* launches_out, void* stream);
 
+/* Bound of every wait inside the tensor-core operator kernels of the
+ * CFFYN_MIXED path (mbarrier waits for operand copies, for the producers'
+ * operand slices and for the tensor-core products), in seconds; the default
+ * is 1.  A wait that runs out makes that kernel stop, mark the shell's status
+ * word and return; cffyn_rk4_step / cffyn_batch_rk4_step then report
+ * CFFYN_ETIMEOUT (cffyn_derivs_static writes NaN), the results are invalid
+ * and the context stays usable.  seconds < 0 restores the default; 0 makes
+ * every such wait give up at once without polling, the way to exercise the
+ * CFFYN_ETIMEOUT path.  The waits that let copies and products already in
+ * flight finish before a kernel block exits keep the 1 s bound whatever the
+ * setting.  Drops the shell's captured step graph (the next step
+ * recaptures; so does a batch holding the shell).  CFFYN_EINVAL for more
+ * than 60 s or NaN. */
+CFFYN_API int cffyn_set_wait_limit(cffyn_shell* sh, double seconds);
+
 /* Live tracing of cffyn_rk4_step: with tracing on, the captured step graph
  * records a CUDA event after every kernel group (same groups as
  * cffyn_profile_step) and each cffyn_rk4_step call adds the group durations
@@ -262,17 +277,17 @@ CFFYN_API int cffyn_set_trace(cffyn_shell* sh, int on);
 CFFYN_API int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launches_out,
                               long long* steps);
 
-/* Allocation-free Cartesian derivatives.  A library facility: the paper has
- * no counterpart (it is a variant of cffyn_derivs, Secs. 2.3-2.4, eq. dvdx).
+/* Allocation-free Cartesian derivatives.  A library facility with no
+ * counterpart in the paper: a variant of cffyn_derivs.
  * Computes what cffyn_derivs computes, for the first n_f fields of u only:
  *     dxyz[d][mu][n_phi][n_theta][n_r], d = x, y, z, mu < n_f (3 * n_f arrays).
  * Every intermediate (the spherical derivatives and, on the CFFYN_MIXED
- * path, the per-field exponents) lives in one fixed array
- * of CFFYN_STATIC_SCRATCH_BYTES of the library's own device memory, which
- * exists on each device once the library's device code is loaded there.  The
- * call allocates nothing (no cudaMalloc, no library allocator) and neither
- * reads nor writes the shell's workspace: it reads only the shell's constant
- * grid and operators.
+ * path, the per-field exponents and the call's status word) lives in one
+ * fixed array of CFFYN_STATIC_SCRATCH_BYTES of the library's own device
+ * memory, which exists on each device once the library's device code is
+ * loaded there.  The call allocates nothing (no cudaMalloc, no library
+ * allocator) and neither reads nor writes the shell's workspace or its
+ * status word: it reads only the shell's constant grid and operators.
  *
  * Who it is for: callers that cannot get device memory at the point of the
  * call, or must not cause an allocation there: code running with the
@@ -290,10 +305,16 @@ CFFYN_API int cffyn_get_trace(const cffyn_shell* sh, double* ms_out, int* launch
  * and launches nothing.  Examples: 9 x 12 x 24, all 50 fields; 33 x 32 x 64,
  * 5 fields.
  *
- * Zeroing: the 64 per-field exponent words of the mixed path are maxima
- * accumulated with atomics and must start at zero on every call; the call
- * zeroes them itself on `stream` (cudaMemsetAsync, no allocation).  The
- * caller clears nothing; every other byte is written before it is read.
+ * Zeroing: the 64 words after the derivatives on the mixed path (per-field
+ * exponents, maxima accumulated with atomics, and the status word) must
+ * start at zero on every call; the call zeroes them itself on `stream`
+ * (cudaMemsetAsync, no allocation).  The caller clears nothing; every other
+ * byte is written before it is read.
+ *
+ * Timeouts: the call is asynchronous and returns before the device work
+ * ends.  If a bounded wait of the tensor-core kernel gives up (CFFYN_ETIMEOUT
+ * elsewhere), every value of dxyz is written as a quiet NaN, so the caller
+ * sees the failure in the output itself.
  *
  * Races: there is one array per device, shared by every call on that device
  * for every shell.  Calls whose device work can overlap (other streams,

@@ -26,6 +26,7 @@ EXPORTED = [
     "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_constraint_norms",
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
+    "cffyn_set_wait_limit",
     "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch",
     "cffyn_workspace_size", "cffyn_attach_workspace", "cffyn_derivs_fft",
 ]
@@ -73,6 +74,7 @@ def load(path=LIB_PATH):
         "cffyn_init_gauge_from_state": ([vp, dp, vp], i),
         "cffyn_derivs": ([vp, dp, dp, vp], i),
         "cffyn_derivs_static": ([vp, dp, i, dp, vp], i),
+        "cffyn_set_wait_limit": ([vp, d], i),
         "cffyn_derivs_fft": ([vp, dp, dp, vp], i),
         "cffyn_rhs": ([vp, dp, dp, vp], i),
         "cffyn_filter": ([vp, dp, dp, vp], i),
@@ -217,6 +219,11 @@ class Shell:
         la = (ctypes.c_int * n)()
         _check(load().cffyn_profile_step(self.h, _ptr(u, "u"), float(dt), ms, la, _stream(stream)))
         return {k: (float(ms[i]), int(la[i])) for i, k in enumerate(PROFILE_PHASES)}
+
+    def set_wait_limit(self, seconds):
+        """Bound (s) of the tensor-core kernels' waits; < 0 restores 1 s, 0
+        gives up at once (cffyn_set_wait_limit)."""
+        _check(load().cffyn_set_wait_limit(self.h, float(seconds)))
 
     def set_trace(self, on=True):
         _check(load().cffyn_set_trace(self.h, 1 if on else 0))

@@ -694,6 +694,24 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
   return step_flag_status(*sh->flag_host);
 }
 
+int cffyn_set_wait_limit(cffyn_shell* sh, double seconds) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  if (!(seconds == seconds) || seconds > 60.0) {
+    set_error("wait limit %g s outside [0, 60]", seconds);
+    return CFFYN_EINVAL;
+  }
+  const unsigned long long ns = seconds < 0 ? 1000000000ull : (unsigned long long)(seconds * 1e9);
+  if (ns == sh->tc_wait_ns) return CFFYN_OK;
+  sh->tc_wait_ns = ns;
+  // the bound is a parameter of the captured kernels
+  if (sh->graph) {
+    cudaGraphExecDestroy(sh->graph);
+    sh->graph = nullptr;
+  }
+  ++sh->ws_gen;
+  return CFFYN_OK;
+}
+
 int cffyn_set_trace(cffyn_shell* sh, int on) {
   if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
   sh->trace = on ? 1 : 0;

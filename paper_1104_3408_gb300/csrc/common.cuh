@@ -106,9 +106,13 @@ struct cffyn_shell {
   double* dH = nullptr;   // [3][4][P] d_i H_a, + [4][P] d_t H_a for 58 fields
   bool gauge_set = false;
 
+  // bound of every pipeline wait of the tensor-core operator kernel (ns;
+  // 0: give up at once), cffyn_set_wait_limit
+  unsigned long long tc_wait_ns = 1000000000ull;
+
   // workspace: one block (ws, ws_bytes) carved into the arrays below; owned
-  // by the library (ws_owned) or attached by the caller; ws_gen counts
-  // attachments so that captured graphs can tell they are stale
+  // by the library (ws_owned) or attached by the caller; ws_gen counts the
+  // changes that make captured graphs stale (attachments, wait limits)
   void* ws = nullptr;
   size_t ws_bytes = 0;
   bool ws_owned = false;

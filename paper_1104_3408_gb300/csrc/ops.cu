@@ -435,7 +435,13 @@ __global__ void __launch_bounds__(kExpThreads) k_field_exp(const long long* __re
 constexpr int kTcCols = 128;
 constexpr int kTcXSlice = kTcCols * 16 * 2;                 // bytes of one data slice per k-step
 constexpr int kTcXBytes = kSlices * kTcXSlice;               // 24576
-constexpr unsigned long long kTcWaitNs = 1000000000ull;      // bounded waits: 1 s
+constexpr unsigned long long kTcWaitNs = 1000000000ull;      // bound of the drain waits: 1 s
+
+// A wait of the pipeline with the shell's bound; a bound of 0 gives up at
+// once without polling (the way callers exercise the timeout path).
+__device__ __forceinline__ bool pipe_wait(uint64_t* b, unsigned parity, unsigned long long limit_ns) {
+  return limit_ns ? tc::bar_wait(b, parity, limit_ns) : false;
+}
 
 // Up to four operator applications with the same row-group size in one
 // launch (the projections of the spin classes); blockIdx.y = class * nm + m.
@@ -447,6 +453,7 @@ struct TcBatch {
   int nclass, nm;
   int eoff;  // added to every column exponent: a bound from an earlier scan times the operator gain
   int sum6;  // issue the digit-sum-6 pairs (derivatives); the filter's operators stop at digit sum 5
+  unsigned long long wait_ns;  // bound of every pipeline wait (the shell's setting; 0: give up at once)
 };
 
 template <int ROWS>
@@ -608,7 +615,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
 #pragma unroll
       for (int i = 0; i < KQ; ++i) cur[i] = nxt[i];
       if (ks + 1 < ksteps) gather<FI, KQ>(a, col, (ks + 1) * 16 + kq, nxt);
-      if (ks >= S && ok) ok = tc::bar_wait(&empty[s], ((ks - S) / S) & 1, kTcWaitNs);
+      if (ks >= S && ok) ok = pipe_wait(&empty[s], ((ks - S) / S) & 1, B.wait_ns);
       unsigned char* xs = smtc + s * C::kStage + xoff;
       uint32_t wd[kSlices][KQ / 2];
       if (FI && fscale && ks * 16 + kq < a.g.K) {
@@ -647,7 +654,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
       tc::fence_proxy_async();
       bar_arrive(&xfull[s]);
     }
-    if (ok) ok = tc::bar_wait(&accf, 0, kTcWaitNs);
+    if (ok) ok = pipe_wait(&accf, 0, B.wait_ns);
   } else if (tid == C::kProd) {
     // MMA thread
     const unsigned char* wsrc =
@@ -663,7 +670,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     int copied = S < ksteps ? S : ksteps;  // operator k-steps whose copy has been issued
     for (int ks = 0; ks < ksteps && ok; ++ks) {
       const int s = ks % S;
-      ok = tc::bar_wait(&wfull[s], (ks / S) & 1, kTcWaitNs) && tc::bar_wait(&xfull[s], (ks / S) & 1, kTcWaitNs);
+      ok = pipe_wait(&wfull[s], (ks / S) & 1, B.wait_ns) && pipe_wait(&xfull[s], (ks / S) & 1, B.wait_ns);
       if (!ok) break;
       tc::fence_after();
       const uint32_t xa = sbase + s * C::kStage;
@@ -694,7 +701,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
       // refill the stage of k-step ks - 1 with the operator of k-step ks - 1 + S
       if (ks >= 1 && copied < ksteps) {
         const int sp = (ks - 1) % S;
-        ok = tc::bar_wait(&empty[sp], ((ks - 1) / S) & 1, kTcWaitNs);
+        ok = pipe_wait(&empty[sp], ((ks - 1) / S) & 1, B.wait_ns);
         if (!ok) break;
         tc::bar_expect_tx(&wfull[sp], wcopy);
         tc::bulk_g2s(smtc + sp * C::kStage + kTcXBytes, wsrc + (size_t)copied * C::kWBytes, wcopy,
@@ -702,18 +709,19 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
         ++copied;
       }
     }
-    if (ok) tc::commit(&accf);
+    // accf completes once every MMA issued above has completed: then the
+    // accumulators are final, or, after a wait gave up, no MMA still reads
+    // shared memory or writes tensor memory
+    tc::commit(&accf);
     if (!ok) {
-      // let operator copies still in flight land before the CTA's memory goes
+      // let operator copies still in flight land, and the MMAs issued finish,
+      // before the CTA's memory goes (the long bound: these always end)
       for (int c = (copied > S ? copied - S : 0); c < copied; ++c) tc::bar_wait(&wfull[c % S], (c / S) & 1, kTcWaitNs);
+      tc::bar_wait(&accf, 0, kTcWaitNs);
     }
   }
   ok = __syncthreads_and(ok);
   if (!ok && tid == 0) atomicOr(flag, 2);
-  if (!ok && tid == C::kProd) {
-    // MMAs possibly still in flight: one more bounded wait on the last commit
-    tc::bar_wait(&empty[(ksteps - 1) % S], ((ksteps - 1) / S) & 1, kTcWaitNs);
-  }
   tc::fence_after();
   if (ok && producer) {
     // producer warp w reads TMEM lanes 32 (w % 4) .. + 31 (its columns) and
@@ -764,22 +772,25 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
 // Mixed path: one launch of the tcgen05 core over the classes of b (same row
 // group size, same input storage), grid = (max tiles x row groups,
 // classes x nm).
-static int launch_batch(const cffyn_shell* sh, const TcBatch& b, cudaStream_t st, int pairing, bool in_pairs,
-                        const int* exps) {
+static int launch_batch(const cffyn_shell* sh, const TcBatch& b0, cudaStream_t st, int pairing, bool in_pairs,
+                        const int* exps, int* flag = nullptr) {
+  if (!flag) flag = sh->flag;
+  TcBatch b = b0;
+  b.wait_ns = sh->tc_wait_ns;
   long long gx = 0;
   for (int c = 0; c < b.nclass; ++c) gx = std::max(gx, b.tiles[c] * b.W[c].ngroups);
   if (gx == 0) return CFFYN_OK;
   const dim3 grid((unsigned)gx, (unsigned)(b.nclass * b.nm));
   if (b.W[0].rows == 48) {
     if (in_pairs)
-      k_op_tc<true, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, sh->flag);
+      k_op_tc<true, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, flag);
     else
-      k_op_tc<false, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, sh->flag);
+      k_op_tc<false, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, flag);
   } else {
     if (in_pairs)
-      k_op_tc<true, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, sh->flag);
+      k_op_tc<true, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, flag);
     else
-      k_op_tc<false, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, sh->flag);
+      k_op_tc<false, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, flag);
   }
   count_launch();
   CF_CUDA(cudaGetLastError());
@@ -788,10 +799,11 @@ static int launch_batch(const cffyn_shell* sh, const TcBatch& b, cudaStream_t st
 
 // FP64 core, or on the mixed path the tcgen05 core with the per-field
 // exponents of the input at exps (op_prepare fills sh->exps); in_pairs: the
-// input is pair-stored.  Mixed-path outputs are pair-stored.
+// input is pair-stored.  Mixed-path outputs are pair-stored.  flag: the
+// status word a timed-out wait of the tcgen05 core marks (sh->flag if NULL).
 static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, const TcOp* Wt, dim3 extra,
                   cudaStream_t st, int pairing, bool in_pairs, const int* exps = nullptr, int eoff = 0,
-                  int sum6 = 1) {
+                  int sum6 = 1, int* flag = nullptr) {
   if (a.g.ncols <= 0) return CFFYN_OK;
   if (sh->d.precision == CFFYN_FP64 || Wt == nullptr) {
     unsigned gx = (unsigned)((a.g.ncols + F64_QT - 1) / F64_QT);
@@ -811,7 +823,7 @@ static int launch(const cffyn_shell* sh, const OpArgs& a, const double* W64, con
   b.nm = (int)extra.y;
   b.eoff = eoff;
   b.sum6 = sum6;
-  return launch_batch(sh, b, st, pairing, in_pairs, exps ? exps : sh->exps);
+  return launch_batch(sh, b, st, pairing, in_pairs, exps ? exps : sh->exps, flag);
 }
 
 int set_op_smem_limits() {
@@ -1081,10 +1093,13 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
 
 // Spherical derivatives of nf fields (FP64 input) into D = [3][nf][P], with the
 // mixed path's per-field exponents (64 ints) at exps instead of the shell's
-// workspace; exps is zeroed here on st (its words are atomicMax targets).  The
-// FP64 path does not use it.  Same kernels and arithmetic as op_prepare
-// followed by op_deriv_r / op_deriv_theta / op_deriv_phi.
-int op_derivs_at(const cffyn_shell* sh, const double* u, double* D, int nf, int* exps, cudaStream_t st) {
+// workspace; exps is zeroed here on st (its words are atomicMax targets).
+// A timed-out wait of the tcgen05 core sets bit 2 of *flag (not of the
+// shell's own status word).  The FP64 path uses neither.  Same kernels and
+// arithmetic as op_prepare followed by op_deriv_r / op_deriv_theta /
+// op_deriv_phi.
+int op_derivs_at(const cffyn_shell* sh, const double* u, double* D, int nf, int* exps, int* flag,
+                 cudaStream_t st) {
   const long long P = (long long)sh->P;
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   int rc;
@@ -1093,7 +1108,7 @@ int op_derivs_at(const cffyn_shell* sh, const double* u, double* D, int nf, int*
   const TcOp* Wt[3] = {&sh->tDr, &sh->tDth2, &sh->tDph};
   for (int i = 0; i < 3; ++i)
     if ((rc = launch(sh, deriv_args(sh, i, u, D + i * nf * P, nf), W64[i], Wt[i], dim3(1, 1), st, 0, false,
-                     exps)))
+                     exps, 0, 1, flag)))
       return rc;
   return CFFYN_OK;
 }

@@ -593,11 +593,19 @@ __global__ void __launch_bounds__(128, 6) k_reconstruct(const double* __restrict
 // arithmetic; D and out in the given storages).  Setup and API paths only.
 // One thread per point: the Jacobian (FP64 divisions) is formed once and
 // applied to every field, whose values are coalesced across the threads.
+// status (may be NULL): a status word of the operator launches that produced
+// D; if it is non-zero (a timed-out wait) every output value is a NaN.
 template <bool FI, bool FO>
-__global__ void k_cart(const double* __restrict__ D, double* __restrict__ out, int nf, Geo geo) {
+__global__ void k_cart(const double* __restrict__ D, double* __restrict__ out, int nf, Geo geo,
+                       const int* __restrict__ status) {
   const long long P = geo.P;
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= P) return;
+  if (status && *status) {
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    for (int e = 0; e < 3 * nf; ++e) Store<double, FO>::st(out, (long long)e * P + p, qnan);
+    return;
+  }
   const int k = (int)(p % geo.n_r);
   const int i = (int)((p / geo.n_r) % geo.N);
   const int jj = (int)(p / ((long long)geo.n_r * geo.N));
@@ -739,27 +747,32 @@ int pw_reconstruct(const cffyn_shell* sh, const double* sp, double* dst, int mod
   return CFFYN_OK;
 }
 
-// D: internal storage; out_pairs: out is an internal buffer
-int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, bool out_pairs, cudaStream_t st) {
+// D: internal storage; out_pairs: out is an internal buffer; status: see k_cart
+int pw_cart_status(const cffyn_shell* sh, const double* D, double* out, int nf, bool out_pairs,
+                   const int* status, cudaStream_t st) {
   Geo g = geo_of(sh);
   const bool in_pairs = sh->d.precision == CFFYN_MIXED;
   const unsigned nb = blocks_for(g.P, 256);
   if (in_pairs && out_pairs)
-    k_cart<true, true><<<nb, 256, 0, st>>>(D, out, nf, g);
+    k_cart<true, true><<<nb, 256, 0, st>>>(D, out, nf, g, status);
   else if (in_pairs)
-    k_cart<true, false><<<nb, 256, 0, st>>>(D, out, nf, g);
+    k_cart<true, false><<<nb, 256, 0, st>>>(D, out, nf, g, status);
   else
-    k_cart<false, false><<<nb, 256, 0, st>>>(D, out, nf, g);
+    k_cart<false, false><<<nb, 256, 0, st>>>(D, out, nf, g, status);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
+}
+
+int pw_cart(const cffyn_shell* sh, const double* D, double* out, int nf, bool out_pairs, cudaStream_t st) {
+  return pw_cart_status(sh, D, out, nf, out_pairs, nullptr, st);
 }
 
 // FP64 spherical derivatives D (not internal storage) -> FP64 Cartesian out,
 // on either path (the FFT derivative path writes FP64 into the workspace)
 int pw_cart_fp64(const cffyn_shell* sh, const double* D, double* out, int nf, cudaStream_t st) {
   Geo g = geo_of(sh);
-  k_cart<false, false><<<blocks_for(g.P, 256), 256, 0, st>>>(D, out, nf, g);
+  k_cart<false, false><<<blocks_for(g.P, 256), 256, 0, st>>>(D, out, nf, g, nullptr);
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;

@@ -1,18 +1,18 @@
-// cffyn_derivs_static: the Cartesian derivatives of cffyn_derivs (Secs.
-// 2.3-2.4, chain rule eq. dvdx) for the first n_f fields, with every
-// intermediate in one fixed array of the library's own device memory instead
-// of the shell's workspace or a new allocation.  The paper has no counterpart;
-// this is a library facility for callers that cannot allocate at the point of
-// the call (see include/cffyn.h).
+// cffyn_derivs_static: a variant of cffyn_derivs (the Cartesian derivatives)
+// for the first n_f fields, with every intermediate in one fixed array of the
+// library's own device memory instead of the shell's workspace or a new
+// allocation.  The paper has no counterpart; this is a library facility for
+// callers that cannot allocate at the point of the call (see
+// include/cffyn.h).
 #include <mutex>
 
 #include "common.cuh"
 
 namespace cffyn {
 // ops.cu
-int op_derivs_at(const cffyn_shell*, const double*, double*, int, int*, cudaStream_t);
+int op_derivs_at(const cffyn_shell*, const double*, double*, int, int*, int*, cudaStream_t);
 // pointwise.cu
-int pw_cart(const cffyn_shell*, const double*, double*, int, bool, cudaStream_t);
+int pw_cart_status(const cffyn_shell*, const double*, double*, int, bool, const int*, cudaStream_t);
 }  // namespace cffyn
 
 using namespace cffyn;
@@ -21,8 +21,11 @@ namespace {
 
 // One array per device, reserved when the module's device code is loaded
 // there.  Layout of one call: spherical derivatives [3][n_f][P] (8 bytes per
-// value on both paths), then on the mixed path the 64 per-field exponent
-// words, 256-byte aligned.
+// value on both paths), then on the mixed path one 256-byte block of 64
+// words, 256-byte aligned: words 0..n_f-1 the per-field exponents (n_f <= 58),
+// word 63 the call's own status word (a timed-out wait of the tensor-core
+// kernel sets it; the chain-rule kernel then writes NaN).  All 64 words are
+// zeroed at the start of every call.
 __device__ __align__(256) unsigned char g_static_scratch[CFFYN_STATIC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
@@ -91,7 +94,8 @@ extern "C" int cffyn_derivs_static(const cffyn_shell* sh, const double* u, int n
   if ((rc = scratch_address(dev, &base))) return rc;
   double* D = reinterpret_cast<double*>(base);
   int* exps = mixed ? reinterpret_cast<int*>(base + d_bytes) : nullptr;
+  int* status = mixed ? exps + 63 : nullptr;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = op_derivs_at(sh, u, D, n_f, exps, st))) return rc;
-  return pw_cart(sh, D, dxyz, n_f, false, st);
+  if ((rc = op_derivs_at(sh, u, D, n_f, exps, status, st))) return rc;
+  return pw_cart_status(sh, D, dxyz, n_f, false, status, st);
 }

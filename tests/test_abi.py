@@ -67,6 +67,8 @@ def test_null_handles_are_rejected(lib):
     assert lib.cffyn_create_shell_ex(None, None) == cffyn.EINVAL
     assert lib.cffyn_derivs_fft(None, None, None, None) == cffyn.EINVAL
     assert b"NULL" in lib.cffyn_last_error()
+    assert lib.cffyn_set_wait_limit(None, 1.0) == cffyn.EINVAL
+    assert b"NULL" in lib.cffyn_last_error()
 
 
 def test_static_scratch_limit_and_null_shell(lib):

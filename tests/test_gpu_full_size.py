@@ -64,7 +64,10 @@ def test_full_size_operators_and_rhs(cf, c):
     if nf == 50:
         rs.init_gauge_from_state(u0)
     du = rs.derivs(u0)                                   # [3, nf, J, N, n_r]
-    ks = [0, n_r // 2, n_r - 1]                          # sampled radii, the outer one last
+    # sampled radii: the inner sphere and its neighbour (smallest r, so the
+    # largest 1/(r sin theta) of the chain rule on the theta rows next to
+    # the poles), the middle one, and the outer one with its BC, last
+    ks = [0, 1, n_r // 2, n_r - 1]
     u_s = np.ascontiguousarray(u0[..., ks])
     du_s = np.ascontiguousarray(du[..., ks])
     H, dH = (rs.H[..., ks], rs.dH[..., ks]) if nf == 50 else (u_s[50:54], du_s[:, 50:54])
@@ -95,6 +98,9 @@ def test_full_size_operators_and_rhs(cf, c):
         sh.rhs(u, r)
         got = r.cpu().numpy()[..., ks]
         errs[("rhs", prec)] = float(np.abs(got - rhs_ref).max() / scale)
+        # the theta rows next to the poles (i = 0, N - 1) on their own
+        pole = np.abs(got - rhs_ref)[:, :, [0, N - 1], :]
+        errs[("rhs_pole_rows", prec)] = float(pole.max() / scale)
         sh.filter(u, r)
         got = r.cpu().numpy()[..., ks]
         errs[("filter", prec)] = float(rel_rows(got, filt_ref))

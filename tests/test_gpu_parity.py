@@ -92,6 +92,27 @@ def test_filter(cf, prec, n_r, N, J, L):
     assert e < TOL[prec], e
 
 
+@pytest.mark.parametrize("nf", [50, 58])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("n_r,N,J", [(13, 9, 18), (9, 12, 24)])
+@pytest.mark.parametrize("which", ["0", "1", "2", "N-1"])
+def test_filter_edge_degrees(cf, which, n_r, N, J, prec, nf):
+    # L < 3: the spin-3 class keeps no mode (l >= |n|, App. B) and the spin-2
+    # class keeps none (L < 2) or only l = 2; L = N - 1: only what the
+    # grid cannot resolve (the phi Nyquist mode, the projection's null space).
+    # Odd and even N; the 58-field state adds the gauge groups' slots.
+    L = N - 1 if which == "N-1" else int(which)
+    u0 = inputs.band_limited_fields(n_r, N, J, 1.8, 11.0, n_fields=nf, seed=40 + L)
+    ref = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L, n_fields=nf).filter(u0)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, n_fields=nf, precision=prec)
+    out = torch.empty_like(dev(u0))
+    sh.filter(dev(u0), out)
+    got = out.cpu().numpy()
+    sh.destroy()
+    e = rel(got, ref, axis=0)
+    assert e < TOL[prec], e
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n_r,N,J,L", SHAPES)
 def test_rhs_with_boundary(cf, prec, n_r, N, J, L):

@@ -13,7 +13,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-12, 1: 1e-10}   # FP64, MIXED
-SHAPES = [(9, 12, 24, 10), (13, 9, 18, 6), (33, 32, 64, 30), (9, 12, 24, 9)]
+SHAPES = [(9, 12, 24, 10), (13, 9, 18, 6), (33, 32, 64, 30), (9, 12, 24, 9), (9, 12, 24, 0),
+          (13, 9, 18, 1), (13, 9, 18, 8)]
 KINDS = {"y": 1, "yg": 2}
 
 
@@ -41,7 +42,8 @@ def rel_rows(got, ref):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("n_r,N,J,L", SHAPES)
 def test_filter(cf, kind, prec, n_r, N, J, L):
-    # (9, 12, 24, 9): L + 3 > N - 1, the graded degrees are capped
+    # (9, 12, 24, 9): L + 3 > N - 1, the graded degrees are capped;
+    # L = 0, 1: below every field's spatial degree; (13, 9, 18, 8): L = N - 1
     u0 = inputs.band_limited_fields(n_r, N, J, 1.8, 11.0, seed=31)
     ref = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L, filter_kind=kind).filter(u0)
     sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=prec, filter_kind=KINDS[kind])

@@ -78,3 +78,34 @@ def test_static_derivs_reject_requests_above_the_limit(cf, prec, n_ok):
     with pytest.raises(cf.CffynError):
         sh.derivs_static(u, 0, out)
     sh.destroy()
+
+
+def test_static_derivs_beside_a_step_of_the_same_shell(cf):
+    # the static call reads only the shell's constant operators and keeps its
+    # own status word: enqueued on a second stream while an RK4 step of the
+    # same shell runs on a first one, both results equal their serial ones
+    n_r, N, J, L = 9, 12, 24, 10
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L)
+    a = dev(inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-6, ell=2, seed=0))
+    sh.init_gauge_from_state(a)
+    v0 = inputs.band_limited_fields(n_r, N, J, 1.8, 11.0, seed=21)
+    v = dev(v0)
+    ref = torch.empty((3,) + v0.shape, dtype=torch.float64, device="cuda")
+    sh.derivs(v, ref)
+    b = a.clone()
+    sh.rk4_step(b, 0.0, 3)                    # serial step
+    got = torch.full((3, 50) + v0.shape[1:], float("nan"), dtype=torch.float64, device="cuda")
+    sh.derivs_static(v, 50, got)              # set-up call before the streams
+    torch.cuda.synchronize()
+    got.fill_(float("nan"))
+    c = a.clone()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    sh.derivs_static(v, 50, got, stream=s2)   # asynchronous: still running ...
+    sh.rk4_step(c, 0.0, 3, stream=s1)         # ... while the step runs (and syncs s1)
+    torch.cuda.synchronize()
+    assert torch.equal(c, b)
+    g = got.cpu().numpy()
+    assert np.isfinite(g).all()
+    assert rel(g, ref.cpu().numpy()) < TOL[1]
+    sh.destroy()
