@@ -218,6 +218,46 @@ CFFYN_API int cffyn_batch_rk4_step(cffyn_batch* b, double* const* u, const doubl
 /* Releases the batch (not its shells).  NULL is allowed. */
 CFFYN_API int cffyn_destroy_batch(cffyn_batch* b);
 
+/* Nested shells: n shells over consecutive radial intervals, shell i over
+ * [r_in_i, r_out_i] with r_out_i == r_in_{i+1} (to 1e-12 relative), sharing
+ * n_theta, L, n_fields, precision, filter mode and filter kind (n_r and the
+ * Courant factor may differ).  The domain decomposition the paper names as
+ * its next step (Secs. 1 and 5); the coupling is this library's reading of
+ * the characteristic analysis of App. A.2 (eq. characteristics): on every
+ * common sphere (the outer sphere of shell i is the inner sphere of shell
+ * i + 1) the right-hand sides are split into the characteristic fields
+ * w0 = g, w+ = -g + Pi + s^k Phi_k, w- = -g + Pi - s^k Phi_k and
+ * wT_i = Phi_i - s_i s^k Phi_k with the unit normal s_i of the sphere (the
+ * inner shell's metric); w- and wT, which App. A.2's outer condition freezes,
+ * come from the outer shell, w0 and w+ from the inner one, and both shells
+ * get the recombined right-hand side there (gauge fields: the inner
+ * shell's).  Only the outermost shell's outer sphere has the freeze-incoming
+ * condition.  The nest borrows the handles like a batch: they stay alive and
+ * unused by other calls while a nest call runs.  Synchronous.  CFFYN_EINVAL
+ * for mismatched or non-adjacent shells, duplicates, NULL. */
+typedef struct cffyn_nest cffyn_nest;
+CFFYN_API int cffyn_create_nest(int n, cffyn_shell* const* shells, cffyn_nest** out);
+
+/* Right-hand sides of every shell of the nest (host array of n device
+ * pointers each way, FP64, each shell's layout) with the coupling above; no
+ * filter.  Every 50-field shell needs its gauge. */
+CFFYN_API int cffyn_nest_rhs(cffyn_nest* ns, const double* const* u, double* const* dudt, void* stream);
+
+/* n_steps RK4 steps (Sec. 2.5) of all shells with one dt (dt <= 0: the
+ * smallest cffyn_default_dt of the shells), every stage coupling the
+ * right-hand sides on the common spheres before the shells' filters and
+ * stage updates; one CUDA graph per step, captured on the first call and
+ * replayed while u and dt stay the same.  Synchronises `stream`; returns
+ * CFFYN_ETIMEOUT / CFFYN_ENONFINITE as cffyn_rk4_step does, naming the
+ * shell.  The caller filters each shell's initial data once. */
+CFFYN_API int cffyn_nest_rk4_step(cffyn_nest* ns, double* const* u, double dt, int n_steps, void* stream);
+
+/* The smallest default dt of the nest's shells. */
+CFFYN_API double cffyn_nest_default_dt(const cffyn_nest* ns);
+
+/* Releases the nest (not its shells).  NULL is allowed. */
+CFFYN_API int cffyn_destroy_nest(cffyn_nest* ns);
+
 /* RMS over all points of C_iab = d_i g_ab - Phi_iab (30 components, numerical
  * derivative) and of C_a = H_a + Gamma_a (4 components) (App. A.1), reduced
  * in FP64 on the device; out[0] = C_iab RMS, out[1] = C_a RMS (host memory).

@@ -79,8 +79,9 @@ class OracleShell:
         return u[50:54], du[:, 50:54]
 
     # -- operators -----------------------------------------------------------
-    def rhs(self, u):
-        """Derivatives + GHG right-hand side + outer BC, no filter."""
+    def rhs(self, u, outer_bc=True):
+        """Derivatives + GHG right-hand side + outer BC (unless outer_bc is
+        False: the inner shells of a nested set), no filter."""
         du = self.derivs(u)
         H, dH = self._gauge(u, du)
         mu = u.shape[0]
@@ -90,6 +91,8 @@ class OracleShell:
                                 self.gamma0, self.gamma2)
         out = out.reshape(u.shape)
         del shp
+        if not outer_bc:
+            return out
         return ghg.apply_outer_bc(out, u, self.theta, self.phi)
 
     def sf_at(self, L_keep):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libcffyn.so")
-SOURCES = ["setup.cu", "ops.cu", "pointwise.cu", "rhs.cu", "api.cu", "static_scratch.cu", "batch.cu", "fft.cu"]
+SOURCES = ["setup.cu", "ops.cu", "pointwise.cu", "rhs.cu", "api.cu", "static_scratch.cu", "batch.cu", "fft.cu", "nest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-diag-suppress", "177"]

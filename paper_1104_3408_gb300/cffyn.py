@@ -28,6 +28,8 @@ EXPORTED = [
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
     "cffyn_set_wait_limit",
     "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch",
+    "cffyn_create_nest", "cffyn_nest_rhs", "cffyn_nest_rk4_step", "cffyn_nest_default_dt",
+    "cffyn_destroy_nest",
     "cffyn_workspace_size", "cffyn_attach_workspace", "cffyn_derivs_fft",
 ]
 PROFILE_PHASES = ["d_r", "d_theta_phi", "rhs_gamma", "rhs_quad", "rhs_pp", "decompose",
@@ -90,6 +92,11 @@ def load(path=LIB_PATH):
         "cffyn_create_batch": ([i, ctypes.POINTER(vp), ctypes.POINTER(vp)], i),
         "cffyn_batch_rk4_step": ([vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double), i, vp], i),
         "cffyn_destroy_batch": ([vp], i),
+        "cffyn_create_nest": ([i, ctypes.POINTER(vp), ctypes.POINTER(vp)], i),
+        "cffyn_nest_rhs": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
+        "cffyn_nest_rk4_step": ([vp, ctypes.POINTER(vp), d, i, vp], i),
+        "cffyn_nest_default_dt": ([vp], d),
+        "cffyn_destroy_nest": ([vp], i),
         "cffyn_last_error": ([], ctypes.c_char_p),
         "cffyn_version": ([], ctypes.c_char_p),
     }
@@ -283,6 +290,48 @@ class Batch:
     def destroy(self):
         if self.h:
             load().cffyn_destroy_batch(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Nest:
+    """Nested shells over consecutive radial intervals, coupled on their
+    common spheres (a cffyn_nest handle); borrows the Shell objects."""
+
+    def __init__(self, shells):
+        self.shells = list(shells)
+        arr = (ctypes.c_void_p * len(self.shells))(*[s.h.value for s in self.shells])
+        h = ctypes.c_void_p()
+        _check(load().cffyn_create_nest(len(self.shells), arr, ctypes.byref(h)))
+        self.h = h
+
+    def _ptrs(self, ts, what):
+        n = len(self.shells)
+        if len(ts) != n:
+            raise ValueError(f"{n} arrays expected for {what}")
+        return (ctypes.c_void_p * n)(*[_ptr(t, what).value for t in ts])
+
+    def default_dt(self):
+        return float(load().cffyn_nest_default_dt(self.h))
+
+    def rhs(self, us, outs, stream=None):
+        _check(load().cffyn_nest_rhs(self.h, self._ptrs(us, "u[i]"), self._ptrs(outs, "dudt[i]"),
+                                     _stream(stream)))
+        return outs
+
+    def rk4_step(self, us, dt=0.0, n_steps=1, stream=None):
+        _check(load().cffyn_nest_rk4_step(self.h, self._ptrs(us, "u[i]"), float(dt), int(n_steps),
+                                          _stream(stream)))
+        return us
+
+    def destroy(self):
+        if self.h:
+            load().cffyn_destroy_nest(self.h)
             self.h = ctypes.c_void_p()
 
     def __del__(self):

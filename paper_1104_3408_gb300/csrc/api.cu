@@ -479,86 +479,114 @@ int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* stream) {
 // The kernel groups of one RK4 step (Sec. 2.5) in order.  run(phase, fn)
 // enqueues fn() as part of `phase` (the groups of cffyn_profile_step; phase
 // 10 is the per-field exponent scan of the mixed path in front of each
-// operator group); tracing and profiling hooks live in run.
+// operator group); tracing and profiling hooks live in run.  A step is, for
+// every stage s = 0..3, stage_front (derivatives and right-hand side of the
+// stage state into sh->S) then stage_back (filter of the right-hand side and
+// the stage update), then step_tail (the filter of the new state in
+// per-step mode).  Nested shells run the fronts of all their shells, couple
+// the right-hand sides on the common spheres, then run the backs.
 extern "C++" {
+
+// the state that stage s reads: on the mixed path the pair copy Uf of the
+// step's initial state in stage 0 (cffyn_rk4_step fills it from u before the
+// first step and the last stage keeps it current) and the pair-stored stage
+// state U after it; on the FP64 path u, then U
+static const double* stage_state_of(const cffyn_shell* sh, const double* u, int s) {
+  const bool mixed = sh->d.precision == CFFYN_MIXED;
+  return s == 0 ? (mixed ? sh->Uf : u) : sh->U;
+}
+
+// filter of the functions in `spin` (in place through D and D + nvP): the
+// spin slots for Yn, the Cartesian fields for Y / Yg; one exponent scan per
+// filter (the coefficients and the projected ones take bounds: the scan's
+// exponents + the operators' gains)
 template <class Run>
-static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st, Run&& run) {
+static int filter_in_step(cffyn_shell* sh, double* spin, cudaStream_t st, Run&& run) {
   const size_t nvP = (size_t)sh->nv * sh->P;
-  const long long P = (long long)sh->P;
-  const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
-  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
-  int rc;
-  auto prep = [&](const double* in, bool pairs, long long len, int pairing) {
-    return run(10, [&] { return op_prepare(sh, in, pairs, sh->nv, len, pairing, st); });
-  };
-  // filter of the functions in `spin` (in place through D and D + nvP): the
-  // spin slots for Yn, the Cartesian fields for Y / Yg
   const bool yn = yn_filter(sh);
   const int pairing = yn ? 1 : 0;
-  // one exponent scan per filter: the coefficients and the projected ones
-  // take bounds (the scan's exponents + the operators' gains)
   const int e1 = sh->gain_dft, e2 = sh->gain_dft + sh->gain_proj;
-  auto filter = [&](double* spin) -> int {
-    int r;
-    if ((r = prep(spin, true, P, pairing))) return r;
-    if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st, pairing); }))) return r;
-    if ((r = run(7, [&] {
-           return yn ? op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st, e1)
-                     : op_project_scalar(sh, sh->D, sh->D + nvP, st, e1);
-         })))
-      return r;
-    return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st, pairing, e2); });
-  };
-  const bool mixed = sh->d.precision == CFFYN_MIXED;
-  for (int s = 0; s < 4; ++s) {
-    // mixed path: every stage reads pairs (the initial state from Uf, which
-    // cffyn_rk4_step fills from u before the first step and the last stage
-    // keeps current); FP64 path: u, then U
-    const double* X = s == 0 ? (mixed ? sh->Uf : u) : sh->U;
+  const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
+  int r;
+  if ((r = run(10, [&] { return op_prepare(sh, spin, true, sh->nv, (long long)sh->P, pairing, st); })))
+    return r;
+  if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st, pairing); }))) return r;
+  if ((r = run(7, [&] {
+         return yn ? op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st, e1)
+                   : op_project_scalar(sh, sh->D, sh->D + nvP, st, e1);
+       })))
+    return r;
+  return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st, pairing, e2); });
+}
+
+template <class Run>
+static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&& run) {
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  const long long P = (long long)sh->P;
+  const bool xp = sh->d.precision == CFFYN_MIXED;
+  const double* X = stage_state_of(sh, u, s);
+  int rc;
+  if ((rc = run(10, [&] { return op_prepare(sh, X, xp, sh->nv, P, 0, st); }))) return rc;
+  if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
+  if ((rc = run(1, [&] { return op_deriv_theta_phi(sh, X, sh->D + nvP, sh->D + 2 * nvP, sh->nv, xp, st); })))
+    return rc;
+  if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
+  if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
+  return run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); });
+}
+
+template <class Run>
+static int stage_back(cffyn_shell* sh, double* u, double dt, int s, cudaStream_t st, Run&& run) {
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
+  int rc;
+  if (per_sub && yn_filter(sh)) {
     double* spin = sh->D + 2 * nvP;  // derivatives are dead after the rhs
-    const bool xp = mixed;
-    if ((rc = prep(X, xp, P, 0))) return rc;
-    if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
-    if ((rc = run(1, [&] { return op_deriv_theta_phi(sh, X, sh->D + nvP, sh->D + 2 * nvP, sh->nv, xp, st); })))
-      return rc;
-    if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
-    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
-    if ((rc = run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); }))) return rc;
-    if (per_sub && yn) {
-      if ((rc = run(5, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
-      if ((rc = filter(spin))) return rc;
-      if ((rc = run(9, [&] {
-             return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
-           })))
-        return rc;
-    } else {
-      // unfiltered stage rhs (per-step placement), or the component-wise
-      // filter applied to the Cartesian rhs in place
-      if (per_sub && (rc = filter(sh->S))) return rc;
-      if ((rc = run(9, [&] {
-             return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
-           })))
-        return rc;
-    }
+    if ((rc = run(5, [&] { return pw_decompose(sh, sh->S, spin, true, st); }))) return rc;
+    if ((rc = filter_in_step(sh, spin, st, run))) return rc;
+    return run(9, [&] {
+      return pw_reconstruct(sh, spin, nullptr, 1 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
+    });
   }
-  if (!per_sub) {
-    if (yn) {
-      if ((rc = run(5, [&] { return pw_decompose(sh, mixed ? sh->Uf : u, sh->S, mixed, st); }))) return rc;
-    } else {
-      // the Cartesian state itself (pairs on the mixed path)
-      if ((rc = run(5, [&] {
-             CF_CUDA(cudaMemcpyAsync(sh->S, mixed ? sh->Uf : u, nvP * sizeof(double), cudaMemcpyDeviceToDevice, st));
-             return CFFYN_OK;
-           })))
-        return rc;
-    }
-    if ((rc = filter(sh->S))) return rc;
-    if ((rc = run(9, [&] {
-           return pw_reconstruct(sh, sh->S, u, yn ? 0 : 9, nullptr, nullptr, nullptr, sh->Uf, 0.0, sh->flag, st);
+  // unfiltered stage rhs (per-step placement), or the component-wise filter
+  // applied to the Cartesian rhs in place
+  if (per_sub && (rc = filter_in_step(sh, sh->S, st, run))) return rc;
+  return run(9, [&] {
+    return pw_reconstruct(sh, sh->S, nullptr, 5 + s, u, sh->U, sh->kacc, sh->Uf, dt, sh->flag, st);
+  });
+}
+
+template <class Run>
+static int step_tail(cffyn_shell* sh, double* u, cudaStream_t st, Run&& run) {
+  if (sh->d.filter_mode == CFFYN_FILTER_SUBSTEP) return CFFYN_OK;
+  const size_t nvP = (size_t)sh->nv * sh->P;
+  const bool mixed = sh->d.precision == CFFYN_MIXED;
+  const bool yn = yn_filter(sh);
+  int rc;
+  if (yn) {
+    if ((rc = run(5, [&] { return pw_decompose(sh, mixed ? sh->Uf : u, sh->S, mixed, st); }))) return rc;
+  } else {
+    // the Cartesian state itself (pairs on the mixed path)
+    if ((rc = run(5, [&] {
+           CF_CUDA(cudaMemcpyAsync(sh->S, mixed ? sh->Uf : u, nvP * sizeof(double), cudaMemcpyDeviceToDevice, st));
+           return CFFYN_OK;
          })))
       return rc;
   }
-  return CFFYN_OK;
+  if ((rc = filter_in_step(sh, sh->S, st, run))) return rc;
+  return run(9, [&] {
+    return pw_reconstruct(sh, sh->S, u, yn ? 0 : 9, nullptr, nullptr, nullptr, sh->Uf, 0.0, sh->flag, st);
+  });
+}
+
+template <class Run>
+static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st, Run&& run) {
+  int rc;
+  for (int s = 0; s < 4; ++s) {
+    if ((rc = stage_front(sh, u, s, st, run))) return rc;
+    if ((rc = stage_back(sh, u, dt, s, st, run))) return rc;
+  }
+  return step_tail(sh, u, st, run);
 }
 }  // extern "C++"
 
@@ -600,6 +628,31 @@ namespace cffyn {
 int enqueue_step_branch(cffyn_shell* sh, double* u, double dt, cudaStream_t st) {
   auto run = [](int, auto&& fn) -> int { return fn(); };
   return step_sequence(sh, u, dt, st, run);
+}
+
+// The pieces of a step for nested shells (no trace marks): stage s's
+// derivatives and right-hand side into sh->S, its filter and update, and
+// the per-step filter after the last stage.
+int enqueue_stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st) {
+  auto run = [](int, auto&& fn) -> int { return fn(); };
+  return stage_front(sh, u, s, st, run);
+}
+int enqueue_stage_back(cffyn_shell* sh, double* u, double dt, int s, cudaStream_t st) {
+  auto run = [](int, auto&& fn) -> int { return fn(); };
+  return stage_back(sh, u, dt, s, st, run);
+}
+int enqueue_step_tail(cffyn_shell* sh, double* u, cudaStream_t st) {
+  auto run = [](int, auto&& fn) -> int { return fn(); };
+  return step_tail(sh, u, st, run);
+}
+const double* stage_state(const cffyn_shell* sh, const double* u, int s) { return stage_state_of(sh, u, s); }
+
+// Derivatives and right-hand side (with the outer boundary condition) of an
+// FP64 state u into the FP64 array dudt, as cffyn_rhs does.
+int enqueue_rhs(cffyn_shell* sh, const double* u, double* dudt, cudaStream_t st) {
+  int rc;
+  if ((rc = derivs_spherical(sh, u, sh->D, sh->nv, false, st))) return rc;
+  return pw_rhs(sh, u, sh->D, dudt, st);
 }
 
 // Work in front of the first step of a call: clear the finiteness flag and,

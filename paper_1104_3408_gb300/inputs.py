@@ -64,8 +64,11 @@ def _cartesian(n_r, n_theta, n_phi, r_in, r_out):
 
 
 def kerr_schild_state(n_r, n_theta, n_phi, r_in=1.8, r_out=11.0, n_fields=50,
-                      amp=0.0, ell=2, seed=0, mass=1.0):
-    """Perturbed Kerr-Schild GHG state u[n_fields, n_phi, n_theta, n_r]."""
+                      amp=0.0, ell=2, seed=0, mass=1.0, center=None, width=None):
+    """Perturbed Kerr-Schild GHG state u[n_fields, n_phi, n_theta, n_r].
+    center / width (default: the shell's mid radius and an eighth of its
+    thickness) place the Gaussian of the perturbation, so that shells that
+    share a sphere can sample one perturbation."""
     X, R = _cartesian(n_r, n_theta, n_phi, r_in, r_out)
     shp = R.shape
     f = 2.0 * mass / R
@@ -86,8 +89,8 @@ def kerr_schild_state(n_r, n_theta, n_phi, r_in=1.8, r_out=11.0, n_fields=50,
                                + f * lvec[a] * dl[i, b])
     if amp != 0.0:
         rng = np.random.default_rng(seed)
-        rc = 0.5 * (r_in + r_out)
-        w = (r_out - r_in) / 8.0
+        rc = 0.5 * (r_in + r_out) if center is None else float(center)
+        w = (r_out - r_in) / 8.0 if width is None else float(width)
         G = np.exp(-((R - rc) / w) ** 2)
         dG = -2.0 * (R - rc) / w ** 2 * G
         monos = [a for a in itertools.product(range(ell + 1), repeat=3) if sum(a) <= ell]

@@ -69,6 +69,10 @@ def test_null_handles_are_rejected(lib):
     assert b"NULL" in lib.cffyn_last_error()
     assert lib.cffyn_set_wait_limit(None, 1.0) == cffyn.EINVAL
     assert b"NULL" in lib.cffyn_last_error()
+    assert lib.cffyn_create_nest(2, None, None) == cffyn.EINVAL
+    assert lib.cffyn_nest_rhs(None, None, None, None) == cffyn.EINVAL
+    assert lib.cffyn_nest_rk4_step(None, None, 0.1, 1, None) == cffyn.EINVAL
+    assert lib.cffyn_destroy_nest(None) == cffyn.OK
 
 
 def test_static_scratch_limit_and_null_shell(lib):
