@@ -192,26 +192,40 @@ CFFYN_API int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps,
 
 /* Batch of independent shells advanced together (the uneven-shell batch;
  * the shells need not share sizes, field counts, precision or filter mode).
- * The batch borrows the handles: they must stay alive, on the device that
- * is current at cffyn_create_batch, until cffyn_destroy_batch, and must not
- * be used by other calls while a batch call runs.  A shell may appear in one
- * batch position only (its workspace is per handle): duplicates are
- * CFFYN_EINVAL.  The batch owns only its streams, events, graphs and a
- * pinned flag array.  n >= 1. */
+ * Shells of one shape (n_r, n_theta, n_phi, r_in, r_out, L, n_fields,
+ * precision, filter mode and kind, Courant factor and wait bound) are
+ * stacked: the batch keeps one internal handle per such class whose every
+ * kernel covers all the class's shells in one launch (the operators see
+ * n_fields x shells fields, the pointwise kernels n_fields fields of
+ * shells x points), with its own workspace and stacked state; a class of one
+ * shell is stepped as itself.  The batch borrows the handles: they must stay
+ * alive, on the device that is current at cffyn_create_batch, until
+ * cffyn_destroy_batch, and must not be used by other calls while a batch
+ * call runs.  A shell may appear in one batch position only (duplicates are
+ * CFFYN_EINVAL).  The batch owns its stacked handles and states, streams,
+ * events, graphs and a pinned flag array.  n >= 1. */
 typedef struct cffyn_batch cffyn_batch;
 CFFYN_API int cffyn_create_batch(int n, cffyn_shell* const* shells, cffyn_batch** out);
+
+/* Number of independent branches of the batch's step graph: its shape
+ * classes (0 for NULL). */
+CFFYN_API int cffyn_batch_units(const cffyn_batch* b);
 
 /* n_steps RK4 steps (as cffyn_rk4_step, Sec. 2.5) of every shell of the
  * batch: u is a host array of n device state pointers (u[i] in the layout of
  * shells[i]); dt a host array of n step sizes (NULL, or an entry <= 0,
- * selects that shell's cffyn_default_dt).  One step of the whole batch is one
- * CUDA graph launch in which each shell's step is an independent branch, so
- * that small shells run side by side on the GPU; the graph is captured on
- * the first call and replayed while u and dt stay the same.  Every 50-field
- * shell needs its gauge (CFFYN_EINVAL before anything is enqueued
- * otherwise).  Synchronises `stream` at the end and returns
- * CFFYN_ETIMEOUT / CFFYN_ENONFINITE as cffyn_rk4_step does, naming the first
- * shell that reported it. */
+ * selects that shell's cffyn_default_dt); shells of one class must get one
+ * step size (CFFYN_EINVAL otherwise).  Every call copies the states (and,
+ * for 50 fields, the gauge sources) of stacked shells into their class,
+ * advances all classes, and copies the states back; one step of the whole
+ * batch is one CUDA graph launch in which each class is an independent
+ * branch; the graphs are captured on the first call and replayed while u and
+ * dt stay the same.  Results are bit-identical to stepping each shell
+ * alone.  Every 50-field shell needs its gauge (CFFYN_EINVAL before anything
+ * is enqueued otherwise).  Synchronises `stream` at the end and returns
+ * CFFYN_ETIMEOUT / CFFYN_ENONFINITE as cffyn_rk4_step does, naming the
+ * first shell of the class that reported it; a stacked class takes its first
+ * shell's wait bound. */
 CFFYN_API int cffyn_batch_rk4_step(cffyn_batch* b, double* const* u, const double* dt, int n_steps,
                                    void* stream);
 

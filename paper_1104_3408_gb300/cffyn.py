@@ -27,7 +27,7 @@ EXPORTED = [
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
     "cffyn_set_wait_limit",
-    "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch",
+    "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch", "cffyn_batch_units",
     "cffyn_create_nest", "cffyn_nest_rhs", "cffyn_nest_rk4_step", "cffyn_nest_default_dt",
     "cffyn_destroy_nest",
     "cffyn_workspace_size", "cffyn_attach_workspace", "cffyn_derivs_fft",
@@ -92,6 +92,7 @@ def load(path=LIB_PATH):
         "cffyn_create_batch": ([i, ctypes.POINTER(vp), ctypes.POINTER(vp)], i),
         "cffyn_batch_rk4_step": ([vp, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double), i, vp], i),
         "cffyn_destroy_batch": ([vp], i),
+        "cffyn_batch_units": ([vp], i),
         "cffyn_create_nest": ([i, ctypes.POINTER(vp), ctypes.POINTER(vp)], i),
         "cffyn_nest_rhs": ([vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp], i),
         "cffyn_nest_rk4_step": ([vp, ctypes.POINTER(vp), d, i, vp], i),
@@ -286,6 +287,10 @@ class Batch:
         dt_arr = None if dts is None else (ctypes.c_double * n)(*[float(d) for d in dts])
         _check(load().cffyn_batch_rk4_step(self.h, ptrs, dt_arr, int(n_steps), _stream(stream)))
         return us
+
+    def units(self):
+        """Independent branches of the step graph: the batch's shape classes."""
+        return int(load().cffyn_batch_units(self.h))
 
     def destroy(self):
         if self.h:

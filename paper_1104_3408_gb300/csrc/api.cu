@@ -83,7 +83,7 @@ int check_ptr(const void* p, const char* what) {
 // Workspace layout: U, kacc, D (three arrays), S, Rsrc and on the mixed path
 // Uf, each nv x P doubles rounded up to 256 bytes, in this order.
 size_t ws_array_bytes(const cffyn_shell* sh) {
-  return ((size_t)sh->nv * sh->P * sizeof(double) + 255) / 256 * 256;
+  return ((size_t)sh->nv * P_all(sh) * sizeof(double) + 255) / 256 * 256;
 }
 size_t ws_total_bytes(const cffyn_shell* sh) {
   return ws_array_bytes(sh) * (sh->d.precision == CFFYN_MIXED ? 8 : 7);
@@ -181,7 +181,25 @@ extern "C" {
 const char* cffyn_last_error(void) { return g_err; }
 const char* cffyn_version(void) { return "cffyn 0.1 (sm_103a)"; }
 
-int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
+static int create_shell(const cffyn_shell_desc* desc, int ns, cffyn_shell** out);
+
+int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) { return create_shell(desc, 1, out); }
+
+}  // extern "C"
+
+extern "C++" {
+namespace cffyn {
+// A handle of ns shells of one shape stacked as fields [mu][s][P] (the
+// uneven-shell batch's units; stepped with the single-shell step sequence).
+int create_stacked_shell(const cffyn_shell_desc* desc, int ns, cffyn_shell** out) {
+  return create_shell(desc, ns, out);
+}
+}  // namespace cffyn
+}  // extern "C++"
+
+extern "C" {
+
+static int create_shell(const cffyn_shell_desc* desc, int ns, cffyn_shell** out) {
   if (!out) {
     set_error("out is NULL");
     return CFFYN_EINVAL;
@@ -225,6 +243,7 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     return CFFYN_ENOMEM;
   }
   sh->d = d;
+  sh->ns = ns < 1 ? 1 : ns;
   sh->n_r = d.n_r;
   sh->N = d.n_theta;
   sh->J = d.n_phi;
@@ -265,12 +284,12 @@ int cffyn_create_shell_ex(const cffyn_shell_desc* desc, cffyn_shell** out) {
     sh->bytes += n * sizeof(double);
     return CFFYN_OK;
   };
-  if ((rc = alloc(&sh->H, 4 * sh->P)) || (rc = alloc(&sh->dH, (sh->nv == 58 ? 16 : 12) * sh->P)) ||
+  if ((rc = alloc(&sh->H, 4 * P_all(sh))) || (rc = alloc(&sh->dH, (sh->nv == 58 ? 16 : 12) * P_all(sh))) ||
       (rc = alloc(&sh->red, 2)) || (rc = alloc(&sh->triad, (size_t)9 * sh->N * sh->J)))
     return fail(rc);
   (void)nvP;
   if ((rc = pw_triad_table(sh))) return fail(rc);
-  if (d.precision == CFFYN_MIXED && cudaMalloc(&sh->exps, 64 * sizeof(int)) != cudaSuccess)
+  if (d.precision == CFFYN_MIXED && cudaMalloc(&sh->exps, std::max(64, nv_ops(sh)) * sizeof(int)) != cudaSuccess)
     return fail(CFFYN_ENOMEM);
   sh->ws_bytes = ws_total_bytes(sh);
   if (!(d.flags & CFFYN_DEFER_WORKSPACE)) {
@@ -502,33 +521,35 @@ static const double* stage_state_of(const cffyn_shell* sh, const double* u, int 
 // exponents + the operators' gains)
 template <class Run>
 static int filter_in_step(cffyn_shell* sh, double* spin, cudaStream_t st, Run&& run) {
-  const size_t nvP = (size_t)sh->nv * sh->P;
+  const size_t nvP = (size_t)sh->nv * P_all(sh);
+  const int nf = nv_ops(sh);
   const bool yn = yn_filter(sh);
   const int pairing = yn ? 1 : 0;
   const int e1 = sh->gain_dft, e2 = sh->gain_dft + sh->gain_proj;
   const int* cl[3] = {slots_c(sh, 0), slots_c(sh, 1), slots_c(sh, 2)};
   int r;
-  if ((r = run(10, [&] { return op_prepare(sh, spin, true, sh->nv, (long long)sh->P, pairing, st); })))
+  if ((r = run(10, [&] { return op_prepare(sh, spin, true, nf, (long long)sh->P, pairing, st); })))
     return r;
-  if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, sh->nv, st, pairing); }))) return r;
+  if ((r = run(6, [&] { return op_dft_fwd(sh, spin, sh->D, nf, st, pairing); }))) return r;
   if ((r = run(7, [&] {
          return yn ? op_project(sh, sh->D, sh->D + nvP, slots_r0(sh), sh->nR0, cl, sh->nC, st, e1)
                    : op_project_scalar(sh, sh->D, sh->D + nvP, st, e1);
        })))
     return r;
-  return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, sh->nv, st, pairing, e2); });
+  return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, nf, st, pairing, e2); });
 }
 
 template <class Run>
 static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&& run) {
-  const size_t nvP = (size_t)sh->nv * sh->P;
+  const size_t nvP = (size_t)sh->nv * P_all(sh);
   const long long P = (long long)sh->P;
+  const int nf = nv_ops(sh);
   const bool xp = sh->d.precision == CFFYN_MIXED;
   const double* X = stage_state_of(sh, u, s);
   int rc;
-  if ((rc = run(10, [&] { return op_prepare(sh, X, xp, sh->nv, P, 0, st); }))) return rc;
-  if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, sh->nv, xp, st); }))) return rc;
-  if ((rc = run(1, [&] { return op_deriv_theta_phi(sh, X, sh->D + nvP, sh->D + 2 * nvP, sh->nv, xp, st); })))
+  if ((rc = run(10, [&] { return op_prepare(sh, X, xp, nf, P, 0, st); }))) return rc;
+  if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, nf, xp, st); }))) return rc;
+  if ((rc = run(1, [&] { return op_deriv_theta_phi(sh, X, sh->D + nvP, sh->D + 2 * nvP, nf, xp, st); })))
     return rc;
   if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
   if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
@@ -537,7 +558,7 @@ static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&&
 
 template <class Run>
 static int stage_back(cffyn_shell* sh, double* u, double dt, int s, cudaStream_t st, Run&& run) {
-  const size_t nvP = (size_t)sh->nv * sh->P;
+  const size_t nvP = (size_t)sh->nv * P_all(sh);
   const bool per_sub = sh->d.filter_mode == CFFYN_FILTER_SUBSTEP;
   int rc;
   if (per_sub && yn_filter(sh)) {
@@ -559,7 +580,7 @@ static int stage_back(cffyn_shell* sh, double* u, double dt, int s, cudaStream_t
 template <class Run>
 static int step_tail(cffyn_shell* sh, double* u, cudaStream_t st, Run&& run) {
   if (sh->d.filter_mode == CFFYN_FILTER_SUBSTEP) return CFFYN_OK;
-  const size_t nvP = (size_t)sh->nv * sh->P;
+  const size_t nvP = (size_t)sh->nv * P_all(sh);
   const bool mixed = sh->d.precision == CFFYN_MIXED;
   const bool yn = yn_filter(sh);
   int rc;
@@ -660,7 +681,7 @@ int enqueue_rhs(cffyn_shell* sh, const double* u, double* dudt, cudaStream_t st)
 // stage of every step keeps Uf current afterwards).
 int enqueue_step_prologue(cffyn_shell* sh, double* u, cudaStream_t st) {
   CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
-  if (sh->Uf) return pw_to_internal(sh, u, sh->Uf, (long long)sh->nv * sh->P, st);
+  if (sh->Uf) return pw_to_internal(sh, u, sh->Uf, (long long)sh->nv * (long long)P_all(sh), st);
   return CFFYN_OK;
 }
 

@@ -59,7 +59,11 @@ struct cffyn_shell {
   cffyn_shell_desc d;
   int n_r, N, J, L, nv, R;      // R = 2 Lrows + 1 Fourier rows kept
   int Lrows;                    // azimuthal modes kept by the phi DFT: L, or L + 3 (at most N - 1) for Yg
-  size_t P;                     // points per field
+  size_t P;                     // points per field of one shell
+  int ns = 1;                   // shells stacked in this handle (the uneven-shell batch stacks
+                                // shells of one shape: fields [mu][s][P], so that the operators
+                                // see nv * ns fields of P points and the pointwise kernels nv
+                                // fields of ns * P points)
   double dt_default;
   size_t bytes = 0;
   int device = 0;
@@ -153,4 +157,7 @@ struct cffyn_shell {
 namespace cffyn {
 // fft.cu: frees the FFT derivative path's plans and scratch (no-op without)
 void fft_release(cffyn_shell*);
+// fields the operators see (nv per stacked shell) and points of every array
+inline int nv_ops(const cffyn_shell* sh) { return sh->nv * sh->ns; }
+inline size_t P_all(const cffyn_shell* sh) { return sh->P * (size_t)sh->ns; }
 }  // namespace cffyn

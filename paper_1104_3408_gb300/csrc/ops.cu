@@ -63,6 +63,7 @@ struct OpArgs {
   int nslots;
   int batched_m;         // projection launched for all m = 0..L at once
   long long w_stride;    // FP64 operator stride between consecutive m
+  int ns;                // stacked shells: function f of shell s is array f * ns + s
 };
 
 __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
@@ -100,14 +101,16 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
       break;
     }
     case OP_PROJ0: {
-      // columns: (slot index, part, kr); parts: a (row m) and b (row L+m, m >= 1)
+      // columns: (slot index, stacked shell, part, kr); parts: a (row m) and
+      // b (row L+m, m >= 1)
       int nparts = a.m == 0 ? 1 : 2;
       long long per = (long long)nparts * a.n_r;
-      if (c >= per * a.nslots) { d.valid = 0; c = 0; }
+      if (c >= per * a.nslots * a.ns) { d.valid = 0; c = 0; }
       long long fi = c / per;
       int rem = (int)(c - fi * per);
       int part = rem / a.n_r, kr = rem - part * a.n_r;
-      int f = a.slots[fi < a.nslots ? fi : 0];
+      const long long fs = fi / a.ns;
+      int f = a.slots[fs < a.nslots ? fs : 0] * a.ns + (int)(fi - fs * a.ns);
       d.fld = f;
       int row = part == 0 ? a.m : a.L + a.m;
       d.in0 = (((long long)f * a.R + row) * a.N) * a.n_r + kr;
@@ -116,14 +119,16 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
       break;
     }
     case OP_PROJC: {
-      // columns: (pair, output part, kr); parts aR, aI, bR, bI (m >= 1) or aR, aI
+      // columns: (pair, stacked shell, output part, kr); parts aR, aI, bR, bI
+      // (m >= 1) or aR, aI
       int nparts = a.m == 0 ? 2 : 4;
       long long per = (long long)nparts * a.n_r;
-      if (c >= per * a.nslots) { d.valid = 0; c = 0; }
+      if (c >= per * a.nslots * a.ns) { d.valid = 0; c = 0; }
       long long pi = c / per;
       int rem = (int)(c - pi * per);
       int part = rem / a.n_r, kr = rem - part * a.n_r;
-      int fre = a.slots[pi < a.nslots ? pi : 0], fim = fre + 1;
+      const long long ps = pi / a.ns;
+      int fre = a.slots[ps < a.nslots ? ps : 0] * a.ns + (int)(pi - ps * a.ns), fim = fre + a.ns;
       d.fld = fre;
       int ra = a.m, rb = a.L + a.m;
       auto base = [&](int f, int row) {
@@ -583,7 +588,11 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
   const int kq = (tid >> 7) * KQ;               // first k of this producer within a k-step
   const ColDesc col = make_col(a, tile * kTcCols + ctile);
   int ce = exps[col.fld];
-  if (pairing && col.fld >= kPairedFrom) ce = max(ce, exps[col.fld ^ 1]);
+  if (pairing) {
+    // slot pairs (f, f ^ 1), f >= kPairedFrom, of the same stacked shell
+    const int f = col.fld / a.ns, sidx = col.fld - f * a.ns;
+    if (f >= kPairedFrom) ce = max(ce, exps[(f ^ 1) * a.ns + sidx]);
+  }
   const int E = ce - 1022 + B.eoff;
   if (tid < ROWS) rowF[tid] = pow2f(W.rowexp[grp * ROWS + tid]);
   if (tid == 0) {
@@ -835,10 +844,10 @@ int set_op_smem_limits() {
   return CFFYN_OK;
 }
 
-// Per-field exponents of nf fields of len values each into exps (64 words,
-// zeroed here: they are atomicMax targets); in_pairs: pair-stored input.
+// Per-field exponents of nf fields of len values each into exps (max(nf, 64)
+// words, zeroed here: they are atomicMax targets); in_pairs: pair-stored input.
 static int field_exps(const double* in, bool in_pairs, int nf, long long len, int* exps, cudaStream_t st) {
-  CF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * 64, st));
+  CF_CUDA(cudaMemsetAsync(exps, 0, sizeof(int) * std::max(nf, 64), st));
   const long long* x = reinterpret_cast<const long long*>(in);
   const unsigned bx = (unsigned)((len + kExpThreads * kExpPerThread - 1) / (kExpThreads * kExpPerThread));
   if (in_pairs)
@@ -867,6 +876,7 @@ static OpArgs base_args(const cffyn_shell* sh) {
   a.J = sh->J;
   a.R = sh->R;
   a.L = sh->Lrows;  // row of b_1 minus 1 in the DFT coefficient layout
+  a.ns = sh->ns;
   return a;
 }
 
@@ -996,7 +1006,7 @@ int op_project_scalar(const cffyn_shell* sh, const double* C, double* C2, cudaSt
     a.w_stride = (long long)N * N;
     a.g.K = a.g.K0 = a.g.P = a.g.P0 = N;
     a.g.in_rs = a.g.out_rs = sh->n_r;
-    a.g.ncols = (long long)sh->ny[d] * 2 * sh->n_r;
+    a.g.ncols = (long long)sh->ny[d] * 2 * sh->n_r * sh->ns;
     off += sh->ny[d];
     cls[ncls] = a;
     W64[ncls] = graded ? sh->F0g + (size_t)d * nm * N * N : sh->Fproj0;
@@ -1045,7 +1055,7 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     a.w_stride = (long long)N * N;
     a.g.K = a.g.K0 = a.g.P = a.g.P0 = N;
     a.g.in_rs = a.g.out_rs = sh->n_r;
-    a.g.ncols = (long long)n_r0 * 2 * sh->n_r;
+    a.g.ncols = (long long)n_r0 * 2 * sh->n_r * sh->ns;
     cls[ncls] = a;
     W64[ncls] = sh->Fproj0;
     Wt[ncls++] = &sh->tF0;
@@ -1064,7 +1074,7 @@ int op_project(const cffyn_shell* sh, const double* C, double* C2, const int* sl
     b.g.K0 = N;
     b.g.P = b.g.P0 = N;
     b.g.in_rs = b.g.out_rs = sh->n_r;
-    b.g.ncols = (long long)n_c[s] * 4 * sh->n_r;
+    b.g.ncols = (long long)n_c[s] * 4 * sh->n_r * sh->ns;
     cls[ncls] = b;
     W64[ncls] = sh->FprojC + (size_t)s * nm * N * 2 * N;
     Wt[ncls++] = &sh->tFC[s];

@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(128) k_decompose(const double* __restrict__ in
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (p >= geo.P) return;
   const int i = (int)((p / geo.n_r) % geo.N);
-  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const int jj = (int)((p / ((long long)geo.n_r * geo.N)) % geo.J);
   const Triad<T> t = triad_at<T>(geo, i, jj);
   decompose_group<T, FI>(group_of((int)blockIdx.y, (geo.nv - 50) / 4), Scratch<T>{sm}, in, out, geo.P, p, t);
 }
@@ -551,7 +551,7 @@ __device__ __forceinline__ void reconstruct_update(Scratch<T> sc, const double* 
   };
   if (mode <= 4) {
     const int i = (int)((p / geo.n_r) % geo.N);
-    const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+    const int jj = (int)((p / ((long long)geo.n_r * geo.N)) % geo.J);
     const Triad<T> t = triad_at<T>(geo, i, jj);
     reconstruct_group<T>(G, sc, sp, P, p, t, update);
   } else {
@@ -608,7 +608,7 @@ __global__ void k_cart(const double* __restrict__ D, double* __restrict__ out, i
   }
   const int k = (int)(p % geo.n_r);
   const int i = (int)((p / geo.n_r) % geo.N);
-  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const int jj = (int)((p / ((long long)geo.n_r * geo.N)) % geo.J);
   const Jac<double> J = jacobian<double>(geo, k, i, jj);
 #pragma unroll 2
   for (int mu = 0; mu < nf; ++mu) {

@@ -129,7 +129,7 @@ inline Geo geo_of(const cffyn_shell* sh) {
   g.N = sh->N;
   g.J = sh->J;
   g.nv = sh->nv;
-  g.P = (long long)sh->P;
+  g.P = (long long)P_all(sh);
   g.r = sh->r;
   g.sth = sh->sth;
   g.cth = sh->cth;

@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
   if (p >= P) return;
   const int k = (int)(p % geo.n_r);
   const int i = (int)((p / geo.n_r) % geo.N);
-  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const int jj = (int)((p / ((long long)geo.n_r * geo.N)) % geo.J);
   const int nv = geo.nv;
   const T half = S<T>::c(0.5);
   const Jac<T> J = jacobian<T>(geo, k, i, jj);
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(128) k_gauge_rhs(const double* __restrict__ u,
   if (p >= P) return;
   const int k = (int)(p % geo.n_r);
   const int i = (int)((p / geo.n_r) % geo.N);
-  const int jj = (int)(p / ((long long)geo.n_r * geo.N));
+  const int jj = (int)((p / ((long long)geo.n_r * geo.N)) % geo.J);
   const int nv = geo.nv;
   const Jac<T> J = jacobian<T>(geo, k, i, jj);
   const T zero = S<T>::c(0.0);

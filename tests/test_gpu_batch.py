@@ -139,3 +139,39 @@ def test_batch_argument_errors(cf):
     b.destroy()
     sh0.destroy()
     sh1.destroy()
+
+
+@pytest.mark.parametrize("prec,nf", [(1, 50), (0, 50), (1, 58)])
+def test_stacked_classes_are_bitwise_the_lone_step(cf, prec, nf):
+    # three shells of one shape, two of another and one alone: three classes,
+    # each stepped by one stacked handle; results equal lone steps bit for bit
+    shapes = [(9, 12, 24, 10), (13, 8, 16, 6), (9, 12, 24, 10), (9, 12, 24, 10), (13, 8, 16, 6), (5, 6, 12, 4)]
+    shells, us = [], []
+    for k, (n_r, N, J, L) in enumerate(shapes):
+        sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, n_fields=nf, precision=prec)
+        u = torch.from_numpy(inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, n_fields=nf, amp=1e-4 * (k + 1),
+                                                      ell=2, seed=k)).cuda()
+        sh.init_gauge_from_state(u)
+        v = torch.empty_like(u)
+        sh.filter(u, v)
+        shells.append(sh)
+        us.append(v)
+    alone = [u.clone() for u in us]
+    b = cf.Batch(shells)
+    assert b.units() == 3
+    b.rk4_step(us, None, 3)
+    for sh, u in zip(shells, alone):
+        sh.rk4_step(u, 0.0, 3)
+    torch.cuda.synchronize()
+    for i, (x, y) in enumerate(zip(us, alone)):
+        assert torch.isfinite(x).all()
+        assert torch.equal(x, y), i
+    # one class needs one step size
+    dts = [sh.default_dt() for sh in shells]
+    dts[2] *= 0.5
+    with pytest.raises(cf.CffynError) as ei:
+        b.rk4_step(us, dts, 1)
+    assert ei.value.code == cf.EINVAL
+    b.destroy()
+    for sh in shells:
+        sh.destroy()

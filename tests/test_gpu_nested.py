@@ -94,7 +94,9 @@ def test_nest_rk4_steps_match_oracle(cf, prec):
         e = np.abs(g - r).max() / np.abs(r).max()
         assert e < (1e-12 if prec == 0 else 1e-8), e
         assert np.abs(r - s0).max() > 1e-7       # the fields moved
-    assert np.abs(got[0][..., -1] - got[1][..., 0]).max() < 1e-13
+    # the common sphere: one right-hand side, but each shell's filter (the
+    # mixed path's fixed point is relative to the whole shell's field)
+    assert np.abs(got[0][..., -1] - got[1][..., 0]).max() < (1e-13 if prec == 0 else 1e-10)
     nest.destroy()
     for sh in shells:
         sh.destroy()
@@ -122,7 +124,8 @@ def test_three_shells_mixed_vs_fp64(cf):
         assert np.isfinite(a).all()
         assert np.abs(a - b).max() / np.abs(b).max() < 1e-8
     for s in range(2):
-        assert np.abs(res[0][s][..., -1] - res[0][s + 1][..., 0]).max() < 1e-13
+        assert np.abs(res[1][s][..., -1] - res[1][s + 1][..., 0]).max() < 1e-13        # FP64
+        assert np.abs(res[0][s][..., -1] - res[0][s + 1][..., 0]).max() < 1e-10        # mixed
 
 
 def test_nest_arguments(cf):
