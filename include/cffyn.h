@@ -305,6 +305,21 @@ CFFYN_API int cffyn_get_operator(const cffyn_shell* sh, int which, double* host_
 CFFYN_API int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out,
                                  int* launches_out, void* stream);
 
+/* Row-group size of one family of tensor-core operator launches of the
+ * CFFYN_MIXED path: family 0 d_r, 1 d_theta with d_phi, 2 phi analysis,
+ * 3 projections, 4 phi synthesis; rows 48 (two blocks per SM, more row
+ * groups when the operator has more rows) or 96 (one block per SM), 0 for
+ * the rule (48 up to 48 operator rows, else 96).  Shapes measured by the
+ * library's tuner get their fastest choice at creation.  Rebuilds the
+ * family's split operators (synchronises the device; not during a stream
+ * capture) and drops the captured step graph.  The results of the two
+ * choices agree to the mixed path's rounding (the digit sums of the tensor
+ * cores are exact, their FP32 tail is not).  CFFYN_EINVAL for another family
+ * or size; a no-op on the FP64 path apart from recording the choice.
+ * cffyn_get_operator_rows returns the size in use (0 for bad arguments). */
+CFFYN_API int cffyn_set_operator_rows(cffyn_shell* sh, int family, int rows);
+CFFYN_API int cffyn_get_operator_rows(const cffyn_shell* sh, int family);
+
 /* Bound of every wait inside the tensor-core operator kernels of the
  * CFFYN_MIXED path (mbarrier waits for operand copies, for the producers'
  * operand slices and for the tensor-core products), in seconds; the default

@@ -26,7 +26,7 @@ EXPORTED = [
     "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_constraint_norms",
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
-    "cffyn_set_wait_limit",
+    "cffyn_set_wait_limit", "cffyn_set_operator_rows", "cffyn_get_operator_rows",
     "cffyn_create_batch", "cffyn_batch_rk4_step", "cffyn_destroy_batch", "cffyn_batch_units",
     "cffyn_create_nest", "cffyn_nest_rhs", "cffyn_nest_rk4_step", "cffyn_nest_default_dt",
     "cffyn_destroy_nest",
@@ -77,6 +77,8 @@ def load(path=LIB_PATH):
         "cffyn_derivs": ([vp, dp, dp, vp], i),
         "cffyn_derivs_static": ([vp, dp, i, dp, vp], i),
         "cffyn_set_wait_limit": ([vp, d], i),
+        "cffyn_set_operator_rows": ([vp, i, i], i),
+        "cffyn_get_operator_rows": ([vp, i], i),
         "cffyn_derivs_fft": ([vp, dp, dp, vp], i),
         "cffyn_rhs": ([vp, dp, dp, vp], i),
         "cffyn_filter": ([vp, dp, dp, vp], i),
@@ -227,6 +229,14 @@ class Shell:
         la = (ctypes.c_int * n)()
         _check(load().cffyn_profile_step(self.h, _ptr(u, "u"), float(dt), ms, la, _stream(stream)))
         return {k: (float(ms[i]), int(la[i])) for i, k in enumerate(PROFILE_PHASES)}
+
+    def set_operator_rows(self, family, rows):
+        """Row-group size (0, 48, 96) of an operator family (0 d_r, 1 d_theta +
+        d_phi, 2 phi analysis, 3 projections, 4 phi synthesis)."""
+        _check(load().cffyn_set_operator_rows(self.h, int(family), int(rows)))
+
+    def get_operator_rows(self, family):
+        return int(load().cffyn_get_operator_rows(self.h, int(family)))
 
     def set_wait_limit(self, seconds):
         """Bound (s) of the tensor-core kernels' waits; < 0 restores 1 s, 0

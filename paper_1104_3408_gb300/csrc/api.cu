@@ -10,6 +10,7 @@
 #include <new>
 
 #include "common.cuh"
+#include "tile_table.h"
 
 namespace cffyn {
 
@@ -39,6 +40,7 @@ int op_project(const cffyn_shell*, const double*, double*, const int*, int, cons
 int op_prepare(const cffyn_shell*, const double*, bool, int, long long, int, cudaStream_t);
 // setup.cu
 int build_operators(cffyn_shell*);
+int build_tc_family(cffyn_shell*, int);
 void free_tc(TcOp&);
 // pointwise.cu
 int pw_rhs(const cffyn_shell*, const double*, const double*, double*, cudaStream_t);
@@ -273,6 +275,10 @@ static int create_shell(const cffyn_shell_desc* desc, int ns, cffyn_shell** out)
     return code;
   };
   if (set_op_smem_limits() != CFFYN_OK) return fail(CFFYN_ECUDA);
+  for (const TileEntry* t = kTileTable; t->n_r; ++t)
+    if (t->n_r == d.n_r && t->n_theta == d.n_theta && t->L == d.L && t->n_fields == d.n_fields &&
+        t->filter_kind == d.filter_kind)
+      for (int w = 0; w < kOpFamilies; ++w) sh->op_rows[w] = t->rows[w];
   if ((rc = build_operators(sh))) return fail(rc);
   const size_t nvP = (size_t)sh->nv * sh->P;
   auto alloc = [&](double** p, size_t n) -> int {
@@ -766,6 +772,40 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
     sh->trace_steps += n_steps;
   }
   return step_flag_status(*sh->flag_host);
+}
+
+int cffyn_set_operator_rows(cffyn_shell* sh, int family, int rows) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  if (family < 0 || family >= kOpFamilies || (rows != 0 && rows != 48 && rows != 96)) {
+    set_error("operator family %d outside 0..%d or rows %d not 0, 48 or 96", family, kOpFamilies - 1, rows);
+    return CFFYN_EINVAL;
+  }
+  if (sh->op_rows[family] == rows) return CFFYN_OK;
+  if (sh->d.precision != CFFYN_MIXED) {
+    sh->op_rows[family] = rows;
+    return CFFYN_OK;
+  }
+  CF_CUDA(cudaDeviceSynchronize());
+  const int old = sh->op_rows[family];
+  sh->op_rows[family] = rows;
+  int rc;
+  if ((rc = build_tc_family(sh, family))) {
+    sh->op_rows[family] = old;
+    build_tc_family(sh, family);
+    return rc;
+  }
+  if (sh->graph) {
+    cudaGraphExecDestroy(sh->graph);
+    sh->graph = nullptr;
+  }
+  ++sh->ws_gen;
+  return CFFYN_OK;
+}
+
+int cffyn_get_operator_rows(const cffyn_shell* sh, int family) {
+  if (!sh || family < 0 || family >= kOpFamilies) return 0;
+  const cffyn::TcOp* t[kOpFamilies] = {&sh->tDr, &sh->tDth2, &sh->tFan, &sh->tF0, &sh->tFsy};
+  return sh->d.precision == CFFYN_MIXED ? t[family]->rows : sh->op_rows[family];
 }
 
 int cffyn_set_wait_limit(cffyn_shell* sh, double seconds) {

@@ -49,7 +49,7 @@ bool same_shape(const cffyn_shell* a, const cffyn_shell* b) {
   return x.n_r == y.n_r && x.n_theta == y.n_theta && x.n_phi == y.n_phi && x.r_in == y.r_in &&
          x.r_out == y.r_out && x.L == y.L && x.n_fields == y.n_fields && x.precision == y.precision &&
          x.filter_mode == y.filter_mode && x.filter_kind == y.filter_kind && x.courant == y.courant &&
-         a->tc_wait_ns == b->tc_wait_ns;
+         a->tc_wait_ns == b->tc_wait_ns && std::equal(a->op_rows, a->op_rows + kOpFamilies, b->op_rows);
 }
 
 }  // namespace
@@ -172,6 +172,11 @@ int make_units(cffyn_batch* b) {
         return rc;
       }
       u.stack->tc_wait_ns = f->tc_wait_ns;
+      for (int w = 0; w < kOpFamilies; ++w)
+        if (u.stack->op_rows[w] != f->op_rows[w] && (rc = cffyn_set_operator_rows(u.stack, w, f->op_rows[w]))) {
+          b->units.push_back(u);
+          return rc;
+        }
       u.stack->gauge_set = true;  // gathered from the members before every call
       if (cudaMalloc(&u.U, (size_t)d.n_fields * P_all(u.stack) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();

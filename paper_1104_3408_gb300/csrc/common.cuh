@@ -43,6 +43,10 @@ void count_launch();
 // 2^-8 and slices 11..15 digits 1..5 scaled by 2^-16 (they carry the
 // digit-sum-5 and digit-sum-6 products into the digit-sum-4 accumulator).
 constexpr int kTcWSlices = 16;
+// families of operator launches whose row-group size can be chosen
+// (cffyn_set_operator_rows): d_r, d_theta + d_phi, phi analysis,
+// projections, phi synthesis
+constexpr int kOpFamilies = 5;
 struct TcOp {
   unsigned short* w = nullptr;  // [batch][group][kstep][slice][rows x 16]
   int* rowexp = nullptr;        // [batch][groups * rows]
@@ -86,6 +90,10 @@ struct cffyn_shell {
   // split-precision operators (tcgen05 core); tF0 and tFC are batched over
   // m = 0..L, tFC per spin 1..3
   cffyn::TcOp tDr, tDth2, tDph, tFan, tFsy, tF0, tFC[3], tF0g[4];
+  // row-group size of each operator family (0: the rule, 48 up to 48 rows,
+  // else 96), set at creation from the tuned table or by
+  // cffyn_set_operator_rows
+  int op_rows[cffyn::kOpFamilies] = {0, 0, 0, 0, 0};
 
   // spin slots of the filter (one real slot per Cartesian field): nR0 real
   // functions filtered with F^0_m (spin 0, including the real and imaginary

@@ -737,7 +737,11 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     // rows [g R, (g + 1) R) of every accumulator, g = w / 4, R = ROWS / (warps / 4)
     constexpr int R = ROWS / (C::kProd / 128);
     const int g = tid >> 7;
-    const int prow = a.g.P - grp * ROWS;  // valid rows of this group
+    const int prow = min(a.g.P - grp * ROWS, ROWS);  // valid rows of this group
+    // d_r (all rows in one group): outputs staged in the free stage buffers
+    // (every MMA and copy has completed) as [column][row]
+    const bool stage_out = a.kind == OP_R && W.ngroups == 1;
+    long long* out_tile = reinterpret_cast<long long*>(smtc);
     const uint32_t lane = tm + ((uint32_t)(((tid >> 5) & 3) * 32) << 16);
     // 2^(E_col - 14) as two factors (the second is 1 unless E_col - 14 is
     // below the float range, i.e. for outputs that underflow anyway)
@@ -762,9 +766,22 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
           const long long w =
               fold_pair(__uint_as_float(v0[j]), __uint_as_float(v1[j]), __uint_as_float(v2[j]),
                         __uint_as_float(v3[j]), __uint_as_float(v4[j]), rowF[p0 + j], cf1, cf2);
-          store_elem(a, col, grp * ROWS + p0 + j, __longlong_as_double(w));
+          if (stage_out)
+            out_tile[ctile * prow + p0 + j] = w;
+          else
+            store_elem(a, col, grp * ROWS + p0 + j, __longlong_as_double(w));
         }
       }
+    }
+    if (stage_out) {
+      // d_r: the tile's outputs (columns c of n_r rows each, out0 = c n_r)
+      // are one contiguous block; after the producers' barrier it is copied
+      // out with consecutive threads on consecutive words
+      asm volatile("bar.sync 1, %0;" ::"r"(C::kProd) : "memory");
+      const long long c0 = tile * kTcCols;
+      const long long nc = min((long long)kTcCols, a.g.ncols - c0);
+      long long* dst = reinterpret_cast<long long*>(a.out) + c0 * prow;
+      for (long long e = tid; e < nc * prow; e += C::kProd) dst[e] = out_tile[e];
     }
   }
   tc::fence_before();

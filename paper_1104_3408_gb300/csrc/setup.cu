@@ -387,10 +387,10 @@ __global__ void k_tc_pack(const double* A, int P, int K, int ld, const int* rowe
 }
 
 int build_tc(TcOp& s, const double* A, int P, int K, int ld, size_t& bytes, int nbatch = 1,
-             size_t a_stride = 0) {
+             size_t a_stride = 0, int rows = 0) {
   s.P = P;
   s.K = K;
-  s.rows = P <= 48 ? 48 : 96;
+  s.rows = rows == 48 || rows == 96 ? rows : (P <= 48 ? 48 : 96);
   s.ngroups = (P + s.rows - 1) / s.rows;
   s.ksteps = (K + 15) / 16;
   s.nbatch = nbatch;
@@ -416,6 +416,55 @@ void free_tc(TcOp& s) {
   if (s.rowexp) cudaFree(s.rowexp);
   s.w = nullptr;
   s.rowexp = nullptr;
+}
+
+// The split-precision operators of one family of launches (the families of
+// cffyn_set_operator_rows): 0 d_r, 1 d_theta with d_phi, 2 phi analysis,
+// 3 projections (every spin class and the graded sets), 4 phi synthesis; with
+// the shell's row-group choice (0: 48 up to 48 rows, else 96).  Frees the
+// family's previous operators.
+int build_tc_family(cffyn_shell* sh, int which) {
+  const int n_r = sh->n_r, N = sh->N, J = sh->J, R = sh->R, Lrows = sh->Lrows;
+  const int nm = sh->L + 1;
+  const int rows = sh->op_rows[which];
+  size_t& B = sh->bytes;
+  int rc = CFFYN_OK;
+  auto rebuild = [&](TcOp& t, const double* A, int P, int K, int ld, int nb, size_t st) {
+    if (t.w) B -= t.w_stride * t.nbatch * sizeof(unsigned short) + t.rowexp_stride * t.nbatch * sizeof(int);
+    free_tc(t);
+    return build_tc(t, A, P, K, ld, B, nb, st, rows);
+  };
+  switch (which) {
+    case 0:
+      rc = rebuild(sh->tDr, sh->Dr, n_r, n_r, n_r, 1, 0);
+      break;
+    case 1:
+      if (!(rc = rebuild(sh->tDth2, sh->Dth2, 2 * N, 2 * N, 2 * N, 1, 0)))
+        rc = rebuild(sh->tDph, sh->Dph, J, J, J, 1, 0);
+      break;
+    case 2:
+      rc = rebuild(sh->tFan, sh->Fan, R, J, J, 1, 0);
+      break;
+    case 3:
+      rc = rebuild(sh->tF0, sh->Fproj0, N, N, N, nm, (size_t)N * N);
+      for (int s = 0; s < 3 && !rc; ++s)
+        rc = rebuild(sh->tFC[s], sh->FprojC + (size_t)s * nm * N * 2 * N, N, 2 * N, 2 * N, nm,
+                     (size_t)N * 2 * N);
+      if (sh->F0g)
+        for (int d = 0; d < 4 && !rc; ++d)
+          rc = rebuild(sh->tF0g[d], sh->F0g + (size_t)d * (Lrows + 1) * N * N, N, N, N, Lrows + 1,
+                       (size_t)N * N);
+      break;
+    case 4:
+      rc = rebuild(sh->tFsy, sh->Fsy, J, R, R, 1, 0);
+      break;
+    default:
+      set_error("operator family %d outside 0..%d", which, kOpFamilies - 1);
+      return CFFYN_EINVAL;
+  }
+  if (rc) return rc;
+  CF_CUDA(cudaDeviceSynchronize());
+  return CFFYN_OK;
 }
 
 // Builds every operator of the shell.  Called from cffyn_create_shell_ex.
@@ -517,24 +566,9 @@ int build_operators(cffyn_shell* sh) {
   }
 
   // split-precision digits of every operator (used by the mixed path)
-  if (sh->d.precision == CFFYN_MIXED) {
-    if ((rc = build_tc(sh->tDr, sh->Dr, n_r, n_r, n_r, B))) return rc;
-    if ((rc = build_tc(sh->tDth2, sh->Dth2, 2 * N, 2 * N, 2 * N, B))) return rc;
-    if ((rc = build_tc(sh->tDph, sh->Dph, J, J, J, B))) return rc;
-    if ((rc = build_tc(sh->tFan, sh->Fan, R, J, J, B))) return rc;
-    if ((rc = build_tc(sh->tFsy, sh->Fsy, J, R, R, B))) return rc;
-    if ((rc = build_tc(sh->tF0, sh->Fproj0, N, N, N, B, nm, (size_t)N * N))) return rc;
-    for (int s = 0; s < 3; ++s)
-      if ((rc = build_tc(sh->tFC[s], sh->FprojC + (size_t)s * nm * N * 2 * N, N, 2 * N, 2 * N, B, nm,
-                         (size_t)N * 2 * N)))
-        return rc;
-    if (sh->F0g)
-      for (int d = 0; d < 4; ++d)
-        if ((rc = build_tc(sh->tF0g[d], sh->F0g + (size_t)d * (Lrows + 1) * N * N, N, N, N, B, Lrows + 1,
-                           (size_t)N * N)))
-          return rc;
-    CF_CUDA(cudaDeviceSynchronize());
-  }
+  if (sh->d.precision == CFFYN_MIXED)
+    for (int w = 0; w < kOpFamilies; ++w)
+      if ((rc = build_tc_family(sh, w))) return rc;
   return CFFYN_OK;
 }
 

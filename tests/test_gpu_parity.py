@@ -234,3 +234,37 @@ def test_trace_and_profile_report_every_kernel_group(cf):
     assert all(t > 0 and n > 0 for t, n in prof.values())
     assert {k: n for k, (t, n) in prof.items()} == launches
     sh.destroy()
+
+
+@pytest.mark.parametrize("rows", [48, 96])
+def test_operator_row_groups_keep_parity(cf, rows):
+    # every family of operator launches on 48- or 96-row groups (the tuner's
+    # two candidates): derivatives, filter and right-hand side stay within
+    # the mixed path's tolerance against the oracle
+    n_r, N, J, L = 17, 32, 64, 30
+    u0 = inputs.band_limited_fields(n_r, N, J, 1.8, 11.0, seed=5)
+    sh = cf.Shell(n_r, N, J, 1.8, 11.0, L, precision=cf.MIXED)
+    for w in range(5):
+        sh.set_operator_rows(w, rows)
+    assert [sh.get_operator_rows(w) for w in range(5)] == [rows] * 5
+    out = torch.empty((3,) + u0.shape, dtype=torch.float64, device="cuda")
+    sh.derivs(dev(u0), out)
+    ref = cff.cartesian_derivatives(u0, 1.8, 11.0)
+    assert max(rel(out[d].cpu().numpy(), ref[d], axis=0) for d in range(3)) < TOL[1]
+    f = torch.empty_like(dev(u0))
+    sh.filter(dev(u0), f)
+    fref = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L).filter(u0)
+    assert rel(f.cpu().numpy(), fref, axis=0) < TOL[1]
+    ks = inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=1e-4, ell=4, seed=3)
+    rs = oracle.OracleShell(n_r, N, J, 1.8, 11.0, L)
+    rs.init_gauge_from_state(ks)
+    u = dev(ks)
+    sh.init_gauge_from_state(u)
+    r = torch.empty_like(u)
+    sh.rhs(u, r)
+    assert np.abs(r.cpu().numpy() - rs.rhs(ks)).max() / np.abs(rs.derivs(ks)).max() < TOL[1]
+    with pytest.raises(cf.CffynError):
+        sh.set_operator_rows(5, 48)
+    with pytest.raises(cf.CffynError):
+        sh.set_operator_rows(0, 64)
+    sh.destroy()
