@@ -590,7 +590,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
   int ce = exps[col.fld];
   if (pairing) {
     // slot pairs (f, f ^ 1), f >= kPairedFrom, of the same stacked shell
-    const int f = col.fld / a.ns, sidx = col.fld - f * a.ns;
+    const int f = a.ns == 1 ? col.fld : col.fld / a.ns, sidx = col.fld - f * a.ns;
     if (f >= kPairedFrom) ce = max(ce, exps[(f ^ 1) * a.ns + sidx]);
   }
   const int E = ce - 1022 + B.eoff;
@@ -747,32 +747,34 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     // below the float range, i.e. for outputs that underflow anyway)
     const int ec = E - 14;
     const float cf1 = pow2f(ec), cf2 = pow2f(ec - max(-126, min(127, ec)));
+    // the group's rows of this thread's column, each folded result handed to
+    // sink(row within the group, pair bits)
+    auto rows_out = [&](auto&& sink) {
 #pragma unroll 1
-    for (int p0 = g * R; p0 < (g + 1) * R && p0 < prow; p0 += 8) {
-      uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
-      tc::ld8(lane + 0 * ROWS + p0, v0);
-      tc::ld8(lane + 1 * ROWS + p0, v1);
-      tc::ld8(lane + 2 * ROWS + p0, v2);
-      tc::ld8(lane + 3 * ROWS + p0, v3);
-      tc::ld8(lane + 4 * ROWS + p0, v4);
-      tc::ld_wait(v0);
-      tc::tie(v1);
-      tc::tie(v2);
-      tc::tie(v3);
-      tc::tie(v4);
+      for (int p0 = g * R; p0 < (g + 1) * R && p0 < prow; p0 += 8) {
+        uint32_t v0[8], v1[8], v2[8], v3[8], v4[8];
+        tc::ld8(lane + 0 * ROWS + p0, v0);
+        tc::ld8(lane + 1 * ROWS + p0, v1);
+        tc::ld8(lane + 2 * ROWS + p0, v2);
+        tc::ld8(lane + 3 * ROWS + p0, v3);
+        tc::ld8(lane + 4 * ROWS + p0, v4);
+        tc::ld_wait(v0);
+        tc::tie(v1);
+        tc::tie(v2);
+        tc::tie(v3);
+        tc::tie(v4);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (p0 + j < prow) {
-          const long long w =
-              fold_pair(__uint_as_float(v0[j]), __uint_as_float(v1[j]), __uint_as_float(v2[j]),
-                        __uint_as_float(v3[j]), __uint_as_float(v4[j]), rowF[p0 + j], cf1, cf2);
-          if (stage_out)
-            out_tile[ctile * prow + p0 + j] = w;
-          else
-            store_elem(a, col, grp * ROWS + p0 + j, __longlong_as_double(w));
+        for (int j = 0; j < 8; ++j) {
+          if (p0 + j < prow)
+            sink(p0 + j, fold_pair(__uint_as_float(v0[j]), __uint_as_float(v1[j]), __uint_as_float(v2[j]),
+                                   __uint_as_float(v3[j]), __uint_as_float(v4[j]), rowF[p0 + j], cf1, cf2));
         }
       }
-    }
+    };
+    if (!stage_out)
+      rows_out([&](int row, long long w) { store_elem(a, col, grp * ROWS + row, __longlong_as_double(w)); });
+    else
+      rows_out([&](int row, long long w) { out_tile[ctile * prow + row] = w; });
     if (stage_out) {
       // d_r: the tile's outputs (columns c of n_r rows each, out0 = c n_r)
       // are one contiguous block; after the producers' barrier it is copied

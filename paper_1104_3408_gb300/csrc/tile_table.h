@@ -15,6 +15,20 @@ struct TileEntry {
 };
 
 static const TileEntry kTileTable[] = {
+    {33, 48, 46, 50, 0, {48, 96, 96, 48, 96}},
+    {9, 12, 10, 50, 0, {48, 48, 48, 48, 48}},
+    {65, 96, 94, 58, 0, {96, 96, 96, 96, 96}},
+    {17, 16, 14, 50, 0, {48, 48, 48, 48, 48}},
+    {25, 16, 14, 50, 0, {48, 48, 48, 48, 48}},
+    {33, 16, 14, 50, 0, {48, 48, 48, 48, 48}},
+    {17, 24, 22, 50, 0, {48, 48, 48, 48, 48}},
+    {25, 24, 22, 50, 0, {48, 48, 48, 48, 48}},
+    {33, 24, 22, 50, 0, {48, 48, 48, 48, 48}},
+    {17, 32, 30, 50, 0, {48, 96, 96, 48, 96}},
+    {25, 32, 30, 50, 0, {48, 96, 48, 48, 96}},
+    {33, 32, 30, 50, 0, {48, 96, 96, 48, 96}},
+    {17, 48, 46, 50, 0, {48, 96, 96, 48, 96}},
+    {25, 48, 46, 50, 0, {48, 96, 96, 48, 96}},
     {0, 0, 0, 0, 0, {0, 0, 0, 0, 0}},  // end of table
 };
 
