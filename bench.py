@@ -568,7 +568,8 @@ def run_batch(args, rank, local_rank, ws, dist):
         sh.rk4_step(v, 0.0, 1)      # capture each shell's own graph
     mixed_loop = loop_rate(shells, us, 2)
     # kernel launches of one shell's step (the same sequence for every
-    # 50-field mixed shell), from a traced lone step
+    # 50-field mixed shell and for every stacked class of the batch), from a
+    # traced lone step
     shells[0].set_trace(True)
     shells[0].rk4_step(us[0], 0.0, 1)
     launches_per_shell_step = sum(shells[0].get_trace()[1].values())
@@ -660,8 +661,9 @@ def run_batch(args, rank, local_rank, ws, dist):
         "roofline": roof,
         "mixed_per_shell_loop_value": mixed_loop,
         "batch_over_mixed_loop": value / mixed_loop,
-        "gpu_launches": launches_per_shell_step * len(mine) * args.steps,
-        "launches_per_shell_step": launches_per_shell_step,
+        "gpu_launches": launches_per_shell_step * b.units() * args.steps,
+        "launches_per_class_step": launches_per_shell_step,
+        "classes": b.units(),
         "fp64_gpu": fp64,
         "e2e": e2e,
         "cpu_baseline": cpu,

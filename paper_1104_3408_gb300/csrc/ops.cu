@@ -561,7 +561,10 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_addr(b)) : "memory");
 }
 
-template <bool FI, int ROWS>
+// STAGE: the launch is d_r (one operator class, all rows in one group): the
+// epilogue stages the tile's outputs in shared memory and stores them as one
+// contiguous block.
+template <bool FI, int ROWS, bool STAGE = false>
 __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, const int* __restrict__ exps,
                                                                  int pairing, int* __restrict__ flag) {
   using C = TcCfg<ROWS>;
@@ -740,7 +743,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     const int prow = min(a.g.P - grp * ROWS, ROWS);  // valid rows of this group
     // d_r (all rows in one group): outputs staged in the free stage buffers
     // (every MMA and copy has completed) as [column][row]
-    const bool stage_out = a.kind == OP_R && W.ngroups == 1;
+    constexpr bool stage_out = STAGE;
     long long* out_tile = reinterpret_cast<long long*>(smtc);
     const uint32_t lane = tm + ((uint32_t)(((tid >> 5) & 3) * 32) << 16);
     // 2^(E_col - 14) as two factors (the second is 1 unless E_col - 14 is
@@ -771,11 +774,11 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
         }
       }
     };
-    if (!stage_out)
+    if constexpr (!stage_out)
       rows_out([&](int row, long long w) { store_elem(a, col, grp * ROWS + row, __longlong_as_double(w)); });
     else
       rows_out([&](int row, long long w) { out_tile[ctile * prow + row] = w; });
-    if (stage_out) {
+    if constexpr (stage_out) {
       // d_r: the tile's outputs (columns c of n_r rows each, out0 = c n_r)
       // are one contiguous block; after the producers' barrier it is copied
       // out with consecutive threads on consecutive words
@@ -809,17 +812,22 @@ static int launch_batch(const cffyn_shell* sh, const TcBatch& b0, cudaStream_t s
   for (int c = 0; c < b.nclass; ++c) gx = std::max(gx, b.tiles[c] * b.W[c].ngroups);
   if (gx == 0) return CFFYN_OK;
   const dim3 grid((unsigned)gx, (unsigned)(b.nclass * b.nm));
+  // d_r (one class, one row group): the instance with the staged epilogue
+  const bool stage = b.nclass == 1 && b.a[0].kind == OP_R && b.W[0].ngroups == 1;
+#define CFFYN_LAUNCH_TC(R_, FI_, ST_) \
+  k_op_tc<FI_, R_, ST_><<<grid, TcCfg<R_>::kThreads, TcCfg<R_>::kSmem, st>>>(b, exps, pairing, flag)
   if (b.W[0].rows == 48) {
     if (in_pairs)
-      k_op_tc<true, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, flag);
+      stage ? CFFYN_LAUNCH_TC(48, true, true) : CFFYN_LAUNCH_TC(48, true, false);
     else
-      k_op_tc<false, 48><<<grid, TcCfg<48>::kThreads, TcCfg<48>::kSmem, st>>>(b, exps, pairing, flag);
+      stage ? CFFYN_LAUNCH_TC(48, false, true) : CFFYN_LAUNCH_TC(48, false, false);
   } else {
     if (in_pairs)
-      k_op_tc<true, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, flag);
+      stage ? CFFYN_LAUNCH_TC(96, true, true) : CFFYN_LAUNCH_TC(96, true, false);
     else
-      k_op_tc<false, 96><<<grid, TcCfg<96>::kThreads, TcCfg<96>::kSmem, st>>>(b, exps, pairing, flag);
+      stage ? CFFYN_LAUNCH_TC(96, false, true) : CFFYN_LAUNCH_TC(96, false, false);
   }
+#undef CFFYN_LAUNCH_TC
   count_launch();
   CF_CUDA(cudaGetLastError());
   return CFFYN_OK;
@@ -860,6 +868,14 @@ int set_op_smem_limits() {
   CF_CUDA(cudaFuncSetAttribute(k_op_tc<false, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<48>::kSmem));
   CF_CUDA(cudaFuncSetAttribute(k_op_tc<true, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<96>::kSmem));
   CF_CUDA(cudaFuncSetAttribute(k_op_tc<false, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<96>::kSmem));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<true, 48, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcCfg<48>::kSmem));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<false, 48, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcCfg<48>::kSmem));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<true, 96, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcCfg<96>::kSmem));
+  CF_CUDA(cudaFuncSetAttribute(k_op_tc<false, 96, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TcCfg<96>::kSmem));
   return CFFYN_OK;
 }
 
