@@ -830,7 +830,7 @@ def run_other_workloads(args, local_rank):
 
     import torch
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "roofline", "fp64_gpu", "e2e",
-            "clocks", "gpu_launches", "mixed_per_shell_loop_value", "batch_over_mixed_loop")
+            "clocks", "gpu_launches", "mixed_per_shell_loop_value", "batch_over_mixed_loop", "classes")
     res = {}
     for name, fn in (("ks_65x96x192_58f", lambda a: run_ours(a, 0, local_rank, 1, None, acc_steps=10)),
                      ("batch_256", lambda a: run_batch(a, 0, local_rank, 1, None))):
