@@ -597,6 +597,16 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     if (f >= kPairedFrom) ce = max(ce, exps[(f ^ 1) * a.ns + sidx]);
   }
   const int E = ce - 1022 + B.eoff;
+  // input words of this producer's column, PF - 1 k-steps ahead of the one
+  // being sliced (a ring of PF register buffers); the first loads go out
+  // before the set-up barrier so that their latency overlaps it
+  constexpr int PF = ROWS == 96 ? 3 : 2;
+  long long pf[PF][KQ];
+  if (producer) {
+#pragma unroll
+    for (int q = 0; q < PF - 1; ++q)
+      if (q < W.ksteps) gather<FI, KQ>(a, col, q * 16 + kq, pf[q]);
+  }
   if (tid < ROWS) rowF[tid] = pow2f(W.rowexp[grp * ROWS + tid]);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -619,14 +629,11 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     const int xoff = (ctile >> 3) * 256 + (kq >> 3) * 128 + (ctile & 7) * 16 + (kq & 7) * 2;
     const bool fscale = E >= -78 && E <= 126;  // FMA-pipe slicing of float pairs
     const DigitScale dsc = digit_scale(fscale ? E : 0);
-    long long nxt[KQ];
-    gather<FI, KQ>(a, col, kq, nxt);
-    for (int ks = 0; ks < ksteps; ++ks) {
+    // k-step ks from the buffer cur; first the loads of k-step ks + PF - 1
+    // go out into nx (consumed one k-step ago)
+    auto body = [&](int ks, long long(&cur)[KQ], long long(&nx)[KQ]) {
       const int s = ks % S;
-      long long cur[KQ];
-#pragma unroll
-      for (int i = 0; i < KQ; ++i) cur[i] = nxt[i];
-      if (ks + 1 < ksteps) gather<FI, KQ>(a, col, (ks + 1) * 16 + kq, nxt);
+      if (ks + PF - 1 < ksteps) gather<FI, KQ>(a, col, (ks + PF - 1) * 16 + kq, nx);
       if (ks >= S && ok) ok = pipe_wait(&empty[s], ((ks - S) / S) & 1, B.wait_ns);
       unsigned char* xs = smtc + s * C::kStage + xoff;
       uint32_t wd[kSlices][KQ / 2];
@@ -665,6 +672,11 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
       }
       tc::fence_proxy_async();
       bar_arrive(&xfull[s]);
+    };
+    for (int ks0 = 0; ks0 < ksteps; ks0 += PF) {
+#pragma unroll
+      for (int q = 0; q < PF; ++q)
+        if (ks0 + q < ksteps) body(ks0 + q, pf[q], pf[(q + PF - 1) % PF]);
     }
     if (ok) ok = pipe_wait(&accf, 0, B.wait_ns);
   } else if (tid == C::kProd) {
