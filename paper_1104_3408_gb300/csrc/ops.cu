@@ -476,13 +476,15 @@ struct TcCfg {
   static_assert(kStage % 1024 == 0, "stage alignment of the descriptors and bulk copies");
 };
 
-// Raw 64-bit words of N consecutive k of one column (zero outside K or in an
-// empty second segment; the sign of a negated segment applied on the bits).
-// Branch-free so that the loads issue together.
+// Raw 64-bit words of N consecutive k of one column, as plain loads whose
+// results nothing uses yet (a k outside K or in an empty second segment
+// loads the array's first word instead), so that loads issued k-steps ahead
+// or before the set-up barrier do not hold the thread; fix_words applies the
+// zeros and the sign of a negated segment (on the bits) when the words are
+// consumed.
 template <bool FI, int N>
 __device__ __forceinline__ void gather(const OpArgs& a, const ColDesc& d, int k0, long long (&w)[N]) {
   const long long* in = reinterpret_cast<const long long*>(a.in);
-  const long long m = FI ? (long long)0x8000000080000000ull : (long long)0x8000000000000000ull;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const int k = k0 + i;
@@ -490,8 +492,19 @@ __device__ __forceinline__ void gather(const OpArgs& a, const ColDesc& d, int k0
     const int kk = seg1 ? (a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0)) : k;
     const long long base = seg1 ? d.in1 : d.in0;
     const bool live = d.valid && k < a.g.K && !(seg1 && d.sgn1 == 2);
-    const long long v = live ? __ldg(in + base + (long long)kk * a.g.in_rs) : 0ll;
-    w[i] = (seg1 && d.sgn1 == 1) ? (v ^ m) : v;
+    w[i] = __ldg(in + (live ? base + (long long)kk * a.g.in_rs : 0ll));
+  }
+}
+
+template <bool FI, int N>
+__device__ __forceinline__ void fix_words(const OpArgs& a, const ColDesc& d, int k0, long long (&w)[N]) {
+  const long long m = FI ? (long long)0x8000000080000000ull : (long long)0x8000000000000000ull;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    const int k = k0 + i;
+    const bool seg1 = k >= a.g.K0;
+    const bool live = d.valid && k < a.g.K && !(seg1 && d.sgn1 == 2);
+    w[i] = live ? ((seg1 && d.sgn1 == 1) ? (w[i] ^ m) : w[i]) : 0ll;
   }
 }
 
@@ -634,6 +647,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     auto body = [&](int ks, long long(&cur)[KQ], long long(&nx)[KQ]) {
       const int s = ks % S;
       if (ks + PF - 1 < ksteps) gather<FI, KQ>(a, col, (ks + PF - 1) * 16 + kq, nx);
+      fix_words<FI, KQ>(a, col, ks * 16 + kq, cur);
       if (ks >= S && ok) ok = pipe_wait(&empty[s], ((ks - S) / S) & 1, B.wait_ns);
       unsigned char* xs = smtc + s * C::kStage + xoff;
       uint32_t wd[kSlices][KQ / 2];
