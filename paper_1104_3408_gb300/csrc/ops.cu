@@ -476,15 +476,13 @@ struct TcCfg {
   static_assert(kStage % 1024 == 0, "stage alignment of the descriptors and bulk copies");
 };
 
-// Raw 64-bit words of N consecutive k of one column, as plain loads whose
-// results nothing uses yet (a k outside K or in an empty second segment
-// loads the array's first word instead), so that loads issued k-steps ahead
-// or before the set-up barrier do not hold the thread; fix_words applies the
-// zeros and the sign of a negated segment (on the bits) when the words are
-// consumed.
+// Raw 64-bit words of N consecutive k of one column (zero outside K or in an
+// empty second segment; the sign of a negated segment applied on the bits).
+// Branch-free so that the loads issue together.
 template <bool FI, int N>
 __device__ __forceinline__ void gather(const OpArgs& a, const ColDesc& d, int k0, long long (&w)[N]) {
   const long long* in = reinterpret_cast<const long long*>(a.in);
+  const long long m = FI ? (long long)0x8000000080000000ull : (long long)0x8000000000000000ull;
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     const int k = k0 + i;
@@ -492,19 +490,8 @@ __device__ __forceinline__ void gather(const OpArgs& a, const ColDesc& d, int k0
     const int kk = seg1 ? (a.g.rev1 ? (a.g.K - 1 - k) : (k - a.g.K0)) : k;
     const long long base = seg1 ? d.in1 : d.in0;
     const bool live = d.valid && k < a.g.K && !(seg1 && d.sgn1 == 2);
-    w[i] = __ldg(in + (live ? base + (long long)kk * a.g.in_rs : 0ll));
-  }
-}
-
-template <bool FI, int N>
-__device__ __forceinline__ void fix_words(const OpArgs& a, const ColDesc& d, int k0, long long (&w)[N]) {
-  const long long m = FI ? (long long)0x8000000080000000ull : (long long)0x8000000000000000ull;
-#pragma unroll
-  for (int i = 0; i < N; ++i) {
-    const int k = k0 + i;
-    const bool seg1 = k >= a.g.K0;
-    const bool live = d.valid && k < a.g.K && !(seg1 && d.sgn1 == 2);
-    w[i] = live ? ((seg1 && d.sgn1 == 1) ? (w[i] ^ m) : w[i]) : 0ll;
+    const long long v = live ? __ldg(in + base + (long long)kk * a.g.in_rs) : 0ll;
+    w[i] = (seg1 && d.sgn1 == 1) ? (v ^ m) : v;
   }
 }
 
@@ -610,16 +597,6 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     if (f >= kPairedFrom) ce = max(ce, exps[(f ^ 1) * a.ns + sidx]);
   }
   const int E = ce - 1022 + B.eoff;
-  // input words of this producer's column, PF - 1 k-steps ahead of the one
-  // being sliced (a ring of PF register buffers); the first loads go out
-  // before the set-up barrier so that their latency overlaps it
-  constexpr int PF = ROWS == 96 ? 3 : 2;
-  long long pf[PF][KQ];
-  if (producer) {
-#pragma unroll
-    for (int q = 0; q < PF - 1; ++q)
-      if (q < W.ksteps) gather<FI, KQ>(a, col, q * 16 + kq, pf[q]);
-  }
   if (tid < ROWS) rowF[tid] = pow2f(W.rowexp[grp * ROWS + tid]);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
@@ -642,12 +619,14 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     const int xoff = (ctile >> 3) * 256 + (kq >> 3) * 128 + (ctile & 7) * 16 + (kq & 7) * 2;
     const bool fscale = E >= -78 && E <= 126;  // FMA-pipe slicing of float pairs
     const DigitScale dsc = digit_scale(fscale ? E : 0);
-    // k-step ks from the buffer cur; first the loads of k-step ks + PF - 1
-    // go out into nx (consumed one k-step ago)
-    auto body = [&](int ks, long long(&cur)[KQ], long long(&nx)[KQ]) {
+    long long nxt[KQ];
+    gather<FI, KQ>(a, col, kq, nxt);
+    for (int ks = 0; ks < ksteps; ++ks) {
       const int s = ks % S;
-      if (ks + PF - 1 < ksteps) gather<FI, KQ>(a, col, (ks + PF - 1) * 16 + kq, nx);
-      fix_words<FI, KQ>(a, col, ks * 16 + kq, cur);
+      long long cur[KQ];
+#pragma unroll
+      for (int i = 0; i < KQ; ++i) cur[i] = nxt[i];
+      if (ks + 1 < ksteps) gather<FI, KQ>(a, col, (ks + 1) * 16 + kq, nxt);
       if (ks >= S && ok) ok = pipe_wait(&empty[s], ((ks - S) / S) & 1, B.wait_ns);
       unsigned char* xs = smtc + s * C::kStage + xoff;
       uint32_t wd[kSlices][KQ / 2];
@@ -686,11 +665,6 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
       }
       tc::fence_proxy_async();
       bar_arrive(&xfull[s]);
-    };
-    for (int ks0 = 0; ks0 < ksteps; ks0 += PF) {
-#pragma unroll
-      for (int q = 0; q < PF; ++q)
-        if (ks0 + q < ksteps) body(ks0 + q, pf[q], pf[(q + PF - 1) % PF]);
     }
     if (ok) ok = pipe_wait(&accf, 0, B.wait_ns);
   } else if (tid == C::kProd) {
