@@ -23,6 +23,11 @@ paper_1104_3408_gb300.r10 <study> [options]``):
              against the Yn filter on long runs.
 ``dtfac``    Tab. dtfac: a ladder of Courant factors on each of the table's
              grids; the largest stable and the smallest unstable one.
+``nested``   R10 split into two nested shells [1.8, 6.8] and [6.8, 11.8]
+             (n_r each, coupled on the common sphere through the
+             characteristic fields of App. A.2) beside one shell of the same
+             radial points (2 n_r - 1); same filter, Courant factor and
+             monitored quantity.
 
 Every step runs in the CUDA library (cffyn_rk4_step, cffyn_rhs); torch only
 holds the arrays and reduces the monitored maximum.
@@ -53,14 +58,14 @@ def make_shell(n_r, n_theta, n_f=N_F, courant=COURANT, precision=cffyn.MIXED,
                        filter_kind=filter_kind)
 
 
-def initial_state(n_r, n_theta, device="cuda"):
+def initial_state(n_r, n_theta, device="cuda", r_in=R_IN, r_out=R_OUT):
     """Kerr-Schild data with Phi_iab the numerical Cartesian derivative of
     g_ab (taken by an FP64 shell of the library) and Pi_ab = beta^k Phi_kab /
     alpha; returns the 50-field state as a float64 CUDA tensor."""
     import torch
     n_phi = 2 * n_theta
-    u = inputs.kerr_schild_state(n_r, n_theta, n_phi, R_IN, R_OUT, amp=0.0)
-    sh = cffyn.Shell(n_r, n_theta, n_phi, R_IN, R_OUT, 0, precision=cffyn.FP64)
+    u = inputs.kerr_schild_state(n_r, n_theta, n_phi, r_in, r_out, amp=0.0)
+    sh = cffyn.Shell(n_r, n_theta, n_phi, r_in, r_out, 0, precision=cffyn.FP64)
     try:
         ud = torch.from_numpy(u).to(device)
         d = torch.empty((3,) + tuple(ud.shape), dtype=torch.float64, device=device)
@@ -69,7 +74,7 @@ def initial_state(n_r, n_theta, device="cuda"):
     finally:
         sh.destroy()
     u[20:50] = phi.reshape((30,) + u.shape[1:])
-    u[10:20] = inputs.kerr_schild_pi_from_phi(phi, n_r, n_theta, n_phi, R_IN, R_OUT)
+    u[10:20] = inputs.kerr_schild_pi_from_phi(phi, n_r, n_theta, n_phi, r_in, r_out)
     return torch.from_numpy(u).to(device)
 
 
@@ -197,7 +202,74 @@ def study_dtfac(a, emit):
                                smallest_unstable=unstable, paper_lambda_max=lam_paper, runs=runs))
 
 
-STUDIES = {"rconv": study_rconv, "nf": study_nf, "filters": study_filters, "dtfac": study_dtfac}
+def run_nested(n_r, n_theta, t_end, r_mid=6.8, n_f=N_F, courant=COURANT, precision=cffyn.MIXED,
+               sample_steps=20, device="cuda"):
+    """R10 as two nested shells [R_IN, r_mid], [r_mid, R_OUT] of n_r points
+    each (cffyn_nest_*), per-step Yn filter; the monitored quantity is taken
+    on the inner shell's inner sphere."""
+    import torch
+    radii = [R_IN, r_mid, R_OUT]
+    us = [initial_state(n_r, n_theta, device, radii[i], radii[i + 1]) for i in range(2)]
+    shells = [cffyn.Shell(n_r, n_theta, 2 * n_theta, radii[i], radii[i + 1], n_theta - 1 - n_f,
+                          precision=precision, filter_mode=cffyn.FILTER_STEP, courant=courant)
+              for i in range(2)]
+    nest = cffyn.Nest(shells)
+    try:
+        for sh, u in zip(shells, us):
+            sh.init_gauge_from_state(u)
+        bufs = [torch.empty_like(u) for u in us]
+
+        def monitored():
+            nest.rhs(us, bufs)
+            return float(bufs[0][0, :, :, 0].abs().max())
+
+        nest.rhs(us, bufs)
+        trunc0 = max(float(b.abs().max()) for b in bufs)
+        dt = nest.default_dt()
+        n = max(1, int(round(t_end / dt)))
+        series = [(0.0, monitored())]
+        s, failed_at = 0, None
+        t0 = time.perf_counter()
+        while s < n:
+            k = min(sample_steps, n - s)
+            try:
+                nest.rk4_step(us, dt, k)
+            except cffyn.CffynError as e:
+                if e.code != cffyn.ENONFINITE:
+                    raise
+                failed_at = (s + k) * dt
+                break
+            s += k
+            v = monitored()
+            series.append((s * dt, v))
+            if not math.isfinite(v) or v > BLOWUP:
+                failed_at = s * dt
+                break
+        torch.cuda.synchronize()
+        run = dict(dt=dt, steps=s, t=s * dt, failed_at=failed_at, series=series,
+                   seconds=time.perf_counter() - t0)
+        common = float((us[0][..., -1] - us[1][..., 0]).abs().max())
+    finally:
+        nest.destroy()
+        for sh in shells:
+            sh.destroy()
+    out = _summary(run)
+    out.update(grid=f"2 x {n_r}x{n_theta}x{2 * n_theta}", radii=radii, n_f=n_f, courant=courant,
+               precision="fp64" if precision == cffyn.FP64 else "mixed", rhs_all_t0=trunc0,
+               common_sphere_diff=common)
+    return out
+
+
+def study_nested(a, emit):
+    for prec in _precisions(a.precision):
+        for n_r in a.n_r or [13]:
+            t_end = a.t_end or 1000.0
+            emit("nested", run_nested(n_r, a.n_theta or 9, t_end, precision=prec))
+            emit("nested_single_reference", run_one(2 * n_r - 1, a.n_theta or 9, t_end, precision=prec))
+
+
+STUDIES = {"rconv": study_rconv, "nf": study_nf, "filters": study_filters, "dtfac": study_dtfac,
+           "nested": study_nested}
 
 
 def main(argv=None):

@@ -138,3 +138,34 @@ def test_nest_arguments(cf):
         assert ei.value.code == cf.EINVAL
     for s in (a, b, c):
         s.destroy()
+
+
+@pytest.mark.parametrize("mode,kind", [("step", "yn"), ("substep", "yg")])
+def test_nest_filter_placements_and_kinds_match_oracle(cf, mode, kind):
+    n_rs, N, L, radii = [9, 7], 12, 8, [1.8, 5.0, 11.0]
+    us = _states(n_rs, N, radii)
+    ref_n = nested.NestedOracle(n_rs, N, radii, L, filter_mode=mode, filter_kind=kind)
+    ref_n.init_gauge_from_state(us)
+    start = ref_n.filter(us) if mode == "substep" else us
+    dt = ref_n.dx_min()
+    ref = ref_n.rk4_step(start, dt, 4)
+    fm = cf.FILTER_STEP if mode == "step" else cf.FILTER_SUBSTEP
+    fk = {"yn": cf.FILTER_YN, "yg": cf.FILTER_YG}[kind]
+    shells = [cf.Shell(n_r, N, 2 * N, radii[s], radii[s + 1], L, precision=cf.MIXED, filter_mode=fm,
+                       filter_kind=fk) for s, n_r in enumerate(n_rs)]
+    nest = cf.Nest(shells)
+    vs = []
+    for sh, u0 in zip(shells, us):
+        u = torch.from_numpy(u0).cuda()
+        sh.init_gauge_from_state(u)
+        if mode == "substep":
+            v = torch.empty_like(u)
+            sh.filter(u, v)
+            u = v
+        vs.append(u)
+    nest.rk4_step(vs, dt, 4)
+    for g, r in zip([v.cpu().numpy() for v in vs], ref):
+        assert np.abs(g - r).max() / np.abs(r).max() < 1e-8
+    nest.destroy()
+    for sh in shells:
+        sh.destroy()
