@@ -203,10 +203,11 @@ def study_dtfac(a, emit):
 
 
 def run_nested(n_r, n_theta, t_end, r_mid=6.8, n_f=N_F, courant=COURANT, precision=cffyn.MIXED,
-               sample_steps=20, device="cuda"):
+               sample_steps=20, device="cuda", dt=None):
     """R10 as two nested shells [R_IN, r_mid], [r_mid, R_OUT] of n_r points
     each (cffyn_nest_*), per-step Yn filter; the monitored quantity is taken
-    on the inner shell's inner sphere."""
+    on the inner shell's inner sphere.  dt: the nest's default (the Courant
+    factor times its smallest spacing) if None."""
     import torch
     radii = [R_IN, r_mid, R_OUT]
     us = [initial_state(n_r, n_theta, device, radii[i], radii[i + 1]) for i in range(2)]
@@ -225,7 +226,7 @@ def run_nested(n_r, n_theta, t_end, r_mid=6.8, n_f=N_F, courant=COURANT, precisi
 
         nest.rhs(us, bufs)
         trunc0 = max(float(b.abs().max()) for b in bufs)
-        dt = nest.default_dt()
+        dt = nest.default_dt() if dt is None else dt
         n = max(1, int(round(t_end / dt)))
         series = [(0.0, monitored())]
         s, failed_at = 0, None
@@ -264,8 +265,21 @@ def study_nested(a, emit):
     for prec in _precisions(a.precision):
         for n_r in a.n_r or [13]:
             t_end = a.t_end or 1000.0
+            # the single shell of the same radial resolution, then the nest at
+            # its own default dt and at the single shell's dt (the nest's
+            # radial spacing is twice the single shell's, so its default dt
+            # is twice as large against the same angular grid)
+            single = run_one(2 * n_r - 1, a.n_theta or 9, t_end, precision=prec)
+            emit("nested_single_reference", single)
             emit("nested", run_nested(n_r, a.n_theta or 9, t_end, precision=prec))
-            emit("nested_single_reference", run_one(2 * n_r - 1, a.n_theta or 9, t_end, precision=prec))
+            emit("nested_at_single_dt", run_nested(n_r, a.n_theta or 9, t_end, precision=prec, dt=single["dt"]))
+            # the Courant factor on the nest's own smallest spacing: which the
+            # interface coupling keeps stable
+            base = run_nested(n_r, a.n_theta or 9, 1.0, precision=prec)["dt"] / COURANT
+            for lam in (2.0, 2.5, 3.0, 3.5):
+                r = run_nested(n_r, a.n_theta or 9, min(t_end, 500.0), precision=prec, dt=lam * base)
+                r["courant"] = lam
+                emit("nested_courant", r)
 
 
 STUDIES = {"rconv": study_rconv, "nf": study_nf, "filters": study_filters, "dtfac": study_dtfac,

@@ -97,7 +97,8 @@ def tune_shape(cf, inputs, torch, shape, steps, flush):
             "ms_per_step": times}
 
 
-def write_table(results, path):
+def table_text(results):
+    """The C table of the chosen row-group sizes (csrc/tile_table.h)."""
     lines = [
         "// Row-group sizes of the split-precision operator launches, chosen per shell",
         "// shape by timing both candidates (48 or 96 operator rows per CTA) on GB300:",
@@ -121,8 +122,12 @@ def write_table(results, path):
         rows = ", ".join(str(x) for x in r["rows"])
         lines.append(f"    {{{r['n_r']}, {r['n_theta']}, {r['L']}, {r['n_fields']}, 0, {{{rows}}}}},")
     lines += ["    {0, 0, 0, 0, 0, {0, 0, 0, 0, 0}},  // end of table", "};", "", "}  // namespace cffyn", ""]
+    return "\n".join(lines)
+
+
+def write_table(results, path):
     with open(path, "w") as fh:
-        fh.write("\n".join(lines))
+        fh.write(table_text(results))
 
 
 def main():
