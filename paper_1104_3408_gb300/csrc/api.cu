@@ -167,6 +167,9 @@ void free_shell(cffyn_shell* sh) {
   if (sh->yslots) cudaFree(sh->yslots);
   if (sh->exps) cudaFree(sh->exps);
   if (sh->cap_stream) cudaStreamDestroy(sh->cap_stream);
+  if (sh->aux_stream) cudaStreamDestroy(sh->aux_stream);
+  if (sh->ev_fork) cudaEventDestroy(sh->ev_fork);
+  if (sh->ev_join) cudaEventDestroy(sh->ev_join);
   if (sh->flag_host) cudaFreeHost(sh->flag_host);
   if (sh->flag) cudaFree(sh->flag);
   if (sh->graph) cudaGraphExecDestroy(sh->graph);
@@ -353,6 +356,10 @@ static int create_shell(const cffyn_shell_desc* desc, int ns, cffyn_shell** out)
   if (cudaMalloc(&sh->flag, 64) != cudaSuccess) return fail(CFFYN_ENOMEM);
   if (cudaMemset(sh->flag, 0, 64) != cudaSuccess) return fail(CFFYN_ECUDA);
   if (cudaStreamCreateWithFlags(&sh->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(CFFYN_ECUDA);
+  if (cudaStreamCreateWithFlags(&sh->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sh->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sh->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return fail(CFFYN_ECUDA);
   if (cudaMallocHost(&sh->flag_host, sizeof(int)) != cudaSuccess) return fail(CFFYN_ENOMEM);
   if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -545,20 +552,38 @@ static int filter_in_step(cffyn_shell* sh, double* spin, cudaStream_t st, Run&& 
   return run(8, [&] { return op_dft_inv(sh, sh->D + nvP, spin, nf, st, pairing, e2); });
 }
 
+// conc: the algebraic right-hand-side kernels (k_rhs_gamma, k_rhs_quad: they
+// read the stage state only) run on the shell's second stream beside the
+// exponent scan and the derivative launches, which they share no buffer
+// with, and join before the principal parts; not for the evolved gauge of
+// 54/58 fields (k_gauge_rhs reads the derivatives) nor under per-group timing.
 template <class Run>
-static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&& run) {
+static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&& run, bool conc) {
   const size_t nvP = (size_t)sh->nv * P_all(sh);
   const long long P = (long long)sh->P;
   const int nf = nv_ops(sh);
   const bool xp = sh->d.precision == CFFYN_MIXED;
   const double* X = stage_state_of(sh, u, s);
   int rc;
+  const bool fork = conc && sh->ng == 0 && sh->aux_stream;
+  cudaStream_t sa = fork ? sh->aux_stream : st;
+  if (fork) {
+    CF_CUDA(cudaEventRecord(sh->ev_fork, st));
+    CF_CUDA(cudaStreamWaitEvent(sa, sh->ev_fork, 0));
+    if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, sa); }))) return rc;
+    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, sa); }))) return rc;
+    CF_CUDA(cudaEventRecord(sh->ev_join, sa));
+  }
   if ((rc = run(10, [&] { return op_prepare(sh, X, xp, nf, P, 0, st); }))) return rc;
   if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, nf, xp, st); }))) return rc;
   if ((rc = run(1, [&] { return op_deriv_theta_phi(sh, X, sh->D + nvP, sh->D + 2 * nvP, nf, xp, st); })))
     return rc;
-  if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
-  if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
+  if (fork) {
+    CF_CUDA(cudaStreamWaitEvent(st, sh->ev_join, 0));
+  } else {
+    if ((rc = run(2, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 1, xp, true, st); }))) return rc;
+    if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, st); }))) return rc;
+  }
   return run(4, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 3, xp, true, st); });
 }
 
@@ -607,10 +632,10 @@ static int step_tail(cffyn_shell* sh, double* u, cudaStream_t st, Run&& run) {
 }
 
 template <class Run>
-static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st, Run&& run) {
+static int step_sequence(cffyn_shell* sh, double* u, double dt, cudaStream_t st, Run&& run, bool conc) {
   int rc;
   for (int s = 0; s < 4; ++s) {
-    if ((rc = stage_front(sh, u, s, st, run))) return rc;
+    if ((rc = stage_front(sh, u, s, st, run, conc))) return rc;
     if ((rc = stage_back(sh, u, dt, s, st, run))) return rc;
   }
   return step_tail(sh, u, st, run);
@@ -643,7 +668,8 @@ static int enqueue_step(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
   };
   int rc;
   if ((rc = mark(-1))) return rc;
-  if ((rc = step_sequence(sh, u, dt, st, run))) return rc;
+  // traced: one stream, so that the marks bound the kernel groups
+  if ((rc = step_sequence(sh, u, dt, st, run, !tr))) return rc;
   sh->n_marks = nm;
   return CFFYN_OK;
 }
@@ -654,7 +680,7 @@ namespace cffyn {
 // One RK4 step enqueued on st without trace marks (a branch of a batch graph).
 int enqueue_step_branch(cffyn_shell* sh, double* u, double dt, cudaStream_t st) {
   auto run = [](int, auto&& fn) -> int { return fn(); };
-  return step_sequence(sh, u, dt, st, run);
+  return step_sequence(sh, u, dt, st, run, true);
 }
 
 // The pieces of a step for nested shells (no trace marks): stage s's
@@ -662,7 +688,7 @@ int enqueue_step_branch(cffyn_shell* sh, double* u, double dt, cudaStream_t st) 
 // the per-step filter after the last stage.
 int enqueue_stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st) {
   auto run = [](int, auto&& fn) -> int { return fn(); };
-  return stage_front(sh, u, s, st, run);
+  return stage_front(sh, u, s, st, run, true);
 }
 int enqueue_stage_back(cffyn_shell* sh, double* u, double dt, int s, cudaStream_t st) {
   auto run = [](int, auto&& fn) -> int { return fn(); };
@@ -937,7 +963,7 @@ int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* ms_out, in
     return CFFYN_OK;
   };
   if ((rc = enqueue_step_prologue(sh, u, st))) return rc;
-  rc = step_sequence(sh, u, dt, st, phase);
+  rc = step_sequence(sh, u, dt, st, phase, false);
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   return rc;

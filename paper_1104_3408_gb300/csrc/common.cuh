@@ -142,6 +142,10 @@ struct cffyn_shell {
   int* flag_host = nullptr;  // pinned host copy of the flag
   int* slots = nullptr;    // device slot lists: R0 (nR0) | C1 (nC[0]) | C2 (nC[1]) | C3 (nC[2])
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  // second stream of a stage: the algebraic right-hand-side kernels run on
+  // it beside the derivative launches (fork / join events)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // graph of one RK4 step
   cudaGraphExec_t graph = nullptr;

@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(128) k_rhs_pp(const double* __restrict__ D, co
       su[x] = acc.get();
     }
   }
-#pragma unroll 2
+#pragma unroll 1
   for (int s = 0; s < 10; ++s) {
     T Dd[3], DPh[3][3];
 #pragma unroll
