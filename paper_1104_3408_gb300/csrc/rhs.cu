@@ -49,7 +49,7 @@ struct Slots {
   __device__ __forceinline__ T& operator()(int v) const { return s[v * NB + (int)threadIdx.x]; }
 };
 
-constexpr int kRhsBlock = 64;
+constexpr int kRhsBlock = 128;
 constexpr int kGamSlots = 64;   // Gamma_cab (c*10 + s) | S_Pi 40..49 | g_ab 50..59 | C_a 60..63
 constexpr int kQuadSlots = 50;  // Pi 0..9 | Phi_iab 10 + 10 i + s | Q 40..49
 
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kRhsBlock) k_rhs_quad(const double* __restrict
       }
     }
     const T hnn = hal * nnPhi;
-#pragma unroll 2
+#pragma unroll 1
     for (int s = 0; s < 10; ++s) {
       Acc<T> acc;
       acc.fma_(hnn, V(s));
