@@ -422,9 +422,10 @@ __global__ void __launch_bounds__(kExpThreads) k_field_exp(const long long* __re
 //   acc_d = sum_{i+j=d} W_i X_j                            d = 0..3
 //   acc_4 = sum_{i+j=4} W_i X_j + 2^-8 sum_{i+j=5} W_i X_j + 2^-16 sum_{i+j=6} W_i X_j
 // The digit-sum <= 4 pairs of one input slice X_j go out as one MMA of up to
-// 256 rows over adjacent operator slices into adjacent accumulators: the
-// MMAs' shared-memory operand reads are the kernel's limit (a 128 x 96 x 16
-// MMA reads 7 KB for 196 608 MACs), and the wider MMAs re-read X_j less.
+// 256 rows over adjacent operator slices into adjacent accumulators (fewer
+// MMAs per k-step, each input slice read from shared memory fewer times).
+// A block's time goes mostly to the producers' loads and slicing, to its
+// set-up and to the epilogue; the tensor core is busy about a third of it.
 // The digit-sum-6 pairs are issued for the derivatives only (TcBatch::sum6);
 // the filter's DFTs and projections stop at digit sum 5 (21 pairs) and copy
 // eleven operator slices per k-step.
