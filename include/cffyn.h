@@ -266,7 +266,12 @@ CFFYN_API int cffyn_nest_rhs(cffyn_nest* ns, const double* const* u, double* con
  * shell.  The caller filters each shell's initial data once. */
 CFFYN_API int cffyn_nest_rk4_step(cffyn_nest* ns, double* const* u, double dt, int n_steps, void* stream);
 
-/* The smallest default dt of the nest's shells. */
+/* The smallest default dt of the nest's shells.  The coupling on the
+ * common spheres lowers the largest stable Courant factor below a lone
+ * shell's (measured on two 13x9x18 shells over [1.8, 6.8, 11.8] with the Yn
+ * filter per step: stable at 3.0 times the smallest spacing, unstable at
+ * 3.5, where one 13x9x18 shell is stable up to 6.0); callers that raise the
+ * shells' Courant factor set dt explicitly. */
 CFFYN_API double cffyn_nest_default_dt(const cffyn_nest* ns);
 
 /* Releases the nest (not its shells).  NULL is allowed. */
