@@ -25,7 +25,7 @@ static const TileEntry kTileTable[] = {
     {25, 24, 22, 50, 0, {48, 48, 48, 48, 48}},
     {33, 24, 22, 50, 0, {48, 48, 48, 48, 48}},
     {17, 32, 30, 50, 0, {48, 96, 96, 48, 96}},
-    {25, 32, 30, 50, 0, {48, 96, 48, 48, 96}},
+    {25, 32, 30, 50, 0, {48, 96, 96, 48, 96}},
     {33, 32, 30, 50, 0, {48, 96, 96, 48, 96}},
     {17, 48, 46, 50, 0, {48, 96, 96, 48, 96}},
     {25, 48, 46, 50, 0, {48, 96, 96, 48, 96}},
