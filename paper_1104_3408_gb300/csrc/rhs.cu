@@ -50,11 +50,13 @@ struct Slots {
 };
 
 constexpr int kRhsBlock = 128;
-constexpr int kGamSlots = 64;   // Gamma_cab (c*10 + s) | S_Pi 40..49 | g_ab 50..59 | C_a 60..63
+constexpr int kGamSlots = 54;   // Gamma_cab (c*10 + s) | S_Pi 40..49 | C_a 50..53
 constexpr int kQuadSlots = 50;  // Pi 0..9 | Phi_iab 10 + 10 i + s | Q 40..49
 
+// Four blocks per SM: 128 registers, 54 KB of slots (g_ab is read again from
+// u where the gauge terms need it instead of holding ten more slots).
 template <class T, bool FU, bool FO>
-__global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restrict__ u,
+__global__ void __launch_bounds__(kRhsBlock, 4) k_rhs_gamma(const double* __restrict__ u,
                                                          const double* __restrict__ H,
                                                          const double* __restrict__ dH,
                                                          double* __restrict__ src, double* __restrict__ out,
@@ -72,7 +74,6 @@ __global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restric
 #pragma unroll
     for (int s = 0; s < 10; ++s) {
       g[s] = ldA<T, FU>(u, P, p, s);
-      V(50 + s) = g[s];
     }
     metric_from(g, M);
   }
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restric
         }
       const T hc = c == 0 ? Hd[0] : (c == 1 ? Hd[1] : (c == 2 ? Hd[2] : Hd[3]));
       acc.add(hc);
-      V(60 + c) = acc.get();
+      V(50 + c) = acc.get();
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restric
 #pragma unroll
       for (int d = 0; d < 4; ++d) acc.fma_(M.gi4[SI(c, d)], Hd[d]);
       Hup[c] = acc.get();
-      an.fma_(M.nu[c], V(60 + c));
+      an.fma_(M.nu[c], V(50 + c));
     }
     nC = an.get();
   }
@@ -164,9 +165,9 @@ __global__ void __launch_bounds__(kRhsBlock) k_rhs_gamma(const double* __restric
       const T DH = acc.get();
       Acc<T> v;
       v.fma_(-twoal, DH);
-      v.fma_(-(anC), V(50 + s));
-      if (a == 0) v.fma_(aa, V(60 + b));
-      if (b == 0) v.fma_(aa, V(60 + a));
+      v.fma_(-(anC), ldA<T, FU>(u, P, p, s));
+      if (a == 0) v.fma_(aa, V(50 + b));
+      if (b == 0) v.fma_(aa, V(50 + a));
       V(40 + s) = v.get();
     }
   }
