@@ -156,7 +156,7 @@ struct Scratch {
   __device__ __forceinline__ T& operator()(int v) const { return s[v * 128 + (int)threadIdx.x]; }
 };
 constexpr int kDecSlots = 26;  // Trot_a (3 x 6) | (P_rm, P_mm) of legs 1, 2 (2 x 4)
-constexpr int kRecSlots = 36;  // Trot_A (3 x 6) | X_A (3 x 6)
+constexpr int kRecSlots = 18;  // Trot_A (3 x 6), each overwritten by its X_A
 
 // Slot assignment: 16 real spin-0 slots, then (re, im) pairs of spin 1 from
 // slot 16, of spin 2 from slot 38 and of spin 3 at slot 48; the numbers
@@ -432,7 +432,7 @@ __device__ __forceinline__ void reconstruct_group(int grp, Scratch<T> sc, const 
         Pmm[2][1] = half * (zr - xr);
       }
       // slots 6 A + q: the pair part Trot_A of triad leg A (q: rr, r1, r2,
-      // 11, 12, 22); slots 18 + 6 A + q: X_A, the pair back in Cartesian
+      // 11, 12, 22), then in its place X_A, the pair back in Cartesian
 #pragma unroll
       for (int A = 0; A < 3; ++A) {
         sc(6 * A + 0) = Pr[A];
@@ -453,7 +453,7 @@ __device__ __forceinline__ void reconstruct_group(int grp, Scratch<T> sc, const 
 #pragma unroll
         for (int b = 0; b < 3; ++b)
 #pragma unroll
-          for (int c = b; c < 3; ++c) sc(18 + 6 * A + SI(b + 1, c + 1) - 4) = X[b][c];
+          for (int c = b; c < 3; ++c) sc(6 * A + SI(b + 1, c + 1) - 4) = X[b][c];
       }
 #pragma unroll 1
       for (int a = 0; a < 3; ++a) {
@@ -461,7 +461,7 @@ __device__ __forceinline__ void reconstruct_group(int grp, Scratch<T> sc, const 
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           const int f = 20 + 10 * a + 4 + q;  // SI(b + 1, c + 1) = 4 + q
-          emit(f, r0 * sc(18 + q) + r1 * sc(24 + q) + r2 * sc(30 + q));
+          emit(f, r0 * sc(q) + r1 * sc(6 + q) + r2 * sc(12 + q));
         }
       }
     }
@@ -561,8 +561,12 @@ __device__ __forceinline__ void reconstruct_update(Scratch<T> sc, const double* 
   }
 }
 
+// Latency-bound (a few dependent loads and stores per field): eight blocks
+// per SM, i.e. at most 64 registers and 18 KB of slots per block (with 80
+// registers and 36 slots, six blocks: 0.423 -> 0.340 ms per step on the
+// 33 x 48 x 96 shell, same results).
 template <class T, bool FD, int KIND>
-__global__ void __launch_bounds__(128, 6) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
+__global__ void __launch_bounds__(128, 8) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
                                                      Geo geo, int mode, double* __restrict__ u,
                                                      double* __restrict__ U, double* __restrict__ kacc,
                                                      double* __restrict__ uf, double dt,
