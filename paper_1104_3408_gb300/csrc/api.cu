@@ -554,9 +554,11 @@ static int filter_in_step(cffyn_shell* sh, double* spin, cudaStream_t st, Run&& 
 
 // conc: the algebraic right-hand-side kernels (k_rhs_gamma, k_rhs_quad: they
 // read the stage state only) run on the shell's second stream beside the
-// exponent scan and the derivative launches, which they share no buffer
-// with, and join before the principal parts; not for the evolved gauge of
-// 54/58 fields (k_gauge_rhs reads the derivatives) nor under per-group timing.
+// d_theta + d_phi launch, which they share no buffer with, and join before
+// the principal parts; forked after d_r (forked at the start of the stage,
+// they held up the exponent scan and d_r: 3.233 vs 3.248 ms per step); not
+// for the evolved gauge of 54/58 fields (k_gauge_rhs reads the derivatives)
+// nor under per-group timing.
 template <class Run>
 static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&& run, bool conc) {
   const size_t nvP = (size_t)sh->nv * P_all(sh);
@@ -567,6 +569,8 @@ static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&&
   int rc;
   const bool fork = conc && sh->ng == 0 && sh->aux_stream;
   cudaStream_t sa = fork ? sh->aux_stream : st;
+  if ((rc = run(10, [&] { return op_prepare(sh, X, xp, nf, P, 0, st); }))) return rc;
+  if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, nf, xp, st); }))) return rc;
   if (fork) {
     CF_CUDA(cudaEventRecord(sh->ev_fork, st));
     CF_CUDA(cudaStreamWaitEvent(sa, sh->ev_fork, 0));
@@ -574,8 +578,6 @@ static int stage_front(cffyn_shell* sh, double* u, int s, cudaStream_t st, Run&&
     if ((rc = run(3, [&] { return pw_rhs_part(sh, X, sh->D, sh->S, 2, xp, true, sa); }))) return rc;
     CF_CUDA(cudaEventRecord(sh->ev_join, sa));
   }
-  if ((rc = run(10, [&] { return op_prepare(sh, X, xp, nf, P, 0, st); }))) return rc;
-  if ((rc = run(0, [&] { return op_deriv_r(sh, X, sh->D, nf, xp, st); }))) return rc;
   if ((rc = run(1, [&] { return op_deriv_theta_phi(sh, X, sh->D + nvP, sh->D + 2 * nvP, nf, xp, st); })))
     return rc;
   if (fork) {

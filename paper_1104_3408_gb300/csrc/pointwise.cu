@@ -561,12 +561,12 @@ __device__ __forceinline__ void reconstruct_update(Scratch<T> sc, const double* 
   }
 }
 
-// Latency-bound (a few dependent loads and stores per field): eight blocks
-// per SM, i.e. at most 64 registers and 18 KB of slots per block (with 80
-// registers and 36 slots, six blocks: 0.423 -> 0.340 ms per step on the
-// 33 x 48 x 96 shell, same results).
+// Latency-bound (a few dependent loads and stores per field): nine blocks
+// per SM, i.e. at most 56 registers and 18 KB of slots per block (with 80
+// registers and 36 slots, six blocks: 0.423 ms per step on the 33 x 48 x 96
+// shell; eight blocks, 64 registers: 0.340; nine: 0.335, same results).
 template <class T, bool FD, int KIND>
-__global__ void __launch_bounds__(128, 8) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
+__global__ void __launch_bounds__(128, 9) k_reconstruct(const double* __restrict__ sp, double* __restrict__ dst,
                                                      Geo geo, int mode, double* __restrict__ u,
                                                      double* __restrict__ U, double* __restrict__ kacc,
                                                      double* __restrict__ uf, double dt,
