@@ -278,6 +278,79 @@ class Shell:
         return a
 
 
+class HostStepper:
+    """RK4 steps of independent states held in pinned host memory, with the
+    host <-> device copies overlapped with the steps.
+
+    run(host_ins, host_outs, dt) steps every host_ins[i] once (n_steps RK4
+    steps) and writes the result into host_outs[i].  While problem i steps on
+    the given stream, problem i + 1 is copied in on a copy stream and the
+    result of problem i - 1 is copied out on another, so a sequence of
+    problems costs about the steps alone plus one copy in and one out.
+    The shell steps one fixed device buffer (its captured step graph stays
+    valid); two staging buffers of the state's size sit between it and the
+    copies, each moved with one device-to-device copy per problem.
+    Marshalling only: every step is cffyn_rk4_step.  host_ins / host_outs are
+    float64 CPU tensors of the state's shape, pinned for the copies to
+    overlap."""
+
+    def __init__(self, shell, like):
+        import torch
+        if not isinstance(like, torch.Tensor) or not like.is_cuda or like.dtype != torch.float64:
+            raise TypeError("like must be a float64 CUDA tensor of the state's shape")
+        self.sh = shell
+        self.state = torch.empty_like(like, memory_format=torch.contiguous_format)
+        self.stage_in = torch.empty_like(self.state)
+        self.stage_out = torch.empty_like(self.state)
+        self.h2d = torch.cuda.Stream(device=like.device)
+        self.d2h = torch.cuda.Stream(device=like.device)
+        self.ev_in = torch.cuda.Event()        # stage_in holds the next problem
+        self.ev_in_free = torch.cuda.Event()   # stage_in has been moved into the state
+        self.ev_out = torch.cuda.Event()       # stage_out holds the last result
+        self.ev_out_free = torch.cuda.Event()  # stage_out has been copied out
+
+    def run(self, host_ins, host_outs, dt=0.0, n_steps=1, stream=None):
+        import torch
+        n = len(host_ins)
+        if len(host_outs) != n:
+            raise ValueError("one output per input expected")
+        for t in list(host_ins) + list(host_outs):
+            if t.is_cuda or t.dtype != torch.float64 or t.shape != self.state.shape:
+                raise TypeError("host states must be float64 CPU tensors of the state's shape")
+        if n == 0:
+            return host_outs
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.h2d.wait_stream(st)
+        self.d2h.wait_stream(st)
+        with torch.cuda.stream(self.h2d):
+            self.stage_in.copy_(host_ins[0], non_blocking=True)
+            self.ev_in.record(self.h2d)
+        for i in range(n):
+            st.wait_event(self.ev_in)
+            with torch.cuda.stream(st):
+                self.state.copy_(self.stage_in, non_blocking=True)
+            self.ev_in_free.record(st)
+            if i + 1 < n:
+                # the next problem's copy in runs beside this step
+                with torch.cuda.stream(self.h2d):
+                    self.h2d.wait_event(self.ev_in_free)
+                    self.stage_in.copy_(host_ins[i + 1], non_blocking=True)
+                    self.ev_in.record(self.h2d)
+            self.sh.rk4_step(self.state, dt, n_steps, st)
+            st.wait_event(self.ev_out_free)
+            with torch.cuda.stream(st):
+                self.stage_out.copy_(self.state, non_blocking=True)
+            self.ev_out.record(st)
+            # this result's copy out runs beside the next step
+            with torch.cuda.stream(self.d2h):
+                self.d2h.wait_event(self.ev_out)
+                host_outs[i].copy_(self.stage_out, non_blocking=True)
+                self.ev_out_free.record(self.d2h)
+        st.wait_stream(self.h2d)
+        st.wait_stream(self.d2h)
+        return host_outs
+
+
 class Batch:
     """Independent shells advanced together (a cffyn_batch handle).  The
     batch borrows the Shell objects and keeps references to them."""
