@@ -64,6 +64,7 @@ struct OpArgs {
   int batched_m;         // projection launched for all m = 0..L at once
   long long w_stride;    // FP64 operator stride between consecutive m
   int ns;                // stacked shells: function f of shell s is array f * ns + s
+  int fld0;              // OP_ROWS: array index of the launch's first array (its exponent word, pairing)
 };
 
 __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
@@ -81,7 +82,7 @@ __device__ __forceinline__ ColDesc make_col(const OpArgs& a, long long c) {
     }
     case OP_ROWS: {
       long long b = c / a.Q, q = c - b * a.Q;
-      d.fld = (int)b;
+      d.fld = a.fld0 + (int)b;
       d.in0 = b * a.in_bs + q;
       d.out0 = b * a.out_bs + q;
       d.in1 = d.out1 = 0;
@@ -599,7 +600,9 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
     if (f >= kPairedFrom) ce = max(ce, exps[(f ^ 1) * a.ns + sidx]);
   }
   const int E = ce - 1022 + B.eoff;
-  if (tid < ROWS) rowF[tid] = pow2f(W.rowexp[grp * ROWS + tid]);
+  // the row exponents are needed only by the epilogue: loaded here, stored
+  // to shared memory before the barrier that ends the main loop
+  const int rexp = tid < ROWS ? W.rowexp[grp * ROWS + tid] : 0;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       tc::bar_init(&xfull[s], C::kProd);
@@ -738,6 +741,7 @@ __global__ void __launch_bounds__(TcCfg<ROWS>::kThreads) k_op_tc(TcBatch B, cons
       tc::bar_wait(&accf, 0, kTcWaitNs);
     }
   }
+  if (tid < ROWS) rowF[tid] = pow2f(rexp);
   ok = __syncthreads_and(ok);
   if (!ok && tid == 0) atomicOr(flag, 2);
   tc::fence_after();
@@ -989,9 +993,10 @@ int op_deriv_theta_phi(const cffyn_shell* sh, const double* in, double* out_th, 
 
 static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb, int K, int P,
                    long long in_bs, long long out_bs, const double* W, const TcOp* Wt, cudaStream_t st,
-                   int pairing, int eoff = 0) {
+                   int pairing, int eoff = 0, int fld0 = 0) {
   OpArgs a = base_args(sh);
   a.kind = OP_ROWS;
+  a.fld0 = fld0;
   a.in = in;
   a.out = out;
   a.Q = sh->N * sh->n_r;
@@ -1007,20 +1012,21 @@ static int op_rows(const cffyn_shell* sh, const double* in, double* out, int nb,
 }
 
 // phi analysis: S[f][j][i][k] -> C[f][row][i][k] (pair-stored input on the
-// mixed path); pairing: the exponents of slot pairs (f, f ^ 1) are shared
-// (the complex slots of the Yn filter)
-int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st, int pairing) {
+// mixed path) of the nf arrays f0 .. f0 + nf - 1; pairing: the exponents of
+// slot pairs (f, f ^ 1) are shared (the complex slots of the Yn filter)
+int op_dft_fwd(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st, int pairing,
+               int f0) {
   long long Q = (long long)sh->N * sh->n_r;
-  return op_rows(sh, in, out, nf, sh->J, sh->R, (long long)sh->J * Q, (long long)sh->R * Q, sh->Fan,
-                 &sh->tFan, st, pairing);
+  return op_rows(sh, in + (size_t)f0 * sh->J * Q, out + (size_t)f0 * sh->R * Q, nf, sh->J, sh->R,
+                 (long long)sh->J * Q, (long long)sh->R * Q, sh->Fan, &sh->tFan, st, pairing, 0, f0);
 }
 
 // eoff: see TcBatch (the coefficients' exponents are bounds, not a scan)
 int op_dft_inv(const cffyn_shell* sh, const double* in, double* out, int nf, cudaStream_t st, int pairing,
-               int eoff) {
+               int eoff, int f0) {
   long long Q = (long long)sh->N * sh->n_r;
-  return op_rows(sh, in, out, nf, sh->R, sh->J, (long long)sh->R * Q, (long long)sh->J * Q, sh->Fsy,
-                 &sh->tFsy, st, pairing, eoff);
+  return op_rows(sh, in + (size_t)f0 * sh->R * Q, out + (size_t)f0 * sh->J * Q, nf, sh->R, sh->J,
+                 (long long)sh->R * Q, (long long)sh->J * Q, sh->Fsy, &sh->tFsy, st, pairing, eoff, f0);
 }
 
 // Component-wise filters (Sec. 3.5): every field's coefficients projected
