@@ -51,6 +51,9 @@ def _args():
     ap.add_argument("--profile-step", action="store_true",
                     help="run one eager RK4 step with per-group device times and print them "
                          "(the fixed launch sequence used for profiler captures)")
+    ap.add_argument("--profile-graph", action="store_true",
+                    help="run one RK4 step through the captured step graph (as the timed steps run) "
+                         "and exit: the launch sequence of the launch-list capture")
     return ap.parse_args()
 
 
@@ -781,6 +784,28 @@ def run_profile_step(args):
             "launches": {k: n for k, (t, n) in prof.items()}}
 
 
+def run_graph_step(args):
+    """One RK4 step of the workload through cffyn_rk4_step (mixed path): the
+    gauge from the state, then the step graph's launches (the pair copy of the
+    state, then per stage its kernel nodes, the filter as two chains)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1104_3408_gb300 import cffyn
+
+    w = _workload(args.workload)
+    sh = cffyn.Shell(w["n_r"], w["n_theta"], w["n_phi"], w["r_in"], w["r_out"], w["L"],
+                     n_fields=w["n_fields"], precision=cffyn.MIXED)
+    u = torch.from_numpy(_state(w)).cuda()
+    sh.init_gauge_from_state(u)
+    sh.rk4_step(u, 0.0, 1)
+    torch.cuda.synchronize()
+    launches = sh.get_trace()[1]
+    sh.destroy()
+    return {"workload": w["name"], "launches": launches}
+
+
 def run_derivs_sweep(args):
     """Cartesian derivatives of 50 fields on shells n_r x n x 2n (n_r = n) by
     three methods: the split-precision matrices on the tensor cores (MIXED),
@@ -874,6 +899,9 @@ def main():
     args = _args()
     if args.profile_step:
         print(json.dumps(run_profile_step(args)), flush=True)
+        return
+    if args.profile_graph:
+        print(json.dumps(run_graph_step(args)), flush=True)
         return
     if args.sweep:
         print(json.dumps(run_derivs_sweep(args)), flush=True)
