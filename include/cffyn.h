@@ -190,6 +190,29 @@ CFFYN_API int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* 
  * (the results are then invalid; the context stays usable). */
 CFFYN_API int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream);
 
+/* cffyn_rk4_step (Sec. 2.5, the same steps and results) without the
+ * synchronisation at its end: the call enqueues the steps on `stream` and
+ * returns, so that the host can queue the next work (copies, the next
+ * problem's steps) while these run.  After the last step the steps' status
+ * word is copied on `stream` to *status, host memory the caller owns (pinned
+ * memory keeps the copy asynchronous); once the stream has passed that
+ * point, cffyn_step_status(*status) is what cffyn_rk4_step would have
+ * returned (CFFYN_OK, CFFYN_ENONFINITE or CFFYN_ETIMEOUT).  n_steps == 0
+ * runs nothing and writes a zero status word.  Errors found before anything
+ * is enqueued are returned at once: CFFYN_EINVAL for the arguments
+ * cffyn_rk4_step rejects, a NULL status or tracing switched on (the trace
+ * needs the synchronising call); CFFYN_ECUDA if the graph capture or a
+ * launch fails.  Like cffyn_rk4_step, the first call for a given (u, dt)
+ * captures the step graph and must not be made during a stream capture.
+ * Calls on one shell share its workspace: order them on one stream. */
+CFFYN_API int cffyn_rk4_step_async(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream,
+                                   int* status);
+
+/* The status code of a step status word written by cffyn_rk4_step_async:
+ * CFFYN_OK, CFFYN_ENONFINITE or CFFYN_ETIMEOUT (cffyn_last_error() then
+ * names the cause). */
+CFFYN_API int cffyn_step_status(int status_word);
+
 /* Batch of independent shells advanced together (the uneven-shell batch;
  * the shells need not share sizes, field counts, precision or filter mode).
  * Shells of one shape (n_r, n_theta, n_phi, r_in, r_out, L, n_fields,

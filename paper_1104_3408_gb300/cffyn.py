@@ -23,7 +23,8 @@ STATIC_SCRATCH_BYTES = 8 * 1024 * 1024   # CFFYN_STATIC_SCRATCH_BYTES
 EXPORTED = [
     "cffyn_create_shell", "cffyn_create_shell_ex", "cffyn_destroy", "cffyn_device_bytes",
     "cffyn_default_dt", "cffyn_set_gauge", "cffyn_init_gauge_from_state", "cffyn_derivs",
-    "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_constraint_norms",
+    "cffyn_rhs", "cffyn_filter", "cffyn_rk4_step", "cffyn_rk4_step_async", "cffyn_step_status",
+    "cffyn_constraint_norms",
     "cffyn_get_filter_matrix", "cffyn_get_operator", "cffyn_last_error", "cffyn_version",
     "cffyn_profile_step", "cffyn_set_trace", "cffyn_get_trace", "cffyn_derivs_static",
     "cffyn_set_wait_limit", "cffyn_set_operator_rows", "cffyn_get_operator_rows",
@@ -83,6 +84,8 @@ def load(path=LIB_PATH):
         "cffyn_rhs": ([vp, dp, dp, vp], i),
         "cffyn_filter": ([vp, dp, dp, vp], i),
         "cffyn_rk4_step": ([vp, dp, d, i, vp], i),
+        "cffyn_rk4_step_async": ([vp, dp, d, i, vp, vp], i),
+        "cffyn_step_status": ([i], i),
         "cffyn_constraint_norms": ([vp, dp, ctypes.POINTER(ctypes.c_double), vp], i),
         "cffyn_get_filter_matrix": ([vp, i, i, ctypes.POINTER(ctypes.c_double)], i),
         "cffyn_get_operator": ([vp, i, ctypes.POINTER(ctypes.c_double)], i),
@@ -115,6 +118,14 @@ def _check(rc):
     if rc != OK:
         raise CffynError(rc, load().cffyn_last_error().decode())
     return rc
+
+
+def check_status(status):
+    """Raise CffynError if a step status word (see Shell.rk4_step_async) is
+    not CFFYN_OK; status: an int32 CPU tensor or an int."""
+    words = status.tolist() if hasattr(status, "tolist") else [status]
+    for w in (words if isinstance(words, list) else [words]):
+        _check(load().cffyn_step_status(int(w)))
 
 
 def _ptr(t, what):
@@ -222,6 +233,18 @@ class Shell:
         _check(load().cffyn_rk4_step(self.h, _ptr(u, "u"), float(dt), int(n_steps), _stream(stream)))
         return u
 
+    def rk4_step_async(self, u, status, dt=0.0, n_steps=1, stream=None):
+        """Enqueue n_steps RK4 steps on the stream and return; the steps'
+        status word lands in status (an int32 CPU tensor, pinned for the copy
+        to stay asynchronous) in stream order: check_status(status) after
+        synchronising."""
+        import torch
+        if status.is_cuda or status.dtype != torch.int32 or status.numel() < 1:
+            raise TypeError("status must be an int32 CPU tensor")
+        _check(load().cffyn_rk4_step_async(self.h, _ptr(u, "u"), float(dt), int(n_steps), _stream(stream),
+                                           ctypes.c_void_p(status.data_ptr())))
+        return u
+
     def profile_step(self, u, dt=0.0, stream=None):
         """Per-phase device ms and launch counts of one eager RK4 step."""
         n = len(PROFILE_PHASES)
@@ -289,8 +312,11 @@ class HostStepper:
     problems costs about the steps alone plus one copy in and one out.
     The shell steps one fixed device buffer (its captured step graph stays
     valid); two staging buffers of the state's size sit between it and the
-    copies, each moved with one device-to-device copy per problem.
-    Marshalling only: every step is cffyn_rk4_step.  host_ins / host_outs are
+    copies, each moved with one device-to-device copy per problem.  The
+    steps are enqueued with cffyn_rk4_step_async, so the host queues every
+    problem's work without waiting; run() synchronises once at the end and
+    raises CffynError if any problem's steps reported an error.
+    Marshalling only: every step is the library's.  host_ins / host_outs are
     float64 CPU tensors of the state's shape, pinned for the copies to
     overlap."""
 
@@ -320,6 +346,7 @@ class HostStepper:
         if n == 0:
             return host_outs
         st = stream if stream is not None else torch.cuda.current_stream()
+        status = torch.zeros(n, dtype=torch.int32).pin_memory()
         self.h2d.wait_stream(st)
         self.d2h.wait_stream(st)
         with torch.cuda.stream(self.h2d):
@@ -336,7 +363,7 @@ class HostStepper:
                     self.h2d.wait_event(self.ev_in_free)
                     self.stage_in.copy_(host_ins[i + 1], non_blocking=True)
                     self.ev_in.record(self.h2d)
-            self.sh.rk4_step(self.state, dt, n_steps, st)
+            self.sh.rk4_step_async(self.state, status[i:i + 1], dt, n_steps, st)
             st.wait_event(self.ev_out_free)
             with torch.cuda.stream(st):
                 self.stage_out.copy_(self.state, non_blocking=True)
@@ -348,6 +375,8 @@ class HostStepper:
                 self.ev_out_free.record(self.d2h)
         st.wait_stream(self.h2d)
         st.wait_stream(self.d2h)
+        st.synchronize()
+        check_status(status)
         return host_outs
 
 

@@ -788,15 +788,9 @@ int check_state_ptr(const void* p, const char* what) { return check_ptr(p, what)
 }  // namespace cffyn
 }  // extern "C++"
 
-int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream) {
-  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
-  int rc;
-  if ((rc = check_ptr(u, "u"))) return rc;
-  if (n_steps < 0) { set_error("n_steps < 0"); return CFFYN_EINVAL; }
-  if ((rc = check_step_ready(sh))) return rc;
-  if (n_steps == 0) return CFFYN_OK;
-  if (!(dt > 0)) dt = sh->dt_default;
-  cudaStream_t st = (cudaStream_t)stream;
+// The captured step graph for (u, dt) and the shell's trace setting: kept
+// when it matches, else captured and instantiated anew.
+static int step_graph(cffyn_shell* sh, double* u, double dt) {
   if (!sh->graph || sh->graph_u != u || sh->graph_dt != dt || sh->graph_trace != sh->trace) {
     if (sh->graph) {
       cudaGraphExecDestroy(sh->graph);
@@ -822,6 +816,46 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
     sh->graph_dt = dt;
     sh->graph_trace = sh->trace;
   }
+  return CFFYN_OK;
+}
+
+// Argument checks shared by the synchronous and asynchronous step calls.
+static int check_step_call(cffyn_shell* sh, double* u, int n_steps) {
+  if (!sh) { set_error("shell is NULL"); return CFFYN_EINVAL; }
+  int rc;
+  if ((rc = check_ptr(u, "u"))) return rc;
+  if (n_steps < 0) { set_error("n_steps < 0"); return CFFYN_EINVAL; }
+  return check_step_ready(sh);
+}
+
+int cffyn_rk4_step_async(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream, int* status) {
+  int rc;
+  if ((rc = check_step_call(sh, u, n_steps))) return rc;
+  if (!status) { set_error("status is NULL"); return CFFYN_EINVAL; }
+  if (sh->trace) { set_error("tracing is on: use cffyn_rk4_step"); return CFFYN_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n_steps == 0) {
+    // nothing runs; the status word still arrives in stream order
+    CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
+  } else {
+    if (!(dt > 0)) dt = sh->dt_default;
+    if ((rc = step_graph(sh, u, dt))) return rc;
+    if ((rc = enqueue_step_prologue(sh, u, st))) return rc;
+    for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
+  }
+  CF_CUDA(cudaMemcpyAsync(status, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return CFFYN_OK;
+}
+
+int cffyn_step_status(int status_word) { return step_flag_status(status_word); }
+
+int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* stream) {
+  int rc;
+  if ((rc = check_step_call(sh, u, n_steps))) return rc;
+  if (n_steps == 0) return CFFYN_OK;
+  if (!(dt > 0)) dt = sh->dt_default;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((rc = step_graph(sh, u, dt))) return rc;
   if ((rc = enqueue_step_prologue(sh, u, st))) return rc;
   for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
   CF_CUDA(cudaMemcpyAsync(sh->flag_host, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
