@@ -222,11 +222,16 @@ def test_trace_and_profile_report_every_kernel_group(cf):
     # and of its filter's input (the filter's later operators take bounds)
     assert launches["d_theta_phi"] == 4 and launches["rhs_pp"] == 4
     assert launches["project"] == 4 and launches["d_r"] == 4 and launches["field_exp"] == 8
-    # tracing does not change the result
+    # tracing does not change the result: the untraced graph runs the Yn
+    # filter's three operator launches as two chains on two streams (twice
+    # the launches), the traced one as one chain, with bitwise equal results
     v = dev(u0)
     w = dev(u0)
     sh.set_trace(False)
     sh.rk4_step(v, 0.0, 2)
+    plain = sh.get_trace()[1]
+    assert plain["project"] == 8 and plain["dft_fwd"] == 8 and plain["dft_inv"] == 8
+    assert plain["d_theta_phi"] == 4 and plain["field_exp"] == 8
     sh.set_trace(True)
     sh.rk4_step(w, 0.0, 2)
     assert torch.equal(v, w)
