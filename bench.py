@@ -641,23 +641,39 @@ def run_batch(args, rank, local_rank, ws, dist):
 
     # ---- end to end with host buffers: copy in, one batch step, copy out
     hs = [u.cpu().pin_memory() for u in us]
+    hout = [torch.empty_like(h).pin_memory() for h in hs]
     ke = 3
-    b.rk4_step(us, None, 1)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(ke):
-        for u, h in zip(us, hs):
-            u.copy_(h, non_blocking=True)
-        b.rk4_step(us, None, 1)
-        for u, h in zip(us, hs):
-            h.copy_(u, non_blocking=True)
-    e1.record(st)
-    torch.cuda.synchronize()
+
+    def timed_e2e(fn):
+        fn(1)  # captures the step graphs for these state buffers
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn(ke)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    hstep = cffyn.HostStepper(b, us)
+    ms_pipe = timed_e2e(lambda n: hstep.run([hs] * n, [hout] * n, None, 1, st))
+
+    def serial(n):
+        for _ in range(n):
+            for u, h in zip(us, hs):
+                u.copy_(h, non_blocking=True)
+            b.rk4_step(us, None, 1)
+            for u, h in zip(us, hout):
+                h.copy_(u, non_blocking=True)
+    ms_ser = timed_e2e(serial)
+    del hstep
     nbytes = int(sum(u.numel() for u in us) * 8)
-    e2e = {"value": units * ke / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
-           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": ke}
+    e2e = {"value": units * ke / (ms_pipe * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": ke,
+           "how": "cffyn.HostStepper over the batch: ke independent batch problems from pinned host "
+                  "memory, each problem's copies overlapped with the neighbouring problems' steps",
+           "serial": {"value": units * ke / (ms_ser * 1e-3),
+                      "how": "copy in, batch step, copy out in turn on one stream"}}
 
     # ---- whole-step tensor roofline (a lower bound of the operator family's share)
     hbm, bf16s, peak_kind = _peaks()

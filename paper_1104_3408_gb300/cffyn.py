@@ -305,73 +305,101 @@ class HostStepper:
     """RK4 steps of independent states held in pinned host memory, with the
     host <-> device copies overlapped with the steps.
 
-    run(host_ins, host_outs, dt) steps every host_ins[i] once (n_steps RK4
-    steps) and writes the result into host_outs[i].  While problem i steps on
-    the given stream, problem i + 1 is copied in on a copy stream and the
-    result of problem i - 1 is copied out on another, so a sequence of
-    problems costs about the steps alone plus one copy in and one out.
-    The shell steps one fixed device buffer (its captured step graph stays
-    valid); two staging buffers of the state's size sit between it and the
-    copies, each moved with one device-to-device copy per problem.  The
-    steps are enqueued with cffyn_rk4_step_async, so the host queues every
-    problem's work without waiting; run() synchronises once at the end and
-    raises CffynError if any problem's steps reported an error.
-    Marshalling only: every step is the library's.  host_ins / host_outs are
-    float64 CPU tensors of the state's shape, pinned for the copies to
-    overlap."""
+    stepper is a Shell (one state per problem; like: a device tensor of the
+    state's shape) or a Batch (one state per member shell; like: the list of
+    the members' device states).  run(host_ins, host_outs, dt) steps every
+    problem host_ins[i] once (n_steps RK4 steps) and writes the result into
+    host_outs[i]; for a Batch each problem is a list of the members' host
+    states and dt the members' dts (None: each shell's default).  While
+    problem i steps on the given stream, problem i + 1 is copied in on a copy
+    stream and the result of problem i - 1 is copied out on another, so a
+    sequence of problems costs about the steps alone plus one copy in and one
+    out.  The stepper always steps one fixed set of device buffers (its
+    captured step graphs stay valid); two staging sets of the same size sit
+    between them and the copies, each moved with one device-to-device copy
+    per problem.  A Shell's steps are enqueued with cffyn_rk4_step_async, so
+    the host queues every problem's work without waiting; a Batch's step
+    call synchronises, and the copies of the neighbouring problems still run
+    beside it.  run() synchronises once at the end and raises CffynError if
+    any problem's steps reported an error.  Marshalling only: every step is
+    the library's.  Host states are float64 CPU tensors of the device
+    states' shapes, pinned for the copies to overlap."""
 
-    def __init__(self, shell, like):
+    def __init__(self, stepper, like):
         import torch
-        if not isinstance(like, torch.Tensor) or not like.is_cuda or like.dtype != torch.float64:
-            raise TypeError("like must be a float64 CUDA tensor of the state's shape")
-        self.sh = shell
-        self.state = torch.empty_like(like, memory_format=torch.contiguous_format)
-        self.stage_in = torch.empty_like(self.state)
-        self.stage_out = torch.empty_like(self.state)
-        self.h2d = torch.cuda.Stream(device=like.device)
-        self.d2h = torch.cuda.Stream(device=like.device)
+        self.sh = stepper
+        self.batch = isinstance(stepper, Batch)
+        likes = list(like) if self.batch else [like]
+        if self.batch and len(likes) != len(stepper.shells):
+            raise ValueError(f"{len(stepper.shells)} member states expected")
+        for t in likes:
+            if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+                raise TypeError("like must be float64 CUDA tensors of the states' shapes")
+        self.state = [torch.empty_like(t, memory_format=torch.contiguous_format) for t in likes]
+        self.stage_in = [torch.empty_like(t) for t in self.state]
+        self.stage_out = [torch.empty_like(t) for t in self.state]
+        dev = likes[0].device
+        self.h2d = torch.cuda.Stream(device=dev)
+        self.d2h = torch.cuda.Stream(device=dev)
         self.ev_in = torch.cuda.Event()        # stage_in holds the next problem
         self.ev_in_free = torch.cuda.Event()   # stage_in has been moved into the state
         self.ev_out = torch.cuda.Event()       # stage_out holds the last result
         self.ev_out_free = torch.cuda.Event()  # stage_out has been copied out
 
-    def run(self, host_ins, host_outs, dt=0.0, n_steps=1, stream=None):
+    def _members(self, h):
+        hs = list(h) if self.batch else [h]
+        if len(hs) != len(self.state):
+            raise ValueError(f"{len(self.state)} host states per problem expected")
+        return hs
+
+    def run(self, host_ins, host_outs, dt=None, n_steps=1, stream=None):
         import torch
         n = len(host_ins)
         if len(host_outs) != n:
             raise ValueError("one output per input expected")
-        for t in list(host_ins) + list(host_outs):
-            if t.is_cuda or t.dtype != torch.float64 or t.shape != self.state.shape:
-                raise TypeError("host states must be float64 CPU tensors of the state's shape")
+        ins = [self._members(h) for h in host_ins]
+        outs = [self._members(h) for h in host_outs]
+        for prob in ins + outs:
+            for t, ref in zip(prob, self.state):
+                if t.is_cuda or t.dtype != torch.float64 or t.shape != ref.shape:
+                    raise TypeError("host states must be float64 CPU tensors of the states' shapes")
         if n == 0:
             return host_outs
         st = stream if stream is not None else torch.cuda.current_stream()
         status = torch.zeros(n, dtype=torch.int32).pin_memory()
+
+        def copy(dst, src):
+            for d, s_ in zip(dst, src):
+                d.copy_(s_, non_blocking=True)
+
         self.h2d.wait_stream(st)
         self.d2h.wait_stream(st)
         with torch.cuda.stream(self.h2d):
-            self.stage_in.copy_(host_ins[0], non_blocking=True)
+            copy(self.stage_in, ins[0])
             self.ev_in.record(self.h2d)
         for i in range(n):
             st.wait_event(self.ev_in)
             with torch.cuda.stream(st):
-                self.state.copy_(self.stage_in, non_blocking=True)
+                copy(self.state, self.stage_in)
             self.ev_in_free.record(st)
             if i + 1 < n:
                 # the next problem's copy in runs beside this step
                 with torch.cuda.stream(self.h2d):
                     self.h2d.wait_event(self.ev_in_free)
-                    self.stage_in.copy_(host_ins[i + 1], non_blocking=True)
+                    copy(self.stage_in, ins[i + 1])
                     self.ev_in.record(self.h2d)
-            self.sh.rk4_step_async(self.state, status[i:i + 1], dt, n_steps, st)
+            if self.batch:
+                self.sh.rk4_step(self.state, dt, n_steps, st)
+            else:
+                self.sh.rk4_step_async(self.state[0], status[i:i + 1], 0.0 if dt is None else dt, n_steps, st)
             st.wait_event(self.ev_out_free)
             with torch.cuda.stream(st):
-                self.stage_out.copy_(self.state, non_blocking=True)
+                copy(self.stage_out, self.state)
             self.ev_out.record(st)
             # this result's copy out runs beside the next step
             with torch.cuda.stream(self.d2h):
                 self.d2h.wait_event(self.ev_out)
-                host_outs[i].copy_(self.stage_out, non_blocking=True)
+                copy(outs[i], self.stage_out)
                 self.ev_out_free.record(self.d2h)
         st.wait_stream(self.h2d)
         st.wait_stream(self.d2h)

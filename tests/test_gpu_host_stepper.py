@@ -72,3 +72,36 @@ def test_host_stepper_rejects_bad_arguments(cffyn):
         hs.run([good], [], 0.0)
     assert hs.run([], [], 0.0) == []
     sh.destroy()
+
+
+def test_host_stepper_over_a_batch(cffyn):
+    # three shells, two of one shape (a stacked class) and one of another;
+    # each problem is the list of the three members' states
+    shapes = [(9, 12, 24, 10), (9, 12, 24, 10), (5, 6, 12, 4)]
+    shells = [cffyn.Shell(n_r, N, J, 1.8, 11.0, L) for n_r, N, J, L in shapes]
+    problems = []
+    for q in range(3):
+        problems.append([inputs.kerr_schild_state(n_r, N, J, 1.8, 11.0, amp=10.0 ** (-3 - q), ell=2,
+                                                  seed=10 * q + i)
+                         for i, (n_r, N, J, L) in enumerate(shapes)])
+    devs = [torch.from_numpy(s).cuda() for s in problems[0]]
+    for sh, d in zip(shells, devs):
+        sh.init_gauge_from_state(d)
+    b = cffyn.Batch(shells)
+    want = []
+    for prob in problems:
+        vs = [torch.from_numpy(s).cuda() for s in prob]
+        b.rk4_step(vs, None, 2)
+        want.append([v.cpu().numpy() for v in vs])
+    hs = cffyn.HostStepper(b, devs)
+    hins = [[torch.from_numpy(s).pin_memory() for s in prob] for prob in problems]
+    houts = [[torch.full_like(h, float("nan")).pin_memory() for h in prob] for prob in hins]
+    hs.run(hins, houts, None, 2)
+    for got, ref in zip(houts, want):
+        for g, r in zip(got, ref):
+            assert np.array_equal(g.numpy(), r)
+    with pytest.raises(ValueError):
+        hs.run([hins[0][:2]], [houts[0][:2]])
+    b.destroy()
+    for sh in shells:
+        sh.destroy()
