@@ -431,7 +431,9 @@ def run_ours(args, rank, local_rank, ws, dist, acc_steps=100):
     if not args.no_cpu_baseline and ws == 1:
         cpu = _cpu_baseline(w, u0)
 
-    launches_per_step = sum(launches_plain.values())
+    # the step graph's kernel nodes, plus the pair copy of the state that
+    # every mixed-path step call launches ahead of the graph (k_to_store)
+    launches_per_step = sum(launches_plain.values()) + 1
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
