@@ -137,7 +137,7 @@ CFFYN_API size_t cffyn_workspace_size(const cffyn_shell* sh);
  * is attached) the shell's workspace, and frees the workspace the library
  * allocated, if any.  ptr == NULL gives the shell a library-allocated
  * workspace again.  Synchronises the device first (no call of this shell may
- * be in flight); drops the captured step graph (the next cffyn_rk4_step
+ * be in flight); drops the captured step graphs (the next cffyn_rk4_step
  * recaptures; so does a batch holding the shell).  Not during a stream
  * capture.  CFFYN_EINVAL for a misaligned or short buffer. */
 CFFYN_API int cffyn_attach_workspace(cffyn_shell* sh, void* ptr, size_t bytes);
@@ -182,8 +182,10 @@ CFFYN_API int cffyn_filter(cffyn_shell* sh, const double* u, double* out, void* 
  * with the shell's filter mode; dt <= 0 selects cffyn_default_dt.  In
  * CFFYN_FILTER_SUBSTEP mode every stage right-hand side is filtered after the
  * boundary condition; the caller filters the initial data once.  The first
- * call captures one step in a CUDA graph (so it must not itself be made during
- * a stream capture); later calls with the same u and dt replay it.  The call
+ * call for a given (u, dt) captures one step in a CUDA graph (so it must not
+ * itself be made during a stream capture); the shell keeps the graphs of the
+ * two most recently used (u, dt) pairs (and trace settings), so later calls
+ * with either replay it, e.g. a caller alternating two state buffers.  The call
  * synchronises `stream` at its end to read the fused finiteness flag and
  * returns CFFYN_ENONFINITE if a stage right-hand side was not finite, or
  * CFFYN_ETIMEOUT if a bounded wait of a tensor-core operator kernel gave up
@@ -340,7 +342,7 @@ CFFYN_API int cffyn_profile_step(cffyn_shell* sh, double* u, double dt, double* 
  * the rule (48 up to 48 operator rows, else 96).  Shapes measured by the
  * library's tuner get their fastest choice at creation.  Rebuilds the
  * family's split operators (synchronises the device; not during a stream
- * capture) and drops the captured step graph.  The results of the two
+ * capture) and drops the captured step graphs.  The results of the two
  * choices agree to the mixed path's rounding (the digit sums of the tensor
  * cores are exact, their FP32 tail is not).  CFFYN_EINVAL for another family
  * or size; a no-op on the FP64 path apart from recording the choice.
@@ -358,7 +360,7 @@ CFFYN_API int cffyn_get_operator_rows(const cffyn_shell* sh, int family);
  * every such wait give up at once without polling, the way to exercise the
  * CFFYN_ETIMEOUT path.  The waits that let copies and products already in
  * flight finish before a kernel block exits keep the 1 s bound whatever the
- * setting.  Drops the shell's captured step graph (the next step
+ * setting.  Drops the shell's captured step graphs (the next step
  * recaptures; so does a batch holding the shell).  CFFYN_EINVAL for more
  * than 60 s or NaN. */
 CFFYN_API int cffyn_set_wait_limit(cffyn_shell* sh, double seconds);
@@ -367,7 +369,8 @@ CFFYN_API int cffyn_set_wait_limit(cffyn_shell* sh, double seconds);
  * records a CUDA event after every kernel group (same groups as
  * cffyn_profile_step) and each cffyn_rk4_step call adds the group durations
  * of its last replay (times n_steps) to per-group totals.  Switching tracing
- * on or off resets the totals and re-captures the graph on the next step. */
+ * on or off resets the totals; the next step replays the traced or untraced
+ * graph of its (u, dt) if the shell still keeps it, else captures it. */
 CFFYN_API int cffyn_set_trace(cffyn_shell* sh, int on);
 /* Per-group totals in ms, kernel launches per step per group, and the number
  * of traced steps.  Host memory, CFFYN_PROFILE_PHASES entries each. */

@@ -314,16 +314,20 @@ class HostStepper:
     problem i steps on the given stream, problem i + 1 is copied in on a copy
     stream and the result of problem i - 1 is copied out on another, so a
     sequence of problems costs about the steps alone plus one copy in and one
-    out.  The stepper always steps one fixed set of device buffers (its
-    captured step graphs stay valid); two staging sets of the same size sit
-    between them and the copies, each moved with one device-to-device copy
-    per problem.  A Shell's steps are enqueued with cffyn_rk4_step_async, so
-    the host queues every problem's work without waiting; a Batch's step
-    call synchronises, and the copies of the neighbouring problems still run
-    beside it.  run() synchronises once at the end and raises CffynError if
-    any problem's steps reported an error.  Marshalling only: every step is
-    the library's.  Host states are float64 CPU tensors of the device
-    states' shapes, pinned for the copies to overlap."""
+    out.
+
+    A Shell alternates two device state buffers (the shell keeps a step
+    graph for each) and enqueues its steps with cffyn_rk4_step_async, so the
+    host queues every problem's work without waiting and the copies go
+    straight to and from the buffer being stepped.  A Batch steps one fixed
+    set of member buffers (its graphs are captured for one set), with two
+    staging sets between them and the copies, each moved with one
+    device-to-device copy per problem; its step call synchronises and the
+    neighbouring problems' copies run beside it.  run() synchronises once at
+    the end and raises CffynError if any problem's steps reported an error.
+    Marshalling only: every step is the library's.  Host states are float64
+    CPU tensors of the device states' shapes, pinned for the copies to
+    overlap."""
 
     def __init__(self, stepper, like):
         import torch
@@ -335,22 +339,28 @@ class HostStepper:
         for t in likes:
             if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
                 raise TypeError("like must be float64 CUDA tensors of the states' shapes")
-        self.state = [torch.empty_like(t, memory_format=torch.contiguous_format) for t in likes]
-        self.stage_in = [torch.empty_like(t) for t in self.state]
-        self.stage_out = [torch.empty_like(t) for t in self.state]
+        self.shapes = [t.shape for t in likes]
+        new = lambda: [torch.empty_like(t, memory_format=torch.contiguous_format) for t in likes]  # noqa: E731
+        if self.batch:
+            self.state, self.stage_in, self.stage_out = new(), new(), new()
+        else:
+            self.bufs = [new(), new()]
         dev = likes[0].device
         self.h2d = torch.cuda.Stream(device=dev)
         self.d2h = torch.cuda.Stream(device=dev)
-        self.ev_in = torch.cuda.Event()        # stage_in holds the next problem
-        self.ev_in_free = torch.cuda.Event()   # stage_in has been moved into the state
-        self.ev_out = torch.cuda.Event()       # stage_out holds the last result
-        self.ev_out_free = torch.cuda.Event()  # stage_out has been copied out
+        ev = lambda: [torch.cuda.Event(), torch.cuda.Event()]  # noqa: E731
+        self.ev_in, self.ev_done, self.ev_free = ev(), ev(), ev()
 
     def _members(self, h):
         hs = list(h) if self.batch else [h]
-        if len(hs) != len(self.state):
-            raise ValueError(f"{len(self.state)} host states per problem expected")
+        if len(hs) != len(self.shapes):
+            raise ValueError(f"{len(self.shapes)} host states per problem expected")
         return hs
+
+    @staticmethod
+    def _copy(dst, src):
+        for d, s_ in zip(dst, src):
+            d.copy_(s_, non_blocking=True)
 
     def run(self, host_ins, host_outs, dt=None, n_steps=1, stream=None):
         import torch
@@ -360,52 +370,72 @@ class HostStepper:
         ins = [self._members(h) for h in host_ins]
         outs = [self._members(h) for h in host_outs]
         for prob in ins + outs:
-            for t, ref in zip(prob, self.state):
-                if t.is_cuda or t.dtype != torch.float64 or t.shape != ref.shape:
+            for t, shape in zip(prob, self.shapes):
+                if t.is_cuda or t.dtype != torch.float64 or t.shape != shape:
                     raise TypeError("host states must be float64 CPU tensors of the states' shapes")
         if n == 0:
             return host_outs
         st = stream if stream is not None else torch.cuda.current_stream()
-        status = torch.zeros(n, dtype=torch.int32).pin_memory()
-
-        def copy(dst, src):
-            for d, s_ in zip(dst, src):
-                d.copy_(s_, non_blocking=True)
-
         self.h2d.wait_stream(st)
         self.d2h.wait_stream(st)
-        with torch.cuda.stream(self.h2d):
-            copy(self.stage_in, ins[0])
-            self.ev_in.record(self.h2d)
-        for i in range(n):
-            st.wait_event(self.ev_in)
-            with torch.cuda.stream(st):
-                copy(self.state, self.stage_in)
-            self.ev_in_free.record(st)
-            if i + 1 < n:
-                # the next problem's copy in runs beside this step
-                with torch.cuda.stream(self.h2d):
-                    self.h2d.wait_event(self.ev_in_free)
-                    copy(self.stage_in, ins[i + 1])
-                    self.ev_in.record(self.h2d)
-            if self.batch:
-                self.sh.rk4_step(self.state, dt, n_steps, st)
-            else:
-                self.sh.rk4_step_async(self.state[0], status[i:i + 1], 0.0 if dt is None else dt, n_steps, st)
-            st.wait_event(self.ev_out_free)
-            with torch.cuda.stream(st):
-                copy(self.stage_out, self.state)
-            self.ev_out.record(st)
-            # this result's copy out runs beside the next step
-            with torch.cuda.stream(self.d2h):
-                self.d2h.wait_event(self.ev_out)
-                copy(outs[i], self.stage_out)
-                self.ev_out_free.record(self.d2h)
+        status = torch.zeros(n, dtype=torch.int32).pin_memory()
+        if self.batch:
+            self._run_staged(ins, outs, dt, n_steps, st)
+        else:
+            self._run_alternating(ins, outs, 0.0 if dt is None else dt, n_steps, st, status)
         st.wait_stream(self.h2d)
         st.wait_stream(self.d2h)
         st.synchronize()
         check_status(status)
         return host_outs
+
+    def _run_alternating(self, ins, outs, dt, n_steps, st, status):
+        import torch
+        for i in range(len(ins)):
+            b = i % 2
+            buf = self.bufs[b]
+            # copy in once the copy out of problem i - 2 has read this buffer
+            with torch.cuda.stream(self.h2d):
+                self.h2d.wait_event(self.ev_free[b])
+                self._copy(buf, ins[i])
+                self.ev_in[b].record(self.h2d)
+            st.wait_event(self.ev_in[b])
+            self.sh.rk4_step_async(buf[0], status[i:i + 1], dt, n_steps, st)
+            self.ev_done[b].record(st)
+            with torch.cuda.stream(self.d2h):
+                self.d2h.wait_event(self.ev_done[b])
+                self._copy(outs[i], buf)
+                self.ev_free[b].record(self.d2h)
+
+    def _run_staged(self, ins, outs, dts, n_steps, st):
+        import torch
+        # ev_in[0]: stage_in holds the next problem; ev_done[0]: stage_in has
+        # been moved into the state; ev_in[1]: stage_out holds the last
+        # result; ev_free[1]: stage_out has been copied out
+        with torch.cuda.stream(self.h2d):
+            self._copy(self.stage_in, ins[0])
+            self.ev_in[0].record(self.h2d)
+        for i in range(len(ins)):
+            st.wait_event(self.ev_in[0])
+            with torch.cuda.stream(st):
+                self._copy(self.state, self.stage_in)
+            self.ev_done[0].record(st)
+            if i + 1 < len(ins):
+                # the next problem's copy in runs beside this step
+                with torch.cuda.stream(self.h2d):
+                    self.h2d.wait_event(self.ev_done[0])
+                    self._copy(self.stage_in, ins[i + 1])
+                    self.ev_in[0].record(self.h2d)
+            self.sh.rk4_step(self.state, dts, n_steps, st)
+            st.wait_event(self.ev_free[1])
+            with torch.cuda.stream(st):
+                self._copy(self.stage_out, self.state)
+            self.ev_in[1].record(st)
+            # this result's copy out runs beside the next step
+            with torch.cuda.stream(self.d2h):
+                self.d2h.wait_event(self.ev_in[1])
+                self._copy(outs[i], self.stage_out)
+                self.ev_free[1].record(self.d2h)
 
 
 class Batch:

@@ -63,6 +63,16 @@ static_assert(cffyn_shell::kPhases == CFFYN_PROFILE_PHASES, "phase count of the 
 
 namespace {
 
+// Destroy the kept step graphs (their parameters changed: workspace, wait
+// bound, operator row groups); a replay still in flight completes first.
+void drop_step_graphs(cffyn_shell* sh) {
+  for (int e = 0; e < cffyn_shell::kStepGraphs; ++e) {
+    if (sh->graphs[e].exec) cudaGraphExecDestroy(sh->graphs[e].exec);
+    sh->graphs[e] = cffyn_shell::StepGraph{};
+  }
+  sh->graph_victim = 0;
+}
+
 const int* slots_r0(const cffyn_shell* sh) { return sh->slots; }
 const int* slots_c(const cffyn_shell* sh, int s) {
   int o = sh->nR0;
@@ -172,7 +182,7 @@ void free_shell(cffyn_shell* sh) {
   if (sh->ev_join) cudaEventDestroy(sh->ev_join);
   if (sh->flag_host) cudaFreeHost(sh->flag_host);
   if (sh->flag) cudaFree(sh->flag);
-  if (sh->graph) cudaGraphExecDestroy(sh->graph);
+  drop_step_graphs(sh);
   for (int i = 0; i < cffyn_shell::kMaxMarks; ++i)
     if (sh->marks[i]) cudaEventDestroy(sh->marks[i]);
   fft_release(sh);
@@ -424,10 +434,7 @@ int cffyn_attach_workspace(cffyn_shell* sh, void* ptr, size_t bytes) {
   sh->ws_owned = !ptr;
   if (!ptr) sh->bytes += sh->ws_bytes;
   carve_workspace(sh, ptr ? ptr : fresh);
-  if (sh->graph) {
-    cudaGraphExecDestroy(sh->graph);
-    sh->graph = nullptr;
-  }
+  drop_step_graphs(sh);
   ++sh->ws_gen;
   return CFFYN_OK;
 }
@@ -788,34 +795,50 @@ int check_state_ptr(const void* p, const char* what) { return check_ptr(p, what)
 }  // namespace cffyn
 }  // extern "C++"
 
-// The captured step graph for (u, dt) and the shell's trace setting: kept
-// when it matches, else captured and instantiated anew.
-static int step_graph(cffyn_shell* sh, double* u, double dt) {
-  if (!sh->graph || sh->graph_u != u || sh->graph_dt != dt || sh->graph_trace != sh->trace) {
-    if (sh->graph) {
-      cudaGraphExecDestroy(sh->graph);
-      sh->graph = nullptr;
+// The captured step graph for (u, dt) and the shell's trace setting: one of
+// the two kept (the shell's mark table and launch counts then describe it),
+// else captured and instantiated in place of the less recently used one.
+static int step_graph(cffyn_shell* sh, double* u, double dt, cudaGraphExec_t* out) {
+  for (int e = 0; e < cffyn_shell::kStepGraphs; ++e) {
+    cffyn_shell::StepGraph& g = sh->graphs[e];
+    if (g.exec && g.u == u && g.dt == dt && g.trace == sh->trace) {
+      sh->n_marks = g.n_marks;
+      for (int i = 0; i < cffyn_shell::kMaxMarks; ++i) sh->mark_phase[i] = g.mark_phase[i];
+      for (int k = 0; k < cffyn_shell::kPhases; ++k) sh->launches_per_step[k] = g.launches[k];
+      sh->graph_victim = (e + 1) % cffyn_shell::kStepGraphs;
+      *out = g.exec;
+      return CFFYN_OK;
     }
-    cudaGraph_t g;
-    CF_CUDA(cudaStreamBeginCapture(sh->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int erc = enqueue_step(sh, u, dt, sh->cap_stream);
-    cudaError_t ce = cudaStreamEndCapture(sh->cap_stream, &g);
-    if (erc) return erc;
-    if (ce != cudaSuccess) {
-      set_error("graph capture failed: %s", cudaGetErrorString(ce));
-      return CFFYN_ECUDA;
-    }
-    ce = cudaGraphInstantiate(&sh->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (ce != cudaSuccess) {
-      sh->graph = nullptr;
-      set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
-      return CFFYN_ECUDA;
-    }
-    sh->graph_u = u;
-    sh->graph_dt = dt;
-    sh->graph_trace = sh->trace;
   }
+  cffyn_shell::StepGraph& g = sh->graphs[sh->graph_victim];
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);  // a replay still in flight completes first
+    g.exec = nullptr;
+  }
+  cudaGraph_t cg;
+  CF_CUDA(cudaStreamBeginCapture(sh->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int erc = enqueue_step(sh, u, dt, sh->cap_stream);
+  cudaError_t ce = cudaStreamEndCapture(sh->cap_stream, &cg);
+  if (erc) return erc;
+  if (ce != cudaSuccess) {
+    set_error("graph capture failed: %s", cudaGetErrorString(ce));
+    return CFFYN_ECUDA;
+  }
+  ce = cudaGraphInstantiate(&g.exec, cg, 0);
+  cudaGraphDestroy(cg);
+  if (ce != cudaSuccess) {
+    g.exec = nullptr;
+    set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
+    return CFFYN_ECUDA;
+  }
+  g.u = u;
+  g.dt = dt;
+  g.trace = sh->trace;
+  g.n_marks = sh->n_marks;
+  for (int i = 0; i < cffyn_shell::kMaxMarks; ++i) g.mark_phase[i] = sh->mark_phase[i];
+  for (int k = 0; k < cffyn_shell::kPhases; ++k) g.launches[k] = sh->launches_per_step[k];
+  sh->graph_victim = (sh->graph_victim + 1) % cffyn_shell::kStepGraphs;
+  *out = g.exec;
   return CFFYN_OK;
 }
 
@@ -839,9 +862,10 @@ int cffyn_rk4_step_async(cffyn_shell* sh, double* u, double dt, int n_steps, voi
     CF_CUDA(cudaMemsetAsync(sh->flag, 0, sizeof(int), st));
   } else {
     if (!(dt > 0)) dt = sh->dt_default;
-    if ((rc = step_graph(sh, u, dt))) return rc;
+    cudaGraphExec_t ge = nullptr;
+    if ((rc = step_graph(sh, u, dt, &ge))) return rc;
     if ((rc = enqueue_step_prologue(sh, u, st))) return rc;
-    for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
+    for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(ge, st));
   }
   CF_CUDA(cudaMemcpyAsync(status, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   return CFFYN_OK;
@@ -855,12 +879,13 @@ int cffyn_rk4_step(cffyn_shell* sh, double* u, double dt, int n_steps, void* str
   if (n_steps == 0) return CFFYN_OK;
   if (!(dt > 0)) dt = sh->dt_default;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((rc = step_graph(sh, u, dt))) return rc;
+  cudaGraphExec_t ge = nullptr;
+  if ((rc = step_graph(sh, u, dt, &ge))) return rc;
   if ((rc = enqueue_step_prologue(sh, u, st))) return rc;
-  for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(sh->graph, st));
+  for (int i = 0; i < n_steps; ++i) CF_CUDA(cudaGraphLaunch(ge, st));
   CF_CUDA(cudaMemcpyAsync(sh->flag_host, sh->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CF_CUDA(cudaStreamSynchronize(st));
-  if (sh->trace && sh->graph_trace && sh->n_marks > 1) {
+  if (sh->trace && sh->n_marks > 1) {
     // the marks hold the last replay; count it n_steps times
     for (int i = 1; i < sh->n_marks; ++i) {
       float ms = 0.f;
@@ -897,10 +922,7 @@ int cffyn_set_operator_rows(cffyn_shell* sh, int family, int rows) {
     build_tc_family(sh, family);
     return rc;
   }
-  if (sh->graph) {
-    cudaGraphExecDestroy(sh->graph);
-    sh->graph = nullptr;
-  }
+  drop_step_graphs(sh);
   ++sh->ws_gen;
   return CFFYN_OK;
 }
@@ -921,10 +943,7 @@ int cffyn_set_wait_limit(cffyn_shell* sh, double seconds) {
   if (ns == sh->tc_wait_ns) return CFFYN_OK;
   sh->tc_wait_ns = ns;
   // the bound is a parameter of the captured kernels
-  if (sh->graph) {
-    cudaGraphExecDestroy(sh->graph);
-    sh->graph = nullptr;
-  }
+  drop_step_graphs(sh);
   ++sh->ws_gen;
   return CFFYN_OK;
 }

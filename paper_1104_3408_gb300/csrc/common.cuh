@@ -147,17 +147,26 @@ struct cffyn_shell {
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
-  // graph of one RK4 step
-  cudaGraphExec_t graph = nullptr;
-  double* graph_u = nullptr;
-  double graph_dt = 0.0;
-  int graph_trace = 0;
-  cudaStream_t graph_stream = nullptr;
-
   // tracing: event nodes at every phase boundary of the captured step
   int trace = 0;
   static constexpr int kPhases = 11;
   static constexpr int kMaxMarks = 64;
+
+  // graphs of one RK4 step for the two most recently used (u, dt, trace):
+  // a caller alternating two state buffers replays both without capturing
+  // again.  Each keeps what its capture recorded about its kernel groups.
+  struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    double* u = nullptr;
+    double dt = 0.0;
+    int trace = 0;
+    int n_marks = 0;
+    int mark_phase[kMaxMarks] = {};
+    int launches[kPhases] = {};
+  };
+  static constexpr int kStepGraphs = 2;
+  StepGraph graphs[kStepGraphs];
+  int graph_victim = 0;  // the entry the next capture replaces
   cudaEvent_t marks[kMaxMarks] = {};
   int mark_phase[kMaxMarks] = {};   // phase that ends at mark i (-1: start)
   int n_marks = 0;

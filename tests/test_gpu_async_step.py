@@ -115,3 +115,26 @@ def test_async_argument_errors(cf):
     with pytest.raises(TypeError):
         sh.rk4_step_async(u, torch.zeros(1, dtype=torch.int64), 0.0, 1)
     sh.destroy()
+
+
+def test_kept_step_graphs_alternating_and_evicted(cf):
+    # the shell keeps the step graphs of its two most recent (u, dt): two
+    # buffers stepped in turn replay them, a third evicts one; every state
+    # must equal the same number of steps taken on a buffer of its own
+    sh, u0 = _shell(cf, cf.MIXED)
+    dt = sh.default_dt()
+    ref = []
+    for k in (1, 2, 3):
+        r = torch.from_numpy(u0).cuda()
+        sh.rk4_step(r, dt, k)
+        ref.append(r)
+    bufs = [torch.from_numpy(u0).cuda() for _ in range(3)]
+    st = _status(9)
+    order = [0, 1, 0, 1, 2, 0, 2, 1, 2]
+    for q, b in enumerate(order):
+        sh.rk4_step_async(bufs[b], st[q:q + 1], dt, 1)
+    torch.cuda.synchronize()
+    cf.check_status(st)
+    for b in range(3):
+        assert torch.equal(bufs[b], ref[order.count(b) - 1])
+    sh.destroy()
