@@ -64,6 +64,7 @@ def test_null_handles_are_rejected(lib):
     assert lib.cffyn_rhs(None, None, None, None) == cffyn.EINVAL
     assert lib.cffyn_filter(None, None, None, None) == cffyn.EINVAL
     assert lib.cffyn_rk4_step(None, None, 0.1, 1, None) == cffyn.EINVAL
+    assert lib.cffyn_rk4_step_async(None, None, 0.1, 1, None, None) == cffyn.EINVAL
     assert lib.cffyn_create_shell_ex(None, None) == cffyn.EINVAL
     assert lib.cffyn_derivs_fft(None, None, None, None) == cffyn.EINVAL
     assert b"NULL" in lib.cffyn_last_error()
@@ -113,3 +114,19 @@ def test_create_checks_filter_kind_and_flags_on_host(lib, field, value, code):
 def test_workspace_calls_reject_null_shell(lib):
     assert lib.cffyn_workspace_size(None) == 0
     assert lib.cffyn_attach_workspace(None, None, 0) == cffyn.EINVAL
+
+
+def test_step_status_words(lib):
+    # the status word of cffyn_rk4_step_async: bit 0 a non-finite stage
+    # right-hand side, bit 1 a bounded tensor-core wait that gave up (the
+    # timeout wins when both are set); host-side decoding only
+    assert lib.cffyn_step_status(0) == cffyn.OK
+    assert lib.cffyn_step_status(1) == cffyn.ENONFINITE
+    assert b"non-finite" in lib.cffyn_last_error()
+    assert lib.cffyn_step_status(2) == cffyn.ETIMEOUT
+    assert b"gave up" in lib.cffyn_last_error()
+    assert lib.cffyn_step_status(3) == cffyn.ETIMEOUT
+    cffyn.check_status(0)
+    with pytest.raises(cffyn.CffynError) as ei:
+        cffyn.check_status(1)
+    assert ei.value.code == cffyn.ENONFINITE
